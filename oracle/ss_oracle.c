@@ -1,0 +1,201 @@
+/*
+ * CPU oracle for string sorting with LCP output.  TEST INFRASTRUCTURE ONLY:
+ * the tests, the smoke check and the benchmark's CPU-baseline leg use it; the
+ * library's sorting path never calls it.  It shares no code with the CUDA
+ * sources.
+ *
+ * It is the plain definition, written to be checked by eye, with no blocking,
+ * caching or fusion:
+ *
+ *   - Section 2.1: the input is n strings s_0..s_{n-1} over the alphabet
+ *     {1..255}; each string ends at its first zero byte, and a shorter string
+ *     that is a prefix of a longer one sorts first (the canonical
+ *     lexicographic order).  Here string i starts at chars[offsets[i]] and,
+ *     when max_len > 0, also ends after max_len bytes (a byte at position
+ *     >= max_len is read as the terminator).
+ *   - Ties (equal strings) are broken by the original index, ascending.  The
+ *     paper leaves this open; this is the reading the sort implements.
+ *   - Section 2.1: lcp(s, t) is the length of the longest common prefix; the
+ *     LCP array of the sorted sequence is H = [h_0, h_1, ..., h_{n-1}] with
+ *     h_i = lcp(s_{i-1}, s_i).  h_0 is undefined in the paper and is 0 here.
+ *     As in the compare loop of Algorithm 4.2, matching stops at the
+ *     terminator, so two equal strings have lcp = their length.
+ *   - Lemma 2.1 (proof): the distinguishing prefix of the sorted string i is
+ *     d_i = max(h_i, h_{i+1}) + 1 with h_0 = h_n = 0, D = sum d_i, and
+ *     L = sum_{i>=1} h_i.
+ *
+ * Parity pins (see tests/): brute force over all n! orders on tiny inputs,
+ * the suffix arrays printed in Figure 5.1, Examples 8.4 and 8.11 and
+ * Figure 6.5, the word list of Figure 2.3, Lemma 2.1's example and bounds, and
+ * an independent library sort on random inputs.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* Byte j of string s (a pointer to its first byte), with the cap applied. */
+static inline unsigned char_at(const uint8_t* s, uint64_t j, uint32_t max_len) {
+    if (max_len != 0 && j >= max_len) return 0;
+    return s[j];
+}
+
+/* Lexicographic comparison of two strings: <0, 0, >0. */
+static int str_compare(const uint8_t* a, const uint8_t* b, uint32_t max_len) {
+    for (uint64_t j = 0;; ++j) {
+        unsigned ca = char_at(a, j, max_len), cb = char_at(b, j, max_len);
+        if (ca != cb) return ca < cb ? -1 : 1;
+        if (ca == 0) return 0;
+    }
+}
+
+/* lcp(a, b): matching positions before the first mismatch or terminator. */
+static uint64_t str_lcp(const uint8_t* a, const uint8_t* b, uint32_t max_len) {
+    uint64_t j = 0;
+    for (;; ++j) {
+        unsigned ca = char_at(a, j, max_len), cb = char_at(b, j, max_len);
+        if (ca != cb || ca == 0) return j;
+    }
+}
+
+/* "i goes before k": string order, ties by index. */
+static int goes_before(const uint8_t* chars, const uint64_t* offsets, uint32_t max_len,
+                       uint32_t i, uint32_t k) {
+    int c = str_compare(chars + offsets[i], chars + offsets[k], max_len);
+    return c < 0 || (c == 0 && i < k);
+}
+
+/* Top-down merge sort of perm[lo, hi) (plain, stable). */
+static void merge_sort(const uint8_t* chars, const uint64_t* offsets, uint32_t max_len,
+                       uint32_t* perm, uint32_t* tmp, uint64_t lo, uint64_t hi) {
+    if (hi - lo < 2) return;
+    uint64_t mid = lo + (hi - lo) / 2;
+    merge_sort(chars, offsets, max_len, perm, tmp, lo, mid);
+    merge_sort(chars, offsets, max_len, perm, tmp, mid, hi);
+    uint64_t a = lo, b = mid, o = lo;
+    while (a < mid && b < hi) {
+        if (goes_before(chars, offsets, max_len, perm[b], perm[a])) tmp[o++] = perm[b++];
+        else tmp[o++] = perm[a++];
+    }
+    while (a < mid) tmp[o++] = perm[a++];
+    while (b < hi) tmp[o++] = perm[b++];
+    memcpy(perm + lo, tmp + lo, (hi - lo) * sizeof(uint32_t));
+}
+
+/* Sort n strings; write the sorted order to perm[n] and, if lcp != NULL, the
+ * LCP array to lcp[n].  Returns 0, or -1 on bad arguments / no memory. */
+int oracle_sort(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t max_len,
+                uint32_t* perm, uint32_t* lcp) {
+    if (n > 0xFFFFFFFFull) return -1;
+    if (n == 0) return 0;
+    uint32_t* tmp = (uint32_t*)malloc(n * sizeof(uint32_t));
+    if (!tmp) return -1;
+    for (uint64_t i = 0; i < n; ++i) perm[i] = (uint32_t)i;
+    merge_sort(chars, offsets, max_len, perm, tmp, 0, n);
+    free(tmp);
+    if (lcp) {
+        lcp[0] = 0;
+        for (uint64_t j = 1; j < n; ++j)
+            lcp[j] = (uint32_t)str_lcp(chars + offsets[perm[j - 1]], chars + offsets[perm[j]], max_len);
+    }
+    return 0;
+}
+
+/* The naive LCP scan alone, for a given order. */
+void oracle_lcp_array(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t max_len,
+                      const uint32_t* perm, uint32_t* lcp) {
+    if (n == 0) return;
+    lcp[0] = 0;
+    for (uint64_t j = 1; j < n; ++j)
+        lcp[j] = (uint32_t)str_lcp(chars + offsets[perm[j - 1]], chars + offsets[perm[j]], max_len);
+}
+
+/* Checks a claimed result without sorting, in O(n + D) time:
+ *   perm is a permutation of [0, n); adjacent strings are in order with ties
+ *   ascending by index; lcp (if given) has lcp[0] = 0 and lcp[j] equal to the
+ *   direct comparison of the two adjacent strings.
+ * Such an order is unique, so passing this check is the same as matching the
+ * oracle's output.  Returns -1 if all holds, else the first failing position
+ * (n for a repeated or out-of-range index). */
+int64_t oracle_check(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t max_len,
+                     const uint32_t* perm, const uint32_t* lcp) {
+    if (n == 0) return -1;
+    uint8_t* seen = (uint8_t*)calloc(n, 1);
+    if (!seen) return 0;
+    for (uint64_t j = 0; j < n; ++j) {
+        if (perm[j] >= n || seen[perm[j]]) { free(seen); return (int64_t)n; }
+        seen[perm[j]] = 1;
+    }
+    free(seen);
+    if (lcp && lcp[0] != 0) return 0;
+    for (uint64_t j = 1; j < n; ++j) {
+        const uint8_t* a = chars + offsets[perm[j - 1]];
+        const uint8_t* b = chars + offsets[perm[j]];
+        int c = str_compare(a, b, max_len);
+        if (c > 0 || (c == 0 && perm[j - 1] > perm[j])) return (int64_t)j;
+        if (lcp && lcp[j] != str_lcp(a, b, max_len)) return (int64_t)j;
+    }
+    return -1;
+}
+
+/* D and L of a sorted set from its LCP array (Lemma 2.1 and its proof). */
+void oracle_dl(const uint32_t* lcp, uint64_t n, uint64_t* D, uint64_t* L) {
+    uint64_t d = 0, l = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        uint64_t left = (i == 0) ? 0 : lcp[i];
+        uint64_t right = (i + 1 < n) ? lcp[i + 1] : 0;
+        d += (left > right ? left : right) + 1;
+        if (i >= 1) l += lcp[i];
+    }
+    *D = d;
+    *L = l;
+}
+
+/* chars_h(s) of Algorithm 4.1: the w = 8 characters of string i at depth h,
+ * packed so that the first character is the most significant byte, with every
+ * position at or after the terminator (or the cap) read as 0.  Reads byte by
+ * byte and never past the terminator. */
+uint64_t oracle_cache(const uint8_t* chars, const uint64_t* offsets, uint64_t i, uint64_t h,
+                      uint32_t max_len) {
+    const uint8_t* s = chars + offsets[i];
+    /* the string has a terminator at or after h only if no terminator lies before h */
+    for (uint64_t j = 0; j < h; ++j)
+        if (char_at(s, j, max_len) == 0) return 0;
+    uint64_t c = 0;
+    int ended = 0;
+    for (int k = 0; k < 8; ++k) {
+        unsigned b = ended ? 0 : char_at(s, h + (uint64_t)k, max_len);
+        if (b == 0) ended = 1;
+        c = (c << 8) | b;
+    }
+    return c;
+}
+
+/* The bucket of Algorithm 4.1 for a key c and v sorted splitters x_0..x_{v-1}:
+ * r = the number of splitters smaller than c (bucket b_{2r}: x_{r-1} < c <
+ * x_r), or the equality bucket 2r+1 when r < v and x_r = c.  Written as a
+ * linear count, not as a tree descent. */
+uint32_t oracle_bucket(uint64_t c, const uint64_t* x, uint32_t v) {
+    uint32_t r = 0;
+    for (uint32_t j = 0; j < v; ++j)
+        if (x[j] < c) ++r;
+    if (r < v && x[r] == c) return 2 * r + 1;
+    return 2 * r;
+}
+
+/* The implicit splitter tree of Section 4.2.3: the perfect binary search tree
+ * whose in-order sequence is x_0..x_{v-1} (v = 2^d - 1), stored in level order
+ * as the one-based array t[1..v] (t[0] is left unused).  For v = 7 this is
+ * t = [x_3, x_1, x_5, x_0, x_2, x_4, x_6].  Written as a recursive in-order
+ * walk over the level-order indices. */
+static void tree_fill(const uint64_t* x, uint64_t* t, uint32_t v, uint32_t node, uint32_t* next) {
+    if (node > v) return;
+    tree_fill(x, t, v, 2 * node, next);
+    t[node] = x[(*next)++];
+    tree_fill(x, t, v, 2 * node + 1, next);
+}
+
+void oracle_tree(const uint64_t* x, uint32_t v, uint64_t* t) {
+    uint32_t next = 0;
+    t[0] = 0;
+    tree_fill(x, t, v, 1, &next);
+}

@@ -1,0 +1,222 @@
+"""Parity pins for the CPU oracle.
+
+Each pin checks the oracle against something other than itself: values the
+paper prints for a worked example (tests/golden/), brute force over all n!
+orders on tiny inputs, Python's own byte-string ordering (an independent
+library sort), closed forms and invariants.  Every pin takes the oracle
+library as an argument so that tests/test_oracle_mutants.py can run the same
+pins against builds of the oracle with a planted mistake.
+"""
+from __future__ import annotations
+
+import bisect
+import itertools
+import os
+
+import numpy as np
+
+import oracle
+from conftest import golden
+
+
+def _strings(chars, offsets, max_len=0):
+    out = []
+    for o in offsets:
+        o = int(o)
+        e = o
+        while chars[e] != 0 and (max_len == 0 or e - o < max_len):
+            e += 1
+        out.append(bytes(chars[o:e]))
+    return out
+
+
+def _text_fixture(name):
+    g = golden(name)
+    text = g["text"].encode() + b"\0"
+    chars = np.frombuffer(text, np.uint8).copy()
+    offsets = np.array([int(x) for x in g["offsets"].split()], np.uint64)
+    perm = [int(x) for x in g["perm"].split()]
+    lcp = [int(x) for x in g["lcp"].split()] if "lcp" in g else None
+    return chars, offsets, int(g["max_len"]), perm, lcp
+
+
+def pin_paper_suffix_examples(lib):
+    """Figure 5.1, Examples 8.4 and 8.11, Figure 6.5: printed suffix arrays
+    (and LCP arrays where printed)."""
+    for name in ("fig5_1.txt", "example_8_4.txt", "example_8_11.txt", "fig6_5.txt"):
+        chars, offsets, max_len, perm, lcp = _text_fixture(name)
+        p, l = oracle.sort(chars, offsets, max_len, lib=lib)
+        assert p.tolist() == perm, name
+        if lcp is not None:
+            assert l.tolist() == lcp, name
+
+
+def pin_word_list_ties(lib):
+    """Figure 2.3: the word list is sorted; the three equal words keep their
+    input order whatever order they are given in."""
+    words = [w.encode() for w in golden("fig2_3.txt")["words"].split()]
+    rng = np.random.default_rng(23)
+    for _ in range(20):
+        order = rng.permutation(len(words))
+        shuffled = [words[i] for i in order]
+        chars, offsets = oracle.from_strings(shuffled)
+        p, l = oracle.sort(chars, offsets, lib=lib)
+        assert [shuffled[i] for i in p] == words
+        by = [int(i) for i in p if shuffled[i] == b"by"]
+        assert by == sorted(by)
+        assert l.tolist()[0] == 0
+
+
+def pin_lemma_2_1(lib):
+    """Lemma 2.1: the printed example (D = 8, L = 2) and n + L <= D <= 2L + n."""
+    g = golden("lemma2_1.txt")
+    words = [w.encode() for w in g["words"].split()]
+    chars, offsets = oracle.from_strings(words)
+    p, l = oracle.sort(chars, offsets, lib=lib)
+    D, L = oracle.dl(l, lib=lib)
+    assert (D, L) == (int(g["D"]), int(g["L"]))
+    rng = np.random.default_rng(21)
+    for t in range(30):
+        n = int(rng.integers(1, 60))
+        strs = [bytes(rng.integers(97, 100, size=int(rng.integers(0, 6))).astype(np.uint8)) for _ in range(n)]
+        chars, offsets = oracle.from_strings(strs)
+        p, l = oracle.sort(chars, offsets, lib=lib)
+        D, L = oracle.dl(l, lib=lib)
+        assert n + L <= D <= 2 * L + n
+        # D counted directly from its definition in the lemma's proof:
+        # d_i = 1 + the longer common prefix with either sorted neighbour.
+        s = sorted(strs)
+        direct = 0
+        for i in range(n):
+            best = 0
+            for j in (i - 1, i + 1):
+                if 0 <= j < n:
+                    best = max(best, len(os.path.commonprefix([s[i], s[j]])))
+            direct += best + 1
+        assert D == direct
+
+
+def _brute_force_order(strs):
+    """The unique order that is non-decreasing with ties by index, found by
+    trying every permutation (Python compares bytes lexicographically by
+    unsigned value, a proper prefix first)."""
+    n = len(strs)
+    for perm in itertools.permutations(range(n)):
+        if all((strs[perm[j - 1]], perm[j - 1]) < (strs[perm[j]], perm[j]) for j in range(1, n)):
+            return list(perm)
+    raise AssertionError("no order found")
+
+
+def pin_brute_force(lib):
+    """All n! orders, n <= 6, small alphabets incl. bytes >= 128, caps."""
+    rng = np.random.default_rng(5)
+    alphabets = [[ord("a"), ord("b")], [1, 200, 255], [ord("x")]]
+    for t in range(150):
+        n = int(rng.integers(1, 7))
+        alpha = alphabets[t % 3]
+        strs = [bytes(rng.choice(alpha, size=int(rng.integers(0, 5))).astype(np.uint8)) for _ in range(n)]
+        if n > 2 and t % 4 == 0:
+            strs[-1] = strs[0]
+        max_len = [0, 0, 1, 2, 3][t % 5]
+        view = [s[:max_len] if max_len else s for s in strs]
+        chars, offsets = oracle.from_strings(strs)
+        p, l = oracle.sort(chars, offsets, max_len, lib=lib)
+        want = _brute_force_order(view)
+        assert p.tolist() == want, (strs, max_len)
+        lcps = [0] + [len(os.path.commonprefix([view[want[j - 1]], view[want[j]]])) for j in range(1, n)]
+        assert l.tolist() == lcps
+
+
+def pin_library_sort(lib):
+    """Python's sorted() on bytes (ties by index) for larger random sets with
+    duplicates, empty strings, high bytes and caps."""
+    rng = np.random.default_rng(9)
+    for t in range(12):
+        n = int(rng.integers(100, 3000))
+        lo, hi = [(97, 99), (1, 255), (65, 68)][t % 3]
+        strs = [bytes(rng.integers(lo, hi + 1, size=int(rng.integers(0, 12))).astype(np.uint8)) for _ in range(n)]
+        for k in range(0, n, 17):
+            strs[k] = strs[(k * 7) % n]
+        max_len = [0, 5, 1, 0][t % 4]
+        view = [s[:max_len] if max_len else s for s in strs]
+        chars, offsets = oracle.from_strings(strs)
+        p, l = oracle.sort(chars, offsets, max_len, lib=lib)
+        want = sorted(range(n), key=lambda i: (view[i], i))
+        assert p.tolist() == want
+        lcps = [0] + [len(os.path.commonprefix([view[want[j - 1]], view[want[j]]])) for j in range(1, n)]
+        assert l.tolist() == lcps
+
+
+def pin_checker(lib):
+    """The O(n + D) checker accepts the true result and rejects planted errors."""
+    rng = np.random.default_rng(11)
+    strs = [bytes(rng.integers(97, 100, size=int(rng.integers(0, 6))).astype(np.uint8)) for _ in range(500)]
+    chars, offsets = oracle.from_strings(strs)
+    want = sorted(range(len(strs)), key=lambda i: (strs[i], i))
+    perm = np.array(want, np.uint32)
+    lcp = np.array([0] + [len(os.path.commonprefix([strs[want[j - 1]], strs[want[j]]]))
+                          for j in range(1, len(want))], np.uint32)
+    assert oracle.check(chars, offsets, perm, lcp, lib=lib) == -1
+    bad = perm.copy()
+    j = next(j for j in range(1, len(want)) if strs[want[j - 1]] != strs[want[j]])
+    bad[j - 1], bad[j] = bad[j], bad[j - 1]
+    assert oracle.check(chars, offsets, bad, lcp, lib=lib) != -1
+    j = next(j for j in range(1, len(want)) if strs[want[j - 1]] == strs[want[j]])
+    bad = perm.copy()
+    bad[j - 1], bad[j] = bad[j], bad[j - 1]
+    assert oracle.check(chars, offsets, bad, lcp, lib=lib) != -1  # tie order
+    badl = lcp.copy()
+    badl[len(badl) // 2] += 1
+    assert oracle.check(chars, offsets, perm, badl, lib=lib) != -1
+    dup = perm.copy()
+    dup[3] = dup[4]
+    assert oracle.check(chars, offsets, dup, lcp, lib=lib) != -1
+
+
+def pin_cache(lib):
+    """chars_h: the 8-byte window read as a big-endian integer (int.from_bytes)
+    with everything at/after the terminator or cap as zero."""
+    rng = np.random.default_rng(13)
+    strs = [bytes(rng.integers(1, 256, size=int(rng.integers(0, 30))).astype(np.uint8)) for _ in range(200)]
+    chars, offsets = oracle.from_strings(strs)
+    for i, s in enumerate(strs):
+        for cap in (0, 3, 8, 9):
+            view = s[:cap] if cap else s
+            for h in (0, 1, 5, 8, 13, 40):
+                window = (view[h:h + 8] if h <= len(view) else b"").ljust(8, b"\0")
+                assert oracle.cache(chars, offsets, i, h, cap, lib=lib) == int.from_bytes(window, "big")
+
+
+def pin_bucket_and_tree(lib):
+    """Section 4.2.3: the printed level-order layout for v = 7; a descent of
+    that tree with i := 2i + [c > t_i] lands on bisect_left(x, c); and the
+    bucket index satisfies the bucket definitions (x_{r-1} < c < x_r for 2r,
+    c == x_r for 2r+1)."""
+    g = golden("tree_v7.txt")
+    v = int(g["v"])
+    x = np.array([10 * (k + 1) for k in range(v)], np.uint64)
+    t = oracle.tree(x, lib=lib)
+    assert [int(z) for z in t[1:]] == [int(x[k]) for k in map(int, g["t_index"].split())]
+    rng = np.random.default_rng(17)
+    for d in (1, 2, 3, 5, 8):
+        v = (1 << d) - 1
+        for _ in range(20):
+            x = np.sort(rng.integers(0, 50, size=v).astype(np.uint64))
+            t = oracle.tree(x, lib=lib)
+            xs = [int(z) for z in x]
+            for c in rng.integers(0, 52, size=20):
+                c = int(c)
+                i = 1
+                for _lvl in range(d):
+                    i = 2 * i + (1 if c > int(t[i]) else 0)
+                assert i - (v + 1) == bisect.bisect_left(xs, c)
+                b = oracle.bucket(c, x, lib=lib)
+                r = b // 2
+                if b % 2:
+                    assert xs[r] == c
+                else:
+                    assert (r == 0 or xs[r - 1] < c) and (r == v or c < xs[r])
+
+
+ALL_PINS = [pin_paper_suffix_examples, pin_word_list_ties, pin_lemma_2_1, pin_brute_force,
+            pin_library_sort, pin_checker, pin_cache, pin_bucket_and_tree]
