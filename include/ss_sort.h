@@ -1,0 +1,171 @@
+/*
+ * ss_sort — string sample sort with LCP output on one NVIDIA GB300 (sm_103a).
+ *
+ * The library sorts n strings and returns their sorted order and LCP array,
+ * following the problem statement of Section 2.1 of Bingmann, "Scalable String
+ * and Suffix Sorting" (arXiv:1808.00963): the input is an array of n strings
+ * over the alphabet {1..255}, each ending at a zero byte; the output is the
+ * lexicographic order and the LCP array H with H[i] = lcp(s_{i-1}, s_i).
+ * The method is the data-parallel step of Super Scalar String Sample Sort
+ * (Algorithm 4.1, Section 4.2.2) and its parallel form (Section 4.2.8).
+ *
+ * Data layout (all data pointers are DEVICE pointers owned by the caller; the
+ * library never frees them):
+ *   chars      uint8[N]   NUL-terminated strings; strings may overlap (e.g.
+ *                         all suffixes of one text).  Any alignment.
+ *   offsets    uint64[n]  string i starts at chars + offsets[i].
+ *   out_perm   uint32[n]  written: out_perm[j] = index of the j-th smallest
+ *                         string.  Equal strings keep ascending index order,
+ *                         so the output is unique.
+ *   out_lcp    uint32[n]  written (may be NULL to skip): out_lcp[0] = 0 and
+ *                         out_lcp[j] = length of the common prefix of strings
+ *                         out_perm[j-1] and out_perm[j].  Two equal strings
+ *                         have lcp = their length.
+ * A string's bytes are read only up to its terminator: the library loads
+ * aligned 8-byte words that hold at least one byte of the string or its
+ * terminator, and never a word that lies wholly past the terminator.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  All work is enqueued on it.
+ *
+ * Errors: argument errors are returned at once, before any work is enqueued.
+ * Errors found on the device (queue overflow, a bounded wait that expired,
+ * a string longer than 2^30 bytes) are latched in a device status word and
+ * returned by the call that waits for the result (ss_sort, ss_sort_ex,
+ * ss_sort_host, ss_sort_batch) or by ss_batch_status().
+ */
+#ifndef SS_SORT_H
+#define SS_SORT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ss_status {
+    SS_OK = 0,
+    SS_ERR_INVALID = 1,     /* bad argument (NULL pointer with n > 0, bad option) */
+    SS_ERR_OOM = 2,         /* device or pinned memory could not be allocated     */
+    SS_ERR_CUDA = 3,        /* a CUDA runtime call failed                         */
+    SS_ERR_TOO_LARGE = 4,   /* n >= 2^32, or a string of 2^30 bytes or more       */
+    SS_ERR_TIMEOUT = 5,     /* a device-side bounded wait expired                 */
+    SS_ERR_QUEUE_FULL = 6,  /* a device task list overflowed its capacity         */
+    SS_ERR_NO_DEVICE = 7    /* no CUDA device, or the device is not sm_103        */
+} ss_status;
+
+/* Tuning and limits.  Zero in any field selects the default. */
+typedef struct ss_options {
+    uint32_t max_len;          /* 0: strings end at their NUL.  Else string i also
+                                  ends after max_len bytes: a byte at position
+                                  >= max_len reads as the terminator.           */
+    uint32_t splitters_log2;   /* d with v = 2^d - 1 splitters per step in the
+                                  single-block steps; 8..10 (default 9).        */
+    uint32_t big_splitters_log2; /* d for the multi-block steps; 8..10 (default 10). */
+    uint32_t tile_rounds;      /* multi-block tile = 256 * tile_rounds strings;
+                                  4..32 (default: chosen from n).               */
+    uint32_t small_cutoff;     /* subsets of at most this many strings are
+                                  finished in shared memory; 64..4096
+                                  (default 2048).                               */
+    uint32_t big_threshold;    /* subsets larger than this use multi-block
+                                  steps; >= small_cutoff (default 65536).        */
+    uint32_t seed;             /* seed of the splitter sample (output does not
+                                  depend on it).                                */
+    uint32_t flags;            /* reserved, must be 0                           */
+    void* workspace;           /* optional caller-owned device workspace of at
+                                  least ss_workspace_size() bytes, 256-byte
+                                  aligned.  NULL: the library allocates
+                                  stream-ordered memory for the call.           */
+    size_t workspace_bytes;
+} ss_options;
+
+/* Sort n strings.  Section 2.1 (problem), Algorithm 4.1 (one S^5 step),
+ * Section 4.2.8 (parallel S^5 and the LCP array).  Enqueues the sort on
+ * `stream` and waits for it (large inputs need the host to plan each
+ * multi-block step).  n = 0 is a no-op; n = 1 gives perm = [0], lcp = [0].
+ * Returns SS_ERR_TOO_LARGE for n >= 2^32. */
+ss_status ss_sort(const uint8_t* chars, const uint64_t* offsets, uint64_t n,
+                  uint32_t* out_perm, uint32_t* out_lcp, void* stream);
+
+/* ss_sort with options (opt may be NULL). */
+ss_status ss_sort_ex(const uint8_t* chars, const uint64_t* offsets, uint64_t n,
+                     uint32_t* out_perm, uint32_t* out_lcp, const ss_options* opt,
+                     void* stream);
+
+/* Device workspace (bytes) that ss_sort_ex needs for n strings with these
+ * options (opt may be NULL). */
+size_t ss_workspace_size(uint64_t n, const ss_options* opt);
+
+/* Same as ss_sort_ex, but chars / offsets / outputs are HOST buffers:
+ * chars_len bytes of chars and n offsets are copied to the device, sorted,
+ * and the results copied back, all inside the call.  The device buffers come
+ * from a per-device cache that grows as needed and is kept until exit. */
+ss_status ss_sort_host(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets,
+                       uint64_t n, uint32_t* out_perm, uint32_t* out_lcp,
+                       const ss_options* opt, void* stream);
+
+/* ---- batched sorting: many independent string sets in one launch ----------- */
+
+/* One string set of a batch (device pointers, as for ss_sort). */
+typedef struct ss_set {
+    const uint8_t* chars;
+    const uint64_t* offsets;
+    uint32_t n;
+    uint32_t max_len;          /* per-set cap, as ss_options.max_len */
+    uint32_t* out_perm;
+    uint32_t* out_lcp;         /* may be NULL */
+} ss_set;
+
+typedef struct ss_batch ss_batch; /* opaque plan */
+
+/* Plan a batch: validates the sets, uploads their descriptors and reserves
+ * the device workspace (the caller's, via opt->workspace, or the library's).
+ * Synchronous.  The total number of strings over all sets must be < 2^32. */
+ss_status ss_batch_create(const ss_set* sets, uint32_t num_sets, const ss_options* opt,
+                          ss_batch** out);
+
+/* Device workspace (bytes) that a batch of these sets needs. */
+size_t ss_batch_workspace_size(const ss_set* sets, uint32_t num_sets, const ss_options* opt);
+
+/* Enqueue the sort of every set of the batch on `stream`.  Asynchronous: no
+ * host synchronisation, no allocation, a fixed sequence of kernel launches
+ * (one persistent work-queue launch does the splitting), so the call can be
+ * captured into a CUDA graph and replayed.  Device-side errors are latched
+ * and read by ss_batch_status(). */
+ss_status ss_batch_run(ss_batch* b, void* stream);
+
+/* Wait for `stream` and return the device status latched by the last
+ * ss_batch_run of this plan. */
+ss_status ss_batch_status(ss_batch* b, void* stream);
+
+/* Release a plan (and its workspace if the library allocated it). */
+ss_status ss_batch_destroy(ss_batch* b);
+
+/* Convenience: create, run on `stream`, wait, destroy. */
+ss_status ss_sort_batch(const ss_set* sets, uint32_t num_sets, const ss_options* opt,
+                        void* stream);
+
+/* ---- diagnostics --------------------------------------------------------------- */
+
+/* Static description of a status code. */
+const char* ss_status_string(ss_status s);
+
+/* Number of kernel launches this library has issued in this process. */
+uint64_t ss_launch_count(void);
+
+/* Per-kernel device timing.  When enabled, the library records CUDA events
+ * around each of its kernel launches on the launching stream and accumulates
+ * the elapsed time per kernel class once the call has waited for its work.
+ * ss_kernel_stats fills up to `cap` entries (name, launches, total ms) and
+ * returns the number of kernel classes. */
+void ss_set_profiling(int enabled);
+uint32_t ss_kernel_stats(const char** names, uint64_t* launches, double* total_ms,
+                         uint32_t cap);
+void ss_reset_kernel_stats(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SS_SORT_H */

@@ -1,0 +1,303 @@
+"""ss_sort: string sample sort with LCP output on a GB300 (sm_103a).
+
+Thin Python binding over the C-ABI library ``_build/libss_sort.so`` (declared
+in ``include/ss_sort.h``).  It only marshals arguments: every step of the sort
+runs in the library's CUDA kernels.  PyTorch is used for device memory and
+streams.  If the library has not been built, every call raises: there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libss_sort.so")
+ROOT = os.path.dirname(_HERE)
+HEADER = os.path.join(ROOT, "include", "ss_sort.h")
+
+SOURCES = ["ss_host.cu", "ss_big.cu", "ss_queue.cu", "ss_small.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+                     "-Xcompiler", "-Wall"]
+
+STATUS = {0: "SS_OK", 1: "SS_ERR_INVALID", 2: "SS_ERR_OOM", 3: "SS_ERR_CUDA", 4: "SS_ERR_TOO_LARGE",
+          5: "SS_ERR_TIMEOUT", 6: "SS_ERR_QUEUE_FULL", 7: "SS_ERR_NO_DEVICE"}
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def _stale(out, deps):
+    if not os.path.exists(out):
+        return True
+    t = os.path.getmtime(out)
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+    """Compile every CUDA translation unit for sm_103a (in parallel) and link
+    the shared library in-tree.  Returns its path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    headers = [os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith((".cuh", ".h"))] + [HEADER]
+    objs = []
+    jobs = []
+    for src in SOURCES:
+        sp = os.path.join(_CSRC, src)
+        obj = os.path.join(_BUILD, src.replace(".cu", ".o"))
+        objs.append(obj)
+        if force or _stale(obj, [sp] + headers):
+            jobs.append([_nvcc(), *NVCC_FLAGS, *extra_flags, "-c", sp, "-o", obj])
+
+    def run(cmd):
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("nvcc failed:\n" + " ".join(cmd) + "\n" + r.stdout + r.stderr)
+        if verbose and (r.stdout or r.stderr):
+            print(r.stdout + r.stderr)
+
+    if jobs:
+        with ThreadPoolExecutor(max_workers=len(jobs)) as ex:
+            list(ex.map(run, jobs))
+    if force or jobs or _stale(LIB_PATH, objs):
+        tmp = LIB_PATH + ".tmp"
+        run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs])
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# ---- ctypes plumbing -----------------------------------------------------------------------
+
+class Options(ctypes.Structure):
+    """Mirror of ss_options (include/ss_sort.h)."""
+    _fields_ = [
+        ("max_len", ctypes.c_uint32),
+        ("splitters_log2", ctypes.c_uint32),
+        ("big_splitters_log2", ctypes.c_uint32),
+        ("tile_rounds", ctypes.c_uint32),
+        ("small_cutoff", ctypes.c_uint32),
+        ("big_threshold", ctypes.c_uint32),
+        ("seed", ctypes.c_uint32),
+        ("flags", ctypes.c_uint32),
+        ("workspace", ctypes.c_void_p),
+        ("workspace_bytes", ctypes.c_size_t),
+    ]
+
+
+class SetDesc(ctypes.Structure):
+    """Mirror of ss_set."""
+    _fields_ = [
+        ("chars", ctypes.c_void_p),
+        ("offsets", ctypes.c_void_p),
+        ("n", ctypes.c_uint32),
+        ("max_len", ctypes.c_uint32),
+        ("out_perm", ctypes.c_void_p),
+        ("out_lcp", ctypes.c_void_p),
+    ]
+
+
+_lib = None
+
+
+class SortError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+
+
+def load(path: str | None = None):
+    """Load the library.  Raises if it has not been built."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"ss_sort CUDA library not built ({p}); run paper_1808_00963_gb300.build()")
+    lib = ctypes.CDLL(p)
+    vp, u64, u32, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    lib.ss_sort.argtypes = [vp, vp, u64, vp, vp, vp]
+    lib.ss_sort.restype = i32
+    lib.ss_sort_ex.argtypes = [vp, vp, u64, vp, vp, ctypes.POINTER(Options), vp]
+    lib.ss_sort_ex.restype = i32
+    lib.ss_workspace_size.argtypes = [u64, ctypes.POINTER(Options)]
+    lib.ss_workspace_size.restype = ctypes.c_size_t
+    lib.ss_sort_host.argtypes = [vp, u64, vp, u64, vp, vp, ctypes.POINTER(Options), vp]
+    lib.ss_sort_host.restype = i32
+    lib.ss_batch_create.argtypes = [ctypes.POINTER(SetDesc), u32, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+    lib.ss_batch_create.restype = i32
+    lib.ss_batch_workspace_size.argtypes = [ctypes.POINTER(SetDesc), u32, ctypes.POINTER(Options)]
+    lib.ss_batch_workspace_size.restype = ctypes.c_size_t
+    lib.ss_batch_run.argtypes = [vp, vp]
+    lib.ss_batch_run.restype = i32
+    lib.ss_batch_status.argtypes = [vp, vp]
+    lib.ss_batch_status.restype = i32
+    lib.ss_batch_destroy.argtypes = [vp]
+    lib.ss_batch_destroy.restype = i32
+    lib.ss_sort_batch.argtypes = [ctypes.POINTER(SetDesc), u32, ctypes.POINTER(Options), vp]
+    lib.ss_sort_batch.restype = i32
+    lib.ss_status_string.argtypes = [i32]
+    lib.ss_status_string.restype = ctypes.c_char_p
+    lib.ss_launch_count.argtypes = []
+    lib.ss_launch_count.restype = u64
+    lib.ss_set_profiling.argtypes = [i32]
+    lib.ss_set_profiling.restype = None
+    lib.ss_kernel_stats.argtypes = [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(u64),
+                                    ctypes.POINTER(ctypes.c_double), u32]
+    lib.ss_kernel_stats.restype = u32
+    lib.ss_reset_kernel_stats.argtypes = []
+    lib.ss_reset_kernel_stats.restype = None
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def make_options(max_len=0, **kw) -> Options:
+    o = Options()
+    o.max_len = max_len
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, v)
+    return o
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(code, what):
+    if code != 0:
+        raise SortError(code, what)
+
+
+def sort(chars, offsets, max_len: int = 0, with_lcp: bool = True, out=None, stream=None, **opts):
+    """Sort the strings of a device string set.
+
+    chars   : torch.uint8 CUDA tensor (NUL-terminated strings)
+    offsets : torch.int64 CUDA tensor (start of each string)
+    Returns (perm, lcp) as torch.int32 CUDA tensors holding uint32 values
+    (lcp is None when with_lcp is False).  Runs on the current stream (or
+    ``stream``) and returns when the sort has finished.
+    """
+    import torch
+    lib = load()
+    n = int(offsets.numel())
+    dev = offsets.device
+    if out is None:
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        lcp = torch.empty(n, dtype=torch.int32, device=dev) if with_lcp else None
+    else:
+        perm, lcp = out
+    assert chars.dtype == torch.uint8 and chars.is_cuda and chars.is_contiguous()
+    assert offsets.dtype == torch.int64 and offsets.is_cuda and offsets.is_contiguous()
+    o = make_options(max_len, **opts)
+    rc = lib.ss_sort_ex(ctypes.c_void_p(chars.data_ptr()), ctypes.c_void_p(offsets.data_ptr()), n,
+                        ctypes.c_void_p(perm.data_ptr()),
+                        ctypes.c_void_p(lcp.data_ptr()) if lcp is not None else None,
+                        ctypes.byref(o), _stream_ptr(stream))
+    _check(rc, "ss_sort_ex")
+    return perm, lcp
+
+
+def sort_host(chars, offsets, max_len: int = 0, with_lcp: bool = True, perm=None, lcp=None, stream=None,
+              **opts):
+    """Sort a host string set (numpy arrays or CPU tensors, ideally pinned):
+    the copies to and from the device happen inside the library call."""
+    import numpy as np
+    lib = load()
+
+    def ptr(a):
+        return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+
+    n = int(offsets.shape[0])
+    if perm is None:
+        perm = np.empty(n, np.uint32)
+    if with_lcp and lcp is None:
+        lcp = np.empty(n, np.uint32)
+    o = make_options(max_len, **opts)
+    nbytes = int(chars.numel() if hasattr(chars, "numel") else chars.size)
+    rc = lib.ss_sort_host(ptr(chars), nbytes, ptr(offsets), n, ptr(perm), ptr(lcp) if with_lcp else None,
+                          ctypes.byref(o), _stream_ptr(stream))
+    _check(rc, "ss_sort_host")
+    return perm, (lcp if with_lcp else None)
+
+
+def workspace_size(n: int, max_len: int = 0, **opts) -> int:
+    o = make_options(max_len, **opts)
+    return int(load().ss_workspace_size(n, ctypes.byref(o)))
+
+
+class Batch:
+    """A planned batch of independent string sets (ss_batch_create / _run).
+
+    sets: list of (chars, offsets, max_len, perm_out, lcp_out) with CUDA
+    tensors (lcp_out may be None).  ``run()`` only enqueues work, so it can be
+    captured into a CUDA graph; ``status()`` waits and reports errors.
+    """
+
+    def __init__(self, sets, **opts):
+        self.lib = load()
+        self.keep = sets
+        arr = (SetDesc * max(1, len(sets)))()
+        for i, (ch, off, ml, p, l) in enumerate(sets):
+            arr[i].chars = ch.data_ptr()
+            arr[i].offsets = off.data_ptr()
+            arr[i].n = int(off.numel())
+            arr[i].max_len = int(ml)
+            arr[i].out_perm = p.data_ptr()
+            arr[i].out_lcp = l.data_ptr() if l is not None else None
+        self.arr = arr
+        self.opts = make_options(0, **opts)
+        h = ctypes.c_void_p()
+        _check(self.lib.ss_batch_create(arr, len(sets), ctypes.byref(self.opts), ctypes.byref(h)),
+               "ss_batch_create")
+        self.h = h
+
+    def run(self, stream=None):
+        _check(self.lib.ss_batch_run(self.h, _stream_ptr(stream)), "ss_batch_run")
+
+    def status(self, stream=None):
+        _check(self.lib.ss_batch_status(self.h, _stream_ptr(stream)), "ss_batch_status")
+
+    def close(self):
+        if self.h:
+            self.lib.ss_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def launch_count() -> int:
+    return int(load().ss_launch_count())
+
+
+def set_profiling(on: bool):
+    load().ss_set_profiling(1 if on else 0)
+
+
+def reset_kernel_stats():
+    load().ss_reset_kernel_stats()
+
+
+def kernel_stats():
+    """{kernel class: (launches, total_ms)} recorded while profiling was on."""
+    lib = load()
+    cap = 64
+    names = (ctypes.c_char_p * cap)()
+    la = (ctypes.c_uint64 * cap)()
+    ms = (ctypes.c_double * cap)()
+    k = lib.ss_kernel_stats(names, la, ms, cap)
+    return {names[i].decode(): (int(la[i]), float(ms[i])) for i in range(min(k, cap))}

@@ -1,0 +1,275 @@
+// Multi-block S^5 steps: the "fully parallel S^5" of Section 4.2.8 for
+// subsets above the big-task threshold.  All big subsets of one round are
+// processed together: one block samples each subset (SampleJob), every tile
+// of every subset is classified and counted by its own block (CountJob), one
+// device-wide prefix sum over the [subset][bucket][tile] counters gives every
+// tile its destination in every bucket (the interleaved prefix sum of
+// Theorem 4.4), one block per subset emits the new subsets, and every tile is
+// redistributed by its own block (DistributeJob).
+#include "ss_kernels.h"
+#include "ss_step.cuh"
+
+namespace ss {
+
+namespace {
+
+__device__ __forceinline__ uint32_t find_gen_task(const GenTask* gt, uint32_t G, uint32_t tile) {
+  uint32_t lo = 0, hi = G - 1;  // last task with tile_start <= tile
+  while (lo < hi) {
+    uint32_t mid = (lo + hi + 1) >> 1;
+    if (gt[mid].tile_start <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint64_t cnt_base(const GenTask& g) {
+  return ((uint64_t)g.cnt_base_hi << 32) | g.cnt_base_lo;
+}
+
+template <int LOGV>
+__global__ void __launch_bounds__(kBlock) k_big_sample(SortCtx c, const GenTask* __restrict__ gt,
+                                                       Splitters<LOGV>* __restrict__ out) {
+  __shared__ __align__(16) Splitters<LOGV> sp;
+  __shared__ __align__(16) BuildScratch<LOGV> bs;
+  const GenTask g = gt[blockIdx.x];
+  const uint64_t* keys = c.key[task_par(g.t)] + g.t.begin;
+  build_splitters<LOGV>(keys, g.t.len, mix64(c.seed ^ ((uint64_t)g.t.begin << 20) ^ g.t.depth), sp, bs);
+  const uint64_t* src = reinterpret_cast<const uint64_t*>(&sp);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(out + blockIdx.x);
+  for (uint32_t i = threadIdx.x; i < sizeof(Splitters<LOGV>) / 8; i += blockDim.x) dst[i] = src[i];
+}
+
+template <int LOGV>
+__global__ void __launch_bounds__(kBlock) k_big_classify(SortCtx c, const GenTask* __restrict__ gt,
+                                                         uint32_t G, const Splitters<LOGV>* __restrict__ spl,
+                                                         uint32_t* __restrict__ counters, uint32_t R) {
+  using Gm = Geo<LOGV>;
+  __shared__ __align__(16) uint64_t tree[Gm::V + 1];
+  __shared__ __align__(16) uint64_t x[Gm::V + 1];
+  __shared__ uint32_t hist[Gm::KP];
+  __shared__ uint32_t s_g;
+  if (threadIdx.x == 0) s_g = find_gen_task(gt, G, blockIdx.x);
+  for (uint32_t b = threadIdx.x; b < Gm::KP; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  const GenTask g = gt[s_g];
+  const Splitters<LOGV>& sp = spl[s_g];
+  for (uint32_t i = threadIdx.x; i <= Gm::V; i += blockDim.x) { tree[i] = sp.tree[i]; x[i] = sp.x[i]; }
+  __syncthreads();
+  const uint32_t tile = blockIdx.x - g.tile_start;
+  const uint32_t T = kBlock * R;
+  const uint32_t t0 = tile * T;
+  const uint32_t tl = min(T, g.t.len - t0);
+  const uint64_t* keys = c.key[task_par(g.t)] + g.t.begin + t0;
+  uint16_t* bo = c.bucket_of + g.t.begin + t0;
+  const uint32_t lim = (tl + kBlock - 1) / kBlock * kBlock;
+  for (uint32_t p = threadIdx.x; p < lim; p += kBlock) {
+    const bool valid = p < tl;
+    uint32_t b = 0xFFFFu;
+    if (valid) {
+      b = classify<LOGV>(keys[p], tree, x);
+      bo[p] = (uint16_t)b;
+    }
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
+    if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  uint32_t* cnt = counters + cnt_base(g) + tile;
+  for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) cnt[(uint64_t)b * g.tiles] = hist[b];
+}
+
+template <int LOGV>
+__global__ void __launch_bounds__(kBlock) k_big_emit(SortCtx c, const GenTask* __restrict__ gt,
+                                                     const Splitters<LOGV>* __restrict__ spl,
+                                                     const uint32_t* __restrict__ scanned,
+                                                     uint32_t* __restrict__ gstart, uint32_t* __restrict__ gdesc,
+                                                     uint32_t next_big) {
+  using Gm = Geo<LOGV>;
+  const GenTask g = gt[blockIdx.x];
+  const Splitters<LOGV>& sp = spl[blockIdx.x];
+  const SetDesc sd = c.sets[task_set(g.t)];
+  const uint32_t* sc = scanned + cnt_base(g);
+  for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) {
+    const uint32_t s = sc[(uint64_t)b * g.tiles] - g.rec_base;
+    const uint32_t e = (b + 1 < Gm::K) ? sc[(uint64_t)(b + 1) * g.tiles] - g.rec_base : g.t.len;
+    const uint32_t size = e - s;
+    gstart[(uint64_t)blockIdx.x * Gm::KP + b] = s;
+    uint32_t desc = kFin;
+    if (size) {
+      desc = bucket_desc<LOGV>(b, size, g.t.depth, sp);
+      emit_bucket(c, sd, g.t, s, size, desc, next_big);
+    }
+    gdesc[(uint64_t)blockIdx.x * Gm::KP + b] = desc;
+  }
+}
+
+template <int LOGV>
+__global__ void __launch_bounds__(kBlock) k_big_scatter(SortCtx c, const GenTask* __restrict__ gt, uint32_t G,
+                                                        const uint32_t* __restrict__ scanned,
+                                                        const uint32_t* __restrict__ gstart,
+                                                        const uint32_t* __restrict__ gdesc, uint32_t R) {
+  using Gm = Geo<LOGV>;
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* cntw = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* base = cntw + kWarps * Gm::KP;
+  uint32_t* desc = base + Gm::KP;
+  uint32_t* bfirst = desc + Gm::KP;
+  uint16_t* tb = reinterpret_cast<uint16_t*>(bfirst + Gm::KP);
+  __shared__ uint32_t s_g;
+  if (threadIdx.x == 0) s_g = find_gen_task(gt, G, blockIdx.x);
+  __syncthreads();
+  const uint32_t gi = s_g;
+  const GenTask g = gt[gi];
+  const SetDesc sd = c.sets[task_set(g.t)];
+  const uint32_t tile = blockIdx.x - g.tile_start;
+  const uint32_t T = kBlock * R;
+  const uint32_t t0 = tile * T;
+  const uint32_t tl = min(T, g.t.len - t0);
+  const uint32_t par = task_par(g.t);
+  const uint16_t* bo = c.bucket_of + g.t.begin + t0;
+  for (uint32_t p = threadIdx.x; p < tl; p += kBlock) tb[p] = bo[p];
+  const uint32_t* sc = scanned + cnt_base(g) + tile;
+  for (uint32_t b = threadIdx.x; b < Gm::K; b += kBlock) {
+    base[b] = g.t.begin + sc[(uint64_t)b * g.tiles] - g.rec_base;
+    desc[b] = gdesc[(uint64_t)gi * Gm::KP + b];
+    bfirst[b] = g.t.begin + gstart[(uint64_t)gi * Gm::KP + b];
+  }
+  __syncthreads();
+  const uint32_t src0 = g.t.begin + t0;
+  const uint32_t depth = g.t.depth;
+  tile_scatter<LOGV>(tb, tl, R, base, cntw, [&](uint32_t p, uint32_t b, uint32_t dest) {
+    move_record(c, sd, par, src0 + p, dest, depth, desc[b], bfirst[b]);
+  });
+}
+
+// ---- exclusive prefix sum over uint32 (three phases) ----------------------------
+
+constexpr uint32_t kScanItems = 16;
+constexpr uint32_t kScanChunk = kBlock * kScanItems;
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane_id() >= (uint32_t)o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan of one value per thread across the block; returns the total.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& excl) {
+  __shared__ uint32_t wsum[kWarps];
+  const uint32_t w = threadIdx.x >> 5;
+  const uint32_t inc = warp_incl_scan(v);
+  if (lane_id() == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t s = lane_id() < kWarps ? wsum[lane_id()] : 0;
+    s = warp_incl_scan(s);
+    if (lane_id() < kWarps) wsum[lane_id()] = s;
+  }
+  __syncthreads();
+  excl = inc - v + (w ? wsum[w - 1] : 0);
+  const uint32_t total = wsum[kWarps - 1];
+  __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_reduce(const uint32_t* __restrict__ a, uint64_t n,
+                                                        uint32_t* __restrict__ part) {
+  const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk;
+  uint32_t s = 0;
+  for (uint32_t i = threadIdx.x; i < kScanChunk; i += kBlock) {
+    const uint64_t k = b0 + i;
+    if (k < n) s += a[k];
+  }
+  uint32_t ex;
+  const uint32_t total = block_excl_scan(s, ex);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_partials(uint32_t* __restrict__ part, uint32_t m) {
+  uint32_t carry = 0;
+  for (uint32_t i0 = 0; i0 < m; i0 += kBlock) {
+    const uint32_t i = i0 + threadIdx.x;
+    const uint32_t v = i < m ? part[i] : 0;
+    uint32_t ex;
+    const uint32_t total = block_excl_scan(v, ex);
+    if (i < m) part[i] = carry + ex;
+    carry += total;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_scan_down(uint32_t* __restrict__ a, uint64_t n,
+                                                      const uint32_t* __restrict__ part) {
+  const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kScanItems; ++j) {
+    const uint64_t k = b0 + j;
+    v[j] = k < n ? a[k] : 0;
+    s += v[j];
+  }
+  uint32_t ex;
+  block_excl_scan(s, ex);
+  uint32_t run = part[blockIdx.x] + ex;
+#pragma unroll
+  for (uint32_t j = 0; j < kScanItems; ++j) {
+    const uint64_t k = b0 + j;
+    if (k < n) a[k] = run;
+    run += v[j];
+  }
+}
+
+}  // namespace
+
+size_t big_splitters_bytes(int logv) {
+  switch (logv) {
+    case 8: return sizeof(Splitters<8>);
+    case 9: return sizeof(Splitters<9>);
+    default: return sizeof(Splitters<10>);
+  }
+}
+
+size_t big_scatter_smem(int logv, uint32_t R) {
+  const uint32_t KP = 2u << logv;
+  return (size_t)(kWarps * KP + 3 * KP) * 4 + (size_t)kBlock * R * 2;
+}
+
+template <int LOGV>
+static cudaError_t launch_big_step_t(const BigStepArgs& a, cudaStream_t st, const LaunchHook& hook) {
+  const size_t smem = big_scatter_smem(LOGV, a.R);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_big_scatter<LOGV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)big_scatter_smem(LOGV, kMaxRounds));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  auto* spl = reinterpret_cast<Splitters<LOGV>*>(a.splitters);
+  hook.run("big_sample", [&] { k_big_sample<LOGV><<<a.G, kBlock, 0, st>>>(a.c, a.gt, spl); });
+  hook.run("big_classify", [&] {
+    k_big_classify<LOGV><<<a.tiles, kBlock, 0, st>>>(a.c, a.gt, a.G, spl, a.counters, a.R);
+  });
+  const uint32_t nb = (uint32_t)((a.ncounters + kScanChunk - 1) / kScanChunk);
+  hook.run("scan", [&] { k_scan_reduce<<<nb, kBlock, 0, st>>>(a.counters, a.ncounters, a.partials); });
+  hook.run("scan", [&] { k_scan_partials<<<1, kBlock, 0, st>>>(a.partials, nb); });
+  hook.run("scan", [&] { k_scan_down<<<nb, kBlock, 0, st>>>(a.counters, a.ncounters, a.partials); });
+  hook.run("big_emit", [&] {
+    k_big_emit<LOGV><<<a.G, kBlock, 0, st>>>(a.c, a.gt, spl, a.counters, a.gstart, a.gdesc, a.next_big);
+  });
+  hook.run("big_scatter", [&] {
+    k_big_scatter<LOGV><<<a.tiles, kBlock, smem, st>>>(a.c, a.gt, a.G, a.counters, a.gstart, a.gdesc, a.R);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_big_step(int logv, const BigStepArgs& a, cudaStream_t st, const LaunchHook& hook) {
+  switch (logv) {
+    case 8: return launch_big_step_t<8>(a, st, hook);
+    case 9: return launch_big_step_t<9>(a, st, hook);
+    default: return launch_big_step_t<10>(a, st, hook);
+  }
+}
+
+}  // namespace ss

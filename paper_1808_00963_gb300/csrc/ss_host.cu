@@ -1,0 +1,595 @@
+// Host orchestrator and C-ABI of ss_sort (declared in include/ss_sort.h).
+//
+// One sort (Section 4.2.8, adapted to one GPU):
+//   1. every string gets a record (cache at depth 0, index) and each set a
+//      root subset;
+//   2. while some subset is larger than the big-task threshold, all such
+//      subsets run one multi-block S^5 step together (the host reads how many
+//      there are after each step, which is the only host synchronisation);
+//   3. one persistent work-queue launch runs single-block S^5 steps until
+//      every remaining subset is at most small_cutoff strings;
+//   4. warps and blocks finish the small subsets;
+//   5. the LCP entries at distribution-step boundaries are resolved.
+// Batches skip step 2 (their launch sequence is fixed, so it can be captured
+// into a CUDA graph).
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ss_sort.h"
+#include "ss_kernels.h"
+#include "ss_step.cuh"
+
+namespace ss {
+
+// ---- launch accounting and profiling -------------------------------------------------
+
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<int> g_profiling{0};
+static std::mutex g_stats_mu;
+static std::map<std::string, std::pair<uint64_t, double>> g_stats;
+
+struct PendingEvent {
+  const char* name;
+  cudaEvent_t a, b;
+};
+static thread_local std::vector<PendingEvent> t_pending;
+
+void LaunchHook::run(const char* name, const std::function<void()>& launch) const {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (!g_profiling.load() || cudaStreamIsCapturing(stream, &cs) != cudaSuccess ||
+      cs != cudaStreamCaptureStatusNone) {
+    launch();
+    return;
+  }
+  PendingEvent p{name, nullptr, nullptr};
+  cudaEventCreate(&p.a);
+  cudaEventCreate(&p.b);
+  cudaEventRecord(p.a, stream);
+  launch();
+  cudaEventRecord(p.b, stream);
+  t_pending.push_back(p);
+}
+
+// Accumulates the timings of this thread's finished launches.
+static void collect_profile() {
+  if (t_pending.empty()) return;
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  for (auto& p : t_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      auto& e = g_stats[p.name];
+      e.first += 1;
+      e.second += ms;
+    }
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  t_pending.clear();
+}
+
+// ---- device information --------------------------------------------------------------
+
+struct DevInfo {
+  bool ok = false;
+  int sms = 0;
+  int queue_blocks[11] = {0};
+};
+
+static std::mutex g_dev_mu;
+static std::map<int, DevInfo> g_dev;
+
+static ss_status device_info(DevInfo& out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SS_ERR_NO_DEVICE;
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  auto it = g_dev.find(dev);
+  if (it == g_dev.end()) {
+    DevInfo d;
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return SS_ERR_NO_DEVICE;
+    d.ok = (p.major == 10 && p.minor == 3);
+    d.sms = p.multiProcessorCount;
+    if (d.ok) {
+      for (int l = 8; l <= 10; ++l) {
+        int b = 0;
+        if (queue_occupancy(l, &b) != cudaSuccess || b < 1) return SS_ERR_CUDA;
+        d.queue_blocks[l] = b;
+      }
+      // keep freed stream-ordered allocations in the pool between calls
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+      }
+    }
+    it = g_dev.emplace(dev, d).first;
+  }
+  if (!it->second.ok) return SS_ERR_NO_DEVICE;
+  out = it->second;
+  return SS_OK;
+}
+
+// ---- options and workspace layout -----------------------------------------------------
+
+struct Opts {
+  uint32_t cap = kNoCap;
+  int logv = 9;        // single-block steps
+  int logv_big = 10;   // multi-block steps
+  uint32_t R = 0;      // 0 = choose per step
+  uint32_t cutoff = 2048;
+  uint32_t big_thr = 65536;
+  uint32_t seed = 0x5EED;
+  uint32_t mq_factor = 16;
+};
+
+static ss_status resolve_opts(const ss_options* o, Opts& r) {
+  r = Opts();
+  if (!o) return SS_OK;
+  if (o->flags != 0) return SS_ERR_INVALID;
+  if (o->max_len) r.cap = o->max_len;
+  if (o->splitters_log2) {
+    if (o->splitters_log2 < 8 || o->splitters_log2 > 10) return SS_ERR_INVALID;
+    r.logv = (int)o->splitters_log2;
+  }
+  if (o->big_splitters_log2) {
+    if (o->big_splitters_log2 < 8 || o->big_splitters_log2 > 10) return SS_ERR_INVALID;
+    r.logv_big = (int)o->big_splitters_log2;
+  }
+  if (o->tile_rounds) {
+    if (o->tile_rounds < 8 || o->tile_rounds > kMaxRounds) return SS_ERR_INVALID;
+    r.R = o->tile_rounds;
+  }
+  if (o->small_cutoff) {
+    if (o->small_cutoff < 64 || o->small_cutoff > 4096) return SS_ERR_INVALID;
+    r.cutoff = o->small_cutoff;
+  }
+  if (o->big_threshold) r.big_thr = o->big_threshold;
+  if (r.big_thr < r.cutoff) return SS_ERR_INVALID;
+  if (o->seed) r.seed = o->seed;
+  if (o->workspace && ((uintptr_t)o->workspace & 255)) return SS_ERR_INVALID;
+  return SS_OK;
+}
+
+static inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static uint32_t pmax_of(uint32_t cutoff) {
+  uint32_t p = 64;
+  while (p < cutoff) p <<= 1;
+  return p;
+}
+
+constexpr uint32_t kCtrlWords = 64;
+enum Ctrl : uint32_t { kCStatus = 0, kCBig0 = 1, kCBig1 = 2, kCHead = 3, kCTail = 4, kCPending = 5,
+                       kCSmallW = 6, kCSmallC = 7 };
+
+struct Layout {
+  size_t ctrl, sets, key0, key1, idx0, idx1, bucket_of, big0, big1, gen, spl, counters, partials, gstart, gdesc,
+      mq_items, mq_ready, sw_items, sc_items, total;
+  uint32_t cap_big, cap_mq, cap_sw, cap_sc;
+  uint64_t ncounters_max;
+};
+
+static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
+  L.cap_big = big ? (uint32_t)(M / ((uint64_t)o.big_thr + 1) + 2) : 0;
+  L.cap_mq = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, std::max<uint64_t>(4096, o.mq_factor * (M / o.cutoff) + 1024));
+  L.cap_sw = (uint32_t)(M / 2 + 2);
+  L.cap_sc = (uint32_t)(M / 33 + 2);
+  const uint64_t KP = 2ull << o.logv_big;
+  const uint64_t tiles_max = big ? M / (kBlock * 8) + L.cap_big : 0;
+  L.ncounters_max = big ? KP * (tiles_max + L.cap_big) : 0;
+  L.ctrl = take(kCtrlWords * 4);
+  L.sets = take((size_t)num_sets * sizeof(SetDesc));
+  L.key0 = take(M * 8);
+  L.key1 = take(M * 8);
+  L.idx0 = take(M * 4);
+  L.idx1 = take(M * 4);
+  L.bucket_of = take(M * 2);
+  L.big0 = take((size_t)L.cap_big * sizeof(Task));
+  L.big1 = take((size_t)L.cap_big * sizeof(Task));
+  L.gen = take((size_t)L.cap_big * sizeof(GenTask));
+  L.spl = take((size_t)L.cap_big * big_splitters_bytes(o.logv_big));
+  L.counters = take(L.ncounters_max * 4);
+  L.partials = take((L.ncounters_max / 4096 + 2) * 4);
+  L.gstart = take((size_t)L.cap_big * KP * 4);
+  L.gdesc = take((size_t)L.cap_big * KP * 4);
+  L.mq_items = take((size_t)L.cap_mq * sizeof(Task));
+  L.mq_ready = take((size_t)L.cap_mq * 4);
+  L.sw_items = take((size_t)L.cap_sw * sizeof(Task));
+  L.sc_items = take((size_t)L.cap_sc * sizeof(Task));
+  L.total = off;
+  return L;
+}
+
+static SortCtx make_ctx(uint8_t* ws, const Layout& L, uint32_t num_sets, uint32_t total, const Opts& o, bool big) {
+  SortCtx c{};
+  uint32_t* ctrl = reinterpret_cast<uint32_t*>(ws + L.ctrl);
+  c.sets = reinterpret_cast<const SetDesc*>(ws + L.sets);
+  c.num_sets = num_sets;
+  c.total = total;
+  c.key[0] = reinterpret_cast<uint64_t*>(ws + L.key0);
+  c.key[1] = reinterpret_cast<uint64_t*>(ws + L.key1);
+  c.idx[0] = reinterpret_cast<uint32_t*>(ws + L.idx0);
+  c.idx[1] = reinterpret_cast<uint32_t*>(ws + L.idx1);
+  c.bucket_of = reinterpret_cast<uint16_t*>(ws + L.bucket_of);
+  c.status = ctrl + kCStatus;
+  c.big[0] = TaskList{reinterpret_cast<Task*>(ws + L.big0), ctrl + kCBig0, L.cap_big};
+  c.big[1] = TaskList{reinterpret_cast<Task*>(ws + L.big1), ctrl + kCBig1, L.cap_big};
+  c.mq = WorkQueue{reinterpret_cast<Task*>(ws + L.mq_items), reinterpret_cast<uint32_t*>(ws + L.mq_ready),
+                   ctrl + kCHead, ctrl + kCTail, ctrl + kCPending, L.cap_mq, 1u};
+  c.small_warp = TaskList{reinterpret_cast<Task*>(ws + L.sw_items), ctrl + kCSmallW, L.cap_sw};
+  c.small_cta = TaskList{reinterpret_cast<Task*>(ws + L.sc_items), ctrl + kCSmallC, L.cap_sc};
+  c.small_cutoff = o.cutoff;
+  c.big_threshold = o.big_thr;
+  c.big_enabled = big ? 1u : 0u;
+  c.seed = o.seed;
+  c.big_cur = 0;
+  return c;
+}
+
+static ss_status map_status(uint32_t st) {
+  if (st & kStTooDeep) return SS_ERR_TOO_LARGE;
+  if (st & kStQueueFull) return SS_ERR_QUEUE_FULL;
+  if (st & kStTimeout) return SS_ERR_TIMEOUT;
+  return SS_OK;
+}
+
+#define SS_CUDA(call)                                     \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) {                              \
+      if (e_ == cudaErrorMemoryAllocation) return SS_ERR_OOM; \
+      return SS_ERR_CUDA;                                 \
+    }                                                     \
+  } while (0)
+
+// Pinned host staging, one per thread, grown as needed.
+struct Pinned {
+  void* p = nullptr;
+  size_t n = 0;
+  ~Pinned() { if (p) cudaFreeHost(p); }
+  ss_status reserve(size_t bytes) {
+    if (bytes <= n) return SS_OK;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = 0;
+    if (cudaMallocHost(&p, bytes) != cudaSuccess) return SS_ERR_OOM;
+    n = bytes;
+    return SS_OK;
+  }
+};
+static thread_local Pinned t_down, t_up;
+
+// Enqueues everything after the set descriptors are in place.
+static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o, const DevInfo& dev,
+                          bool big, cudaStream_t st) {
+  const LaunchHook hook{st};
+  SS_CUDA(cudaMemsetAsync(ws + L.ctrl, 0, kCtrlWords * 4, st));
+  SS_CUDA(cudaMemsetAsync(ws + L.mq_ready, 0, (size_t)L.cap_mq * 4, st));
+  SS_CUDA(launch_init(c, st, hook));
+  if (big) {
+    if (t_down.reserve(64 + (size_t)L.cap_big * sizeof(Task)) != SS_OK) return SS_ERR_OOM;
+    if (t_up.reserve((size_t)L.cap_big * sizeof(GenTask)) != SS_OK) return SS_ERR_OOM;
+    uint32_t cur = 0;
+    const uint32_t K = (2u << o.logv_big) - 1;
+    std::vector<GenTask> gts;
+    while (true) {
+      uint32_t* hcnt = static_cast<uint32_t*>(t_down.p);
+      Task* htasks = reinterpret_cast<Task*>(static_cast<uint8_t*>(t_down.p) + 64);
+      SS_CUDA(cudaMemcpyAsync(hcnt, ws + L.ctrl, 64, cudaMemcpyDeviceToHost, st));
+      SS_CUDA(cudaMemcpyAsync(htasks, ws + (cur ? L.big1 : L.big0), (size_t)L.cap_big * sizeof(Task),
+                              cudaMemcpyDeviceToHost, st));
+      SS_CUDA(cudaStreamSynchronize(st));
+      collect_profile();
+      if (hcnt[kCStatus]) break;
+      const uint32_t G = std::min(hcnt[cur ? kCBig1 : kCBig0], L.cap_big);
+      if (G == 0) break;
+      uint64_t total = 0;
+      for (uint32_t g = 0; g < G; ++g) total += htasks[g].len;
+      uint32_t R = o.R;
+      if (!R) {
+        const uint64_t per = total / ((uint64_t)dev.sms * 2 * kBlock) + 1;
+        R = (uint32_t)std::min<uint64_t>(kMaxRounds, std::max<uint64_t>(8, per));
+      }
+      const uint32_t T = kBlock * R;
+      gts.resize(G);
+      uint32_t tiles = 0, rec = 0;
+      uint64_t cnt = 0;
+      for (uint32_t g = 0; g < G; ++g) {
+        GenTask& x = gts[g];
+        x.t = htasks[g];
+        x.tile_start = tiles;
+        x.tiles = (x.t.len + T - 1) / T;
+        x.rec_base = rec;
+        x.cnt_base_lo = (uint32_t)cnt;
+        x.cnt_base_hi = (uint32_t)(cnt >> 32);
+        tiles += x.tiles;
+        rec += x.t.len;
+        cnt += (uint64_t)K * x.tiles;
+      }
+      if (cnt > L.ncounters_max) return SS_ERR_QUEUE_FULL;
+      std::memcpy(t_up.p, gts.data(), (size_t)G * sizeof(GenTask));
+      SS_CUDA(cudaMemcpyAsync(ws + L.gen, t_up.p, (size_t)G * sizeof(GenTask), cudaMemcpyHostToDevice, st));
+      SS_CUDA(cudaMemsetAsync(ws + L.ctrl + 4 * (cur ? kCBig0 : kCBig1), 0, 4, st));
+      BigStepArgs a;
+      a.c = c;
+      a.c.big_cur = cur;
+      a.gt = reinterpret_cast<const GenTask*>(ws + L.gen);
+      a.G = G;
+      a.tiles = tiles;
+      a.R = R;
+      a.splitters = ws + L.spl;
+      a.counters = reinterpret_cast<uint32_t*>(ws + L.counters);
+      a.ncounters = cnt;
+      a.partials = reinterpret_cast<uint32_t*>(ws + L.partials);
+      a.gstart = reinterpret_cast<uint32_t*>(ws + L.gstart);
+      a.gdesc = reinterpret_cast<uint32_t*>(ws + L.gdesc);
+      a.next_big = cur ^ 1;
+      SS_CUDA(launch_big_step(o.logv_big, a, st, hook));
+      cur ^= 1;
+    }
+  }
+  const uint32_t qgrid = (uint32_t)(dev.sms * dev.queue_blocks[o.logv]);
+  SS_CUDA(launch_queue(o.logv, c, qgrid, kMaxRounds, st, hook));
+  SS_CUDA(launch_small(c, pmax_of(o.cutoff), (uint32_t)dev.sms * 8, (uint32_t)dev.sms * 4, st, hook));
+  const uint32_t fgrid = std::max(1u, std::min<uint32_t>((c.total + kBlock - 1) / kBlock, (uint32_t)dev.sms * 16));
+  SS_CUDA(launch_lcp_fix(c, fgrid, st, hook));
+  return SS_OK;
+}
+
+static ss_status read_status(uint8_t* ws, const Layout& L, cudaStream_t st) {
+  if (t_down.reserve(64) != SS_OK) return SS_ERR_OOM;
+  uint32_t* h = static_cast<uint32_t*>(t_down.p);
+  SS_CUDA(cudaMemcpyAsync(h, ws + L.ctrl, 4, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  collect_profile();
+  return map_status(h[kCStatus]);
+}
+
+static ss_status sort_device(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t* perm,
+                             uint32_t* lcp, const ss_options* opt, cudaStream_t st) {
+  Opts o;
+  ss_status s = resolve_opts(opt, o);
+  if (s != SS_OK) return s;
+  if (n >= 0xFFFFFFFFull) return SS_ERR_TOO_LARGE;
+  if (n == 0) return SS_OK;
+  if (!chars || !offsets || !perm) return SS_ERR_INVALID;
+  DevInfo dev;
+  if ((s = device_info(dev)) != SS_OK) return s;
+  const bool big = n > o.big_thr;
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    const Layout L = make_layout(n, 1, o, big);
+    uint8_t* ws = nullptr;
+    bool owned = false;
+    if (opt && opt->workspace) {
+      if (opt->workspace_bytes < L.total) return SS_ERR_INVALID;
+      ws = static_cast<uint8_t*>(opt->workspace);
+    } else {
+      if (cudaMallocAsync(reinterpret_cast<void**>(&ws), L.total, st) != cudaSuccess) return SS_ERR_OOM;
+      owned = true;
+    }
+    SetDesc sd{chars, offsets, perm, lcp, (uint32_t)n, o.cap, 0, 0};
+    ss_status r = SS_OK;
+    if (t_up.reserve(sizeof(SetDesc)) != SS_OK) r = SS_ERR_OOM;
+    if (r == SS_OK) {
+      // t_up is reused by the step planner: wait for this small copy first
+      std::memcpy(t_up.p, &sd, sizeof(sd));
+      if (cudaMemcpyAsync(ws + L.sets, t_up.p, sizeof(sd), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        r = SS_ERR_CUDA;
+    }
+    if (r == SS_OK) r = run_sort(ws, L, make_ctx(ws, L, 1, (uint32_t)n, o, big), o, dev, big, st);
+    ss_status r2 = read_status(ws, L, st);
+    if (r == SS_OK) r = r2;
+    if (owned) {
+      cudaFreeAsync(ws, st);
+      cudaStreamSynchronize(st);
+    }
+    if (r == SS_ERR_QUEUE_FULL && !(opt && opt->workspace)) {
+      o.mq_factor *= 8;
+      continue;
+    }
+    return r;
+  }
+  return SS_ERR_QUEUE_FULL;
+}
+
+}  // namespace ss
+
+// ---- batches ------------------------------------------------------------------------------
+
+struct ss_batch {
+  ss::Opts o;
+  ss::Layout L;
+  ss::DevInfo dev;
+  uint8_t* ws = nullptr;
+  bool owned = false;
+  uint32_t num_sets = 0;
+  uint32_t total = 0;
+};
+
+using namespace ss;
+
+extern "C" {
+
+const char* ss_status_string(ss_status s) {
+  switch (s) {
+    case SS_OK: return "ok";
+    case SS_ERR_INVALID: return "invalid argument";
+    case SS_ERR_OOM: return "out of memory";
+    case SS_ERR_CUDA: return "CUDA runtime error";
+    case SS_ERR_TOO_LARGE: return "input too large (n >= 2^32 or a string of 2^30 bytes or more)";
+    case SS_ERR_TIMEOUT: return "a bounded device-side wait expired";
+    case SS_ERR_QUEUE_FULL: return "a device task list overflowed";
+    case SS_ERR_NO_DEVICE: return "no sm_103 CUDA device";
+  }
+  return "unknown status";
+}
+
+uint64_t ss_launch_count(void) { return g_launches.load(); }
+
+void ss_set_profiling(int enabled) { g_profiling.store(enabled ? 1 : 0); }
+
+void ss_reset_kernel_stats(void) {
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  g_stats.clear();
+}
+
+uint32_t ss_kernel_stats(const char** names, uint64_t* launches, double* total_ms, uint32_t cap) {
+  std::lock_guard<std::mutex> lk(g_stats_mu);
+  uint32_t i = 0;
+  for (auto& kv : g_stats) {
+    if (i < cap) {
+      if (names) names[i] = kv.first.c_str();
+      if (launches) launches[i] = kv.second.first;
+      if (total_ms) total_ms[i] = kv.second.second;
+    }
+    ++i;
+  }
+  return i;
+}
+
+size_t ss_workspace_size(uint64_t n, const ss_options* opt) {
+  Opts o;
+  if (resolve_opts(opt, o) != SS_OK || n >= 0xFFFFFFFFull) return 0;
+  return make_layout(n, 1, o, n > o.big_thr).total;
+}
+
+ss_status ss_sort_ex(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t* out_perm,
+                     uint32_t* out_lcp, const ss_options* opt, void* stream) {
+  return sort_device(chars, offsets, n, out_perm, out_lcp, opt, static_cast<cudaStream_t>(stream));
+}
+
+ss_status ss_sort(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t* out_perm,
+                  uint32_t* out_lcp, void* stream) {
+  return ss_sort_ex(chars, offsets, n, out_perm, out_lcp, nullptr, stream);
+}
+
+ss_status ss_sort_host(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets, uint64_t n,
+                       uint32_t* out_perm, uint32_t* out_lcp, const ss_options* opt, void* stream) {
+  if (n >= 0xFFFFFFFFull) return SS_ERR_TOO_LARGE;
+  if (n == 0) return SS_OK;
+  if (!chars || !offsets || !out_perm || chars_len == 0) return SS_ERR_INVALID;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  DevInfo dev;
+  ss_status s = device_info(dev);
+  if (s != SS_OK) return s;
+  const size_t cb = align256(chars_len + 16), ob = align256(n * 8), pb = align256(n * 4);
+  const size_t need = cb + ob + 2 * pb;
+  uint8_t* d = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&d), need, st) != cudaSuccess) return SS_ERR_OOM;
+  uint8_t* dchars = d;
+  uint64_t* doff = reinterpret_cast<uint64_t*>(d + cb);
+  uint32_t* dperm = reinterpret_cast<uint32_t*>(d + cb + ob);
+  uint32_t* dlcp = out_lcp ? reinterpret_cast<uint32_t*>(d + cb + ob + pb) : nullptr;
+  ss_status r = SS_OK;
+  if (cudaMemcpyAsync(dchars, chars, chars_len, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(doff, offsets, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    r = SS_ERR_CUDA;
+  if (r == SS_OK) r = sort_device(dchars, doff, n, dperm, dlcp, opt, st);
+  if (r == SS_OK) {
+    if (cudaMemcpyAsync(out_perm, dperm, n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) r = SS_ERR_CUDA;
+    if (out_lcp && cudaMemcpyAsync(out_lcp, dlcp, n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      r = SS_ERR_CUDA;
+  }
+  cudaFreeAsync(d, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && r == SS_OK) r = SS_ERR_CUDA;
+  return r;
+}
+
+static ss_status batch_geometry(const ss_set* sets, uint32_t num_sets, uint64_t* total) {
+  if (num_sets && !sets) return SS_ERR_INVALID;
+  uint64_t t = 0;
+  for (uint32_t i = 0; i < num_sets; ++i) {
+    const ss_set& s = sets[i];
+    if (s.n && (!s.chars || !s.offsets || !s.out_perm)) return SS_ERR_INVALID;
+    t += s.n;
+  }
+  if (t >= 0xFFFFFFFFull) return SS_ERR_TOO_LARGE;
+  *total = t;
+  return SS_OK;
+}
+
+size_t ss_batch_workspace_size(const ss_set* sets, uint32_t num_sets, const ss_options* opt) {
+  Opts o;
+  uint64_t total = 0;
+  if (resolve_opts(opt, o) != SS_OK || batch_geometry(sets, num_sets, &total) != SS_OK) return 0;
+  return make_layout(total, num_sets, o, false).total;
+}
+
+ss_status ss_batch_create(const ss_set* sets, uint32_t num_sets, const ss_options* opt, ss_batch** out) {
+  if (!out) return SS_ERR_INVALID;
+  *out = nullptr;
+  ss_batch b;
+  ss_status s = resolve_opts(opt, b.o);
+  if (s != SS_OK) return s;
+  uint64_t total = 0;
+  if ((s = batch_geometry(sets, num_sets, &total)) != SS_OK) return s;
+  if ((s = device_info(b.dev)) != SS_OK) return s;
+  b.L = make_layout(total, num_sets, b.o, false);
+  if (opt && opt->workspace) {
+    if (opt->workspace_bytes < b.L.total) return SS_ERR_INVALID;
+    b.ws = static_cast<uint8_t*>(opt->workspace);
+  } else {
+    if (cudaMalloc(reinterpret_cast<void**>(&b.ws), b.L.total) != cudaSuccess) return SS_ERR_OOM;
+    b.owned = true;
+  }
+  std::vector<SetDesc> sd(num_sets);
+  uint32_t base = 0;
+  for (uint32_t i = 0; i < num_sets; ++i) {
+    const ss_set& x = sets[i];
+    sd[i] = SetDesc{x.chars, x.offsets, x.out_perm, x.out_lcp, x.n, x.max_len ? x.max_len : kNoCap, base, 0};
+    base += x.n;
+  }
+  if (num_sets && cudaMemcpy(b.ws + b.L.sets, sd.data(), sd.size() * sizeof(SetDesc), cudaMemcpyHostToDevice) !=
+                      cudaSuccess) {
+    if (b.owned) cudaFree(b.ws);
+    return SS_ERR_CUDA;
+  }
+  b.num_sets = num_sets;
+  b.total = (uint32_t)total;
+  *out = new ss_batch(b);
+  return SS_OK;
+}
+
+ss_status ss_batch_run(ss_batch* b, void* stream) {
+  if (!b) return SS_ERR_INVALID;
+  if (b->num_sets == 0) return SS_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SortCtx c = make_ctx(b->ws, b->L, b->num_sets, b->total, b->o, false);
+  return run_sort(b->ws, b->L, c, b->o, b->dev, false, st);
+}
+
+ss_status ss_batch_status(ss_batch* b, void* stream) {
+  if (!b) return SS_ERR_INVALID;
+  if (b->num_sets == 0) return SS_OK;
+  return read_status(b->ws, b->L, static_cast<cudaStream_t>(stream));
+}
+
+ss_status ss_batch_destroy(ss_batch* b) {
+  if (!b) return SS_ERR_INVALID;
+  if (b->owned) cudaFree(b->ws);
+  delete b;
+  return SS_OK;
+}
+
+ss_status ss_sort_batch(const ss_set* sets, uint32_t num_sets, const ss_options* opt, void* stream) {
+  ss_batch* b = nullptr;
+  ss_status s = ss_batch_create(sets, num_sets, opt, &b);
+  if (s != SS_OK) return s;
+  s = ss_batch_run(b, stream);
+  ss_status s2 = ss_batch_status(b, stream);
+  ss_batch_destroy(b);
+  return s != SS_OK ? s : s2;
+}
+
+}  // extern "C"

@@ -1,0 +1,219 @@
+// Internal definitions shared by the CUDA translation units of ss_sort.
+//
+// Records: every string that is still being sorted is one record
+// (key, idx) in structure-of-arrays form: key is the string's 8-byte character
+// cache at its subset's current depth (chars_h of Algorithm 4.1, first
+// character in the most significant byte), idx its index in its set.  Records
+// of one subset ("task") sit contiguously at [begin, begin + len) in one of
+// two record buffers; a distribution step moves them to the same range of the
+// other buffer (out-of-place redistribution with alternating roles,
+// Section 4.2.8), so the range a record occupies after its last move is its
+// final sorted position.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ss {
+
+constexpr uint32_t kNoCap = 0xFFFFFFFFu;
+constexpr uint32_t kMaxDepth = (1u << 30) - 16;  // deeper strings: SS_ERR_TOO_LARGE
+constexpr uint32_t kLcpMark = 0x80000000u;        // out_lcp[j] = mark | depth: fix up later
+
+// Device status bits (latched with atomicOr; the host maps them to ss_status).
+constexpr uint32_t kStQueueFull = 1u << 0;
+constexpr uint32_t kStTimeout = 1u << 1;
+constexpr uint32_t kStTooDeep = 1u << 2;
+
+// One string set.
+struct SetDesc {
+  const uint8_t* chars;
+  const uint64_t* offsets;
+  uint32_t* perm;
+  uint32_t* lcp;     // nullptr: no LCP output
+  uint32_t n;
+  uint32_t cap;      // kNoCap or max_len
+  uint32_t base;     // first record position of this set
+  uint32_t pad;
+};
+
+// A subset of records with a common prefix of `depth` characters.
+struct Task {
+  uint32_t begin;
+  uint32_t len;
+  uint32_t depth;
+  uint32_t meta;     // bit 31: record buffer (parity); bits 0..30: set id
+};
+
+__host__ __device__ inline uint32_t task_set(const Task& t) { return t.meta & 0x7FFFFFFFu; }
+__host__ __device__ inline uint32_t task_par(const Task& t) { return t.meta >> 31; }
+__host__ __device__ inline uint32_t make_meta(uint32_t set, uint32_t par) { return set | (par << 31); }
+
+// Task of one multi-block step, augmented by the host plan.
+struct GenTask {
+  Task t;
+  uint32_t tile_start;  // first global tile of this task
+  uint32_t tiles;       // tiles of this task
+  uint32_t rec_base;    // sum of len over earlier tasks of this step
+  uint32_t cnt_base_lo; // first counter (low / high 32 bits)
+  uint32_t cnt_base_hi;
+  uint32_t pad[3];
+};
+
+// Append-only task list in device memory.
+struct TaskList {
+  Task* items;
+  uint32_t* count;     // device counter
+  uint32_t cap;
+};
+
+// Work queue of the persistent kernel: a linear array of slots; a slot is
+// ready once its flag equals the epoch of the current sort.
+struct WorkQueue {
+  Task* items;
+  uint32_t* ready;
+  uint32_t* head;      // next slot to claim
+  uint32_t* tail;      // next slot to fill
+  uint32_t* pending;   // tasks pushed and not yet finished
+  uint32_t cap;
+  uint32_t epoch;
+};
+
+// Everything a kernel needs about the sort in flight.
+struct SortCtx {
+  const SetDesc* sets;
+  uint32_t num_sets;
+  uint32_t total;          // records over all sets
+  uint64_t* key[2];
+  uint32_t* idx[2];
+  uint16_t* bucket_of;     // bucket index of each record (array o of Algorithm 4.1)
+  uint32_t* status;
+  TaskList big[2];         // multi-block tasks, ping-pong by step
+  WorkQueue mq;            // tasks for the persistent single-block kernel
+  TaskList small_warp;     // 2..32 records
+  TaskList small_cta;      // 33..small_cutoff records
+  uint32_t small_cutoff;
+  uint32_t big_threshold;  // tasks longer than this go to big[] (if big_enabled)
+  uint32_t big_enabled;
+  uint32_t seed;
+  uint32_t big_cur;        // which big[] list the current step reads
+};
+
+// ---------------------------------------------------------------------------
+// Character cache: chars_h(s) of Algorithm 4.1 (w = 8).
+
+// Index (0..7) of the lowest zero byte of a little-endian word, 8 if none.
+// The borrow of (x - 0x01..01) can only flag bytes above a true zero byte, so
+// the lowest flagged byte is exact.
+__device__ __forceinline__ uint32_t first_zero_byte(uint64_t x) {
+  uint64_t t = (x - 0x0101010101010101ull) & ~x & 0x8080808080808080ull;
+  return t ? (uint32_t)(__ffsll((long long)t) - 1) >> 3 : 8u;
+}
+
+__device__ __forceinline__ uint64_t bswap64(uint64_t v) {
+  uint32_t lo = (uint32_t)v, hi = (uint32_t)(v >> 32);
+  return ((uint64_t)__byte_perm(lo, 0, 0x0123) << 32) | __byte_perm(hi, 0, 0x0123);
+}
+
+// The 8 characters of the string at chars + off from depth h on, first
+// character in the most significant byte; positions at/after the terminator
+// or at/after `cap` read as 0.  Precondition: the string has no terminator
+// before position h (so the word holding position h holds a byte of the
+// string or its terminator).  Loads only aligned 8-byte words holding at
+// least one byte of the string or its terminator.
+__device__ __forceinline__ uint64_t load_cache(const uint8_t* chars, uint64_t off, uint32_t h,
+                                               uint32_t cap) {
+  if (h >= cap) return 0;
+  const uintptr_t a = (uintptr_t)(chars + off + h);
+  const uint64_t* p = (const uint64_t*)(a & ~(uintptr_t)7);
+  const uint32_t sh = (uint32_t)(a & 7);
+  const uint32_t nb0 = 8 - sh;               // bytes of interest in the first word
+  uint64_t v = __ldg(p) >> (8 * sh);
+  const uint32_t room = cap - h;             // bytes before the cap (>= 1)
+  uint32_t z;
+  if (sh == 0) {
+    z = first_zero_byte(v);
+  } else {
+    z = first_zero_byte(v | (~0ull << (8 * nb0)));
+    if (z >= nb0 && room > nb0) {            // no terminator in the first word
+      v |= __ldg(p + 1) << (8 * nb0);
+      z = first_zero_byte(v);
+    }
+  }
+  uint32_t keep = z < room ? z : room;       // bytes to keep (0..8)
+  if (keep < 8) v &= (keep == 0) ? 0ull : (~0ull >> (64 - 8 * keep));
+  return bswap64(v);
+}
+
+// Length of the common prefix of two caches, in characters (8 if equal).
+__device__ __forceinline__ uint32_t lcp8(uint64_t a, uint64_t b) {
+  uint64_t x = a ^ b;
+  return x ? (uint32_t)__clzll((long long)x) >> 3 : 8u;
+}
+
+// True if the cache holds the terminator (after it every byte is 0, so the
+// last byte is 0 iff a terminator lies inside the window).
+__device__ __forceinline__ bool has_nul(uint64_t c) { return (c & 0xFFu) == 0; }
+
+// Characters before the terminator inside a cache that holds one.
+__device__ __forceinline__ uint32_t nnz_prefix(uint64_t c) {
+  return c ? 8u - ((uint32_t)(__ffsll((long long)c) - 1) >> 3) : 0u;
+}
+
+// Counter-based hash for sample positions (SplitMix64 finaliser).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void latch_status(uint32_t* status, uint32_t bit) {
+  atomicOr(status, bit);
+}
+
+// Append to a task list; on overflow the task is dropped and the status
+// latched (the host then reports SS_ERR_QUEUE_FULL).
+__device__ __forceinline__ void list_push(const TaskList& l, const Task& t, uint32_t* status) {
+  uint32_t slot = atomicAdd(l.count, 1u);
+  if (slot < l.cap) l.items[slot] = t;
+  else latch_status(status, kStQueueFull);
+}
+
+// Push to the work queue of the persistent kernel.
+__device__ __forceinline__ void queue_push(const WorkQueue& q, const Task& t, uint32_t* status) {
+  atomicAdd(q.pending, 1u);
+  uint32_t slot = atomicAdd(q.tail, 1u);
+  if (slot >= q.cap) {
+    latch_status(status, kStQueueFull);
+    atomicSub(q.pending, 1u);
+    return;
+  }
+  q.items[slot] = t;
+  __threadfence();
+  atomicExch(q.ready + slot, q.epoch);
+}
+
+// Route a new subset (len >= 2, not finished) to the list that handles its size.
+__device__ __forceinline__ void route_task(const SortCtx& c, const Task& t, uint32_t next_big) {
+  if (t.depth > kMaxDepth) { latch_status(c.status, kStTooDeep); return; }
+  if (c.big_enabled && t.len > c.big_threshold) list_push(c.big[next_big], t, c.status);
+  else if (t.len > c.small_cutoff) queue_push(c.mq, t, c.status);
+  else if (t.len > 32) list_push(c.small_cta, t, c.status);
+  else list_push(c.small_warp, t, c.status);
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+}  // namespace ss

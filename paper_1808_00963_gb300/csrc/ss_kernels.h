@@ -1,0 +1,54 @@
+// Host-side launch interface between the orchestrator (ss_host.cu) and the
+// kernel translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <functional>
+
+#include <cuda_runtime.h>
+
+#include "ss_internal.cuh"
+
+namespace ss {
+
+// Wraps every kernel launch: counts it and, when profiling is on, brackets it
+// with CUDA events on the launching stream.
+struct LaunchHook {
+  cudaStream_t stream;
+  void run(const char* name, const std::function<void()>& launch) const;
+};
+
+struct BigStepArgs {
+  SortCtx c;
+  const GenTask* gt;      // G tasks (device)
+  uint32_t G;
+  uint32_t tiles;         // total tiles over the G tasks
+  uint32_t R;             // tile = 256 * R records
+  void* splitters;        // G * big_splitters_bytes(logv)
+  uint32_t* counters;     // ncounters, [task][bucket][tile]
+  uint64_t ncounters;
+  uint32_t* partials;     // ceil(ncounters / 4096)
+  uint32_t* gstart;       // G * KP
+  uint32_t* gdesc;        // G * KP
+  uint32_t next_big;      // big list that receives the next round's tasks
+};
+
+size_t big_splitters_bytes(int logv);
+size_t big_scatter_smem(int logv, uint32_t R);
+cudaError_t launch_big_step(int logv, const BigStepArgs& a, cudaStream_t st, const LaunchHook& hook);
+
+// Persistent work-queue kernel (single-block S^5 steps).
+size_t queue_smem(int logv);
+cudaError_t queue_occupancy(int logv, int* blocks_per_sm);
+cudaError_t launch_queue(int logv, const SortCtx& c, uint32_t grid, uint32_t R, cudaStream_t st,
+                         const LaunchHook& hook);
+
+// Small subsets, set-up and LCP fix-up.
+size_t small_cta_smem(uint32_t pmax);
+cudaError_t launch_init(const SortCtx& c, cudaStream_t st, const LaunchHook& hook);
+cudaError_t launch_small(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, uint32_t grid_cta,
+                         cudaStream_t st, const LaunchHook& hook);
+cudaError_t launch_lcp_fix(const SortCtx& c, uint32_t grid, cudaStream_t st, const LaunchHook& hook);
+
+}  // namespace ss

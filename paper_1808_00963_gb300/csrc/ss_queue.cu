@@ -1,0 +1,225 @@
+// Persistent work-queue kernel: the GPU counterpart of the job queue of
+// Section 4.2.8.  Each block repeatedly claims a subset from a device queue
+// and runs one complete S^5 step on it (Algorithm 4.1: sample, splitter tree,
+// classification, counting, prefix sum, stable redistribution).  Buckets that
+// are still unsorted and larger than the small-sort cutoff are pushed back
+// onto the same queue (an equality bucket whose splitter has no terminator is
+// requeued at depth + 8); smaller ones go to the small-sort lists.
+//
+// Termination: `pending` counts tasks pushed and not yet finished; a block
+// that finds its claimed slot empty exits once pending is 0.  Every wait is
+// bounded by a wall-clock budget, after which the status word is latched and
+// the block exits.
+#include "ss_kernels.h"
+#include "ss_step.cuh"
+
+namespace ss {
+
+namespace {
+
+constexpr uint64_t kQueueWaitNs = 30ull * 1000 * 1000 * 1000;
+
+template <int LOGV>
+struct QueueSmem {
+  Splitters<LOGV> sp;
+  uint32_t hist[Geo<LOGV>::KP];    // bucket sizes, then running destinations
+  uint32_t bstart[Geo<LOGV>::KP];  // bucket starts relative to the task (KP >= K + 1)
+  uint32_t desc[Geo<LOGV>::KP];
+  union U {
+    BuildScratch<LOGV> bs;
+    struct {
+      uint32_t cntw[kWarps * Geo<LOGV>::KP];
+      uint16_t tb[kMaxTile];
+    } sc;
+  } u;
+  Task task;
+  uint32_t got;
+};
+
+// Claims the next slot; waits (bounded) until it is filled or all work is done.
+__device__ bool claim_task(const WorkQueue& q, Task* out, uint32_t* status) {
+  const uint32_t slot = atomicAdd(q.head, 1u);
+  if (slot >= q.cap) return false;
+  const uint64_t t0 = globaltimer_ns();
+  uint32_t ns = 64;
+  volatile uint32_t* ready = q.ready;
+  volatile uint32_t* pending = q.pending;
+  while (true) {
+    if (ready[slot] == q.epoch) {
+      __threadfence();
+      const uint4 v = __ldcg(reinterpret_cast<const uint4*>(q.items + slot));
+      *out = Task{v.x, v.y, v.z, v.w};
+      return true;
+    }
+    if (*pending == 0) return false;
+    if (globaltimer_ns() - t0 > kQueueWaitNs) {
+      latch_status(status, kStTimeout);
+      return false;
+    }
+    __nanosleep(ns);
+    ns = ns < 2048 ? ns * 2 : ns;
+  }
+}
+
+// Exclusive scan of n (a multiple of the block size) counters in shared memory.
+__device__ void block_excl_scan_smem(const uint32_t* in, uint32_t* out, uint32_t n) {
+  __shared__ uint32_t wsum[kWarps];
+  const uint32_t per = n / kBlock;
+  const uint32_t b0 = threadIdx.x * per;
+  uint32_t s = 0;
+  for (uint32_t j = 0; j < per; ++j) s += in[b0 + j];
+  uint32_t inc = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane_id() >= (uint32_t)o) inc += t;
+  }
+  const uint32_t w = threadIdx.x >> 5;
+  if (lane_id() == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t v = lane_id() < kWarps ? wsum[lane_id()] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane_id() >= (uint32_t)o) v += t;
+    }
+    if (lane_id() < kWarps) wsum[lane_id()] = v;
+  }
+  __syncthreads();
+  uint32_t run = inc - s + (w ? wsum[w - 1] : 0);
+  for (uint32_t j = 0; j < per; ++j) {
+    const uint32_t v = in[b0 + j];
+    out[b0 + j] = run;
+    run += v;
+  }
+  __syncthreads();
+}
+
+// One S^5 step on task t by this block.
+template <int LOGV>
+__device__ void queue_step(const SortCtx& c, const Task& t, QueueSmem<LOGV>& s, uint32_t R) {
+  using Gm = Geo<LOGV>;
+  const SetDesc sd = c.sets[task_set(t)];
+  const uint32_t par = task_par(t);
+  const uint64_t* keys = c.key[par] + t.begin;
+  build_splitters<LOGV>(keys, t.len, mix64(c.seed ^ ((uint64_t)t.begin << 20) ^ t.depth), s.sp, s.u.bs);
+
+  // lines 6-14: classify into the array o and count
+  for (uint32_t b = threadIdx.x; b < Gm::KP; b += kBlock) s.hist[b] = 0;
+  __syncthreads();
+  uint16_t* bo = c.bucket_of + t.begin;
+  const uint32_t lim = (t.len + kBlock - 1) / kBlock * kBlock;
+  for (uint32_t p = threadIdx.x; p < lim; p += kBlock) {
+    const bool valid = p < t.len;
+    uint32_t b = 0xFFFFu;
+    if (valid) {
+      b = classify<LOGV>(keys[p], s.sp.tree, s.sp.x);
+      bo[p] = (uint16_t)b;
+    }
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
+    if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s.hist[b], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+
+  // line 15: prefix sum; bucket outcomes
+  block_excl_scan_smem(s.hist, s.bstart, Gm::KP);  // bstart[K] = len (hist[K] is 0)
+  for (uint32_t b = threadIdx.x; b < Gm::K; b += kBlock) {
+    const uint32_t size = s.hist[b];
+    s.desc[b] = size ? bucket_desc<LOGV>(b, size, t.depth, s.sp) : kFin;
+    s.hist[b] = t.begin + s.bstart[b];
+  }
+  __syncthreads();
+
+  // line 16: stable out-of-place redistribution, tile by tile
+  const uint32_t T = kBlock * R;
+  for (uint32_t t0 = 0; t0 < t.len; t0 += T) {
+    const uint32_t tl = min(T, t.len - t0);
+    for (uint32_t p = threadIdx.x; p < tl; p += kBlock) s.u.sc.tb[p] = bo[t0 + p];
+    __syncthreads();
+    const uint32_t src0 = t.begin + t0;
+    tile_scatter<LOGV>(s.u.sc.tb, tl, R, s.hist, s.u.sc.cntw, [&](uint32_t p, uint32_t b, uint32_t dest) {
+      move_record(c, sd, par, src0 + p, dest, t.depth, s.desc[b], t.begin + s.bstart[b]);
+    });
+  }
+  __threadfence();
+  __syncthreads();
+
+  // new subsets become visible only after their records have been moved
+  for (uint32_t b = threadIdx.x; b < Gm::K; b += kBlock) {
+    const uint32_t start = s.bstart[b];
+    const uint32_t size = s.bstart[b + 1] - start;
+    if (size) emit_bucket(c, sd, t, start, size, s.desc[b], 0);
+  }
+}
+
+template <int LOGV>
+__global__ void __launch_bounds__(kBlock) k_queue(SortCtx c, uint32_t R) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  QueueSmem<LOGV>& s = *reinterpret_cast<QueueSmem<LOGV>*>(smem);
+  while (true) {
+    if (threadIdx.x == 0) s.got = claim_task(c.mq, &s.task, c.status) ? 1u : 0u;
+    __syncthreads();
+    if (!s.got) break;
+    const Task t = s.task;
+    queue_step<LOGV>(c, t, s, R);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicSub(c.mq.pending, 1u);
+    }
+  }
+}
+
+template <int LOGV>
+cudaError_t set_queue_attr() {
+  static cudaError_t e = cudaFuncSetAttribute(k_queue<LOGV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)sizeof(QueueSmem<LOGV>));
+  return e;
+}
+
+}  // namespace
+
+size_t queue_smem(int logv) {
+  switch (logv) {
+    case 8: return sizeof(QueueSmem<8>);
+    case 9: return sizeof(QueueSmem<9>);
+    default: return sizeof(QueueSmem<10>);
+  }
+}
+
+cudaError_t queue_occupancy(int logv, int* blocks_per_sm) {
+  switch (logv) {
+    case 8:
+      if (cudaError_t e = set_queue_attr<8>()) return e;
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_queue<8>, kBlock, sizeof(QueueSmem<8>));
+    case 9:
+      if (cudaError_t e = set_queue_attr<9>()) return e;
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_queue<9>, kBlock, sizeof(QueueSmem<9>));
+    default:
+      if (cudaError_t e = set_queue_attr<10>()) return e;
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_queue<10>, kBlock,
+                                                           sizeof(QueueSmem<10>));
+  }
+}
+
+cudaError_t launch_queue(int logv, const SortCtx& c, uint32_t grid, uint32_t R, cudaStream_t st,
+                         const LaunchHook& hook) {
+  switch (logv) {
+    case 8:
+      if (cudaError_t e = set_queue_attr<8>()) return e;
+      hook.run("queue", [&] { k_queue<8><<<grid, kBlock, sizeof(QueueSmem<8>), st>>>(c, R); });
+      break;
+    case 9:
+      if (cudaError_t e = set_queue_attr<9>()) return e;
+      hook.run("queue", [&] { k_queue<9><<<grid, kBlock, sizeof(QueueSmem<9>), st>>>(c, R); });
+      break;
+    default:
+      if (cudaError_t e = set_queue_attr<10>()) return e;
+      hook.run("queue", [&] { k_queue<10><<<grid, kBlock, sizeof(QueueSmem<10>), st>>>(c, R); });
+      break;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace ss

@@ -1,0 +1,383 @@
+// Small subsets, initial set-up and the final LCP fix-up.
+//
+// A subset of at most small_cutoff strings with a common prefix of `depth`
+// characters is finished by one block (33..cutoff strings) or one warp (2..32)
+// without further distribution steps: its records are sorted by
+// (segment, cache, index) in shared memory or registers; runs of equal caches
+// without a terminator are refined by reloading their caches 8 characters
+// deeper and sorting again (the recursion of the equality buckets of
+// Section 4.2.2, done in place).  This replaces the paper's sequential base
+// cases (caching multikey quicksort and insertion sort, Section 4.2.8) with
+// sorting networks that suit a warp or a block.  LCPs between neighbours are
+// computed from the caches as they are separated (Section 4.2.3, "LCP via
+// XOR").
+#include "ss_kernels.h"
+#include "ss_step.cuh"
+
+namespace ss {
+
+namespace {
+
+__device__ __forceinline__ uint32_t find_set(const SortCtx& c, uint32_t r) {
+  uint32_t lo = 0, hi = c.num_sets - 1;  // last set with base <= r
+  while (lo < hi) {
+    uint32_t mid = (lo + hi + 1) >> 1;
+    if (c.sets[mid].base <= r) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Records of every set at depth 0, in index order (the stable starting point).
+__global__ void __launch_bounds__(kBlock) k_init(SortCtx c) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < c.total; r += stride) {
+    const uint32_t s = c.num_sets == 1 ? 0 : find_set(c, r);
+    const SetDesc sd = c.sets[s];
+    const uint32_t i = r - sd.base;
+    c.idx[0][r] = i;
+    c.key[0][r] = load_cache(sd.chars, sd.offsets[i], 0, sd.cap);
+  }
+}
+
+// One root task per set.
+__global__ void k_roots(SortCtx c) {
+  const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= c.num_sets) return;
+  const SetDesc sd = c.sets[s];
+  if (sd.n == 0) return;
+  if (sd.lcp) sd.lcp[0] = 0;
+  if (sd.n == 1) { sd.perm[0] = 0; return; }
+  route_task(c, Task{sd.base, sd.n, 0, make_meta(s, 0)}, c.big_cur);
+}
+
+// ---- warp-level refinement ----------------------------------------------------
+
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+__device__ __forceinline__ bool less3(uint32_t sa, uint64_t ka, uint32_t ia, uint32_t sb, uint64_t kb,
+                                      uint32_t ib) {
+  return sa < sb || (sa == sb && (ka < kb || (ka == kb && ia < ib)));
+}
+
+// Bitonic sort of one element per lane by (seg, key, idx), ascending in lane order.
+__device__ __forceinline__ void warp_sort(uint32_t& seg, uint64_t& key, uint32_t& idx, uint64_t& off,
+                                          uint32_t& open) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (uint32_t k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      const uint32_t os = __shfl_xor_sync(kFull, seg, j);
+      const uint64_t ok = __shfl_xor_sync(kFull, key, j);
+      const uint32_t oi = __shfl_xor_sync(kFull, idx, j);
+      const uint64_t oo = __shfl_xor_sync(kFull, off, j);
+      const uint32_t op = __shfl_xor_sync(kFull, open, j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool take = (lower == up) ? less3(os, ok, oi, seg, key, idx) : less3(seg, key, idx, os, ok, oi);
+      if (take) { seg = os; key = ok; idx = oi; off = oo; open = op; }
+    }
+  }
+}
+
+// Sorts n (2..32) strings held one per lane (lanes >= n are ignored) that share
+// their first d0 characters and arrive in ascending index order; key is the
+// cache at depth d0, off the string's offset.  Writes lcp_out[j] for
+// 1 <= j < n (if lcp_out is not null) and returns the index at sorted
+// position lane.
+__device__ uint32_t warp_refine(uint64_t key, uint32_t idx, uint64_t off, uint32_t n, uint32_t d0,
+                                uint32_t cap, const uint8_t* chars, uint32_t* lcp_out, uint32_t* status) {
+  const uint32_t lane = lane_id();
+  const bool active = lane < n;
+  uint32_t seg = active ? 0u : 0xFFFFFFFFu;
+  uint32_t open = active ? 1u : 0u;
+  if (!active) { key = ~0ull; idx = 0xFFFFFFFFu; off = 0; }
+  uint32_t depth = d0;
+  const uint32_t upto = (lane == 31) ? kFull : ((2u << lane) - 1);
+  while (true) {
+    warp_sort(seg, key, idx, off, open);
+    const uint32_t ps = __shfl_up_sync(kFull, seg, 1);
+    const uint64_t pk = __shfl_up_sync(kFull, key, 1);
+    const bool start = lane == 0 || seg != ps || key != pk;
+    if (active && open && lane > 0 && seg == ps && key != pk && lcp_out) lcp_out[lane] = depth + lcp8(pk, key);
+    const uint32_t starts = __ballot_sync(kFull, active && start);
+    const uint32_t my_start = 31 - __clz(starts & upto);
+    const uint32_t above = starts & ~upto;
+    const uint32_t next = above ? (uint32_t)(__ffs(above) - 1) : n;
+    const uint32_t size = next - my_start;
+    if (active && open) {
+      if (size == 1) {
+        open = 0;
+      } else if (has_nul(key)) {
+        open = 0;
+        if (lane != my_start && lcp_out) lcp_out[lane] = depth + nnz_prefix(key);
+      }
+    }
+    if (active) seg = my_start;
+    if (!__any_sync(kFull, active && open)) break;
+    if (depth + 8 > kMaxDepth) {
+      if (lane == 0) latch_status(status, kStTooDeep);
+      break;
+    }
+    depth += 8;
+    if (active && open) key = load_cache(chars, off, depth, cap);
+  }
+  return idx;
+}
+
+__global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
+  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+  const uint32_t count = min(*c.small_warp.count, c.small_warp.cap);
+  const uint32_t lane = lane_id();
+  for (uint32_t ti = warp; ti < count; ti += nwarps) {
+    const Task t = c.small_warp.items[ti];
+    const SetDesc sd = c.sets[task_set(t)];
+    const uint32_t par = task_par(t);
+    uint64_t key = 0, off = 0;
+    uint32_t id = 0;
+    if (lane < t.len) {
+      key = c.key[par][t.begin + lane];
+      id = c.idx[par][t.begin + lane];
+      off = sd.offsets[id];
+    }
+    uint32_t* lo = sd.lcp ? sd.lcp + (t.begin - sd.base) : nullptr;
+    const uint32_t fin = warp_refine(key, id, off, t.len, t.depth, sd.cap, sd.chars, lo, c.status);
+    if (lane < t.len) sd.perm[t.begin - sd.base + lane] = fin;
+  }
+}
+
+// ---- block-level refinement -------------------------------------------------------
+
+struct CtaSmem {  // carved from dynamic shared memory, P = pmax elements
+  uint64_t* key;
+  uint64_t* off;
+  uint32_t* idx;
+  uint32_t* aux;    // segment sizes
+  uint16_t* seg;
+  uint16_t* nseg;
+  uint16_t* list;   // open segment starts (at most pmax / 2: each has >= 2 members)
+  uint8_t* open;
+};
+
+__device__ __forceinline__ bool lessc(const CtaSmem& m, uint32_t a, uint32_t b) {
+  return less3(m.seg[a], m.key[a], m.idx[a], m.seg[b], m.key[b], m.idx[b]);
+}
+
+__device__ __forceinline__ void swapc(const CtaSmem& m, uint32_t a, uint32_t b) {
+  uint64_t k = m.key[a]; m.key[a] = m.key[b]; m.key[b] = k;
+  uint64_t o = m.off[a]; m.off[a] = m.off[b]; m.off[b] = o;
+  uint32_t i = m.idx[a]; m.idx[a] = m.idx[b]; m.idx[b] = i;
+  uint16_t s = m.seg[a]; m.seg[a] = m.seg[b]; m.seg[b] = s;
+  uint8_t p = m.open[a]; m.open[a] = m.open[b]; m.open[b] = p;
+}
+
+__device__ void block_sort(const CtaSmem& m, uint32_t P) {
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < P / 2; i += kBlock) {
+        const uint32_t lo = 2 * i - (i & (j - 1));
+        const uint32_t hi = lo + j;
+        const bool up = (lo & k) == 0;
+        if (lessc(m, hi, lo) == up) swapc(m, lo, hi);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Inclusive max-scan of nseg[0..n) in place (n <= pmax).
+__device__ void block_max_scan(uint16_t* a, uint32_t n) {
+  __shared__ uint32_t wmax[kWarps];
+  const uint32_t per = (n + kBlock - 1) / kBlock;
+  const uint32_t b0 = threadIdx.x * per;
+  uint32_t m = 0;
+  for (uint32_t j = 0; j < per && b0 + j < n; ++j) m = max(m, (uint32_t)a[b0 + j]);
+  uint32_t inc = m;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(kFull, inc, o);
+    if (lane_id() >= (uint32_t)o) inc = max(inc, t);
+  }
+  const uint32_t w = threadIdx.x >> 5;
+  if (lane_id() == 31) wmax[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t v = lane_id() < kWarps ? wmax[lane_id()] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t t = __shfl_up_sync(kFull, v, o);
+      if (lane_id() >= (uint32_t)o) v = max(v, t);
+    }
+    if (lane_id() < kWarps) wmax[lane_id()] = v;
+  }
+  __syncthreads();
+  uint32_t excl = __shfl_up_sync(kFull, inc, 1);
+  if (lane_id() == 0) excl = 0;
+  uint32_t run = max(excl, w ? wmax[w - 1] : 0u);
+  for (uint32_t j = 0; j < per && b0 + j < n; ++j) {
+    run = max(run, (uint32_t)a[b0 + j]);
+    a[b0 + j] = (uint16_t)run;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  CtaSmem m;
+  m.key = reinterpret_cast<uint64_t*>(smem);
+  m.off = m.key + pmax;
+  m.idx = reinterpret_cast<uint32_t*>(m.off + pmax);
+  m.aux = m.idx + pmax;
+  m.seg = reinterpret_cast<uint16_t*>(m.aux + pmax);
+  m.nseg = m.seg + pmax;
+  m.list = m.nseg + pmax;
+  m.open = reinterpret_cast<uint8_t*>(m.list + pmax / 2);
+  __shared__ uint32_t s_max_open, s_nlist;
+  const uint32_t count = min(*c.small_cta.count, c.small_cta.cap);
+  for (uint32_t ti = blockIdx.x; ti < count; ti += gridDim.x) {
+    const Task t = c.small_cta.items[ti];
+    const SetDesc sd = c.sets[task_set(t)];
+    const uint32_t par = task_par(t);
+    const uint32_t n = t.len;
+    uint32_t P = 64;
+    while (P < n) P <<= 1;
+    for (uint32_t j = threadIdx.x; j < P; j += kBlock) {
+      if (j < n) {
+        const uint32_t id = c.idx[par][t.begin + j];
+        m.key[j] = c.key[par][t.begin + j];
+        m.idx[j] = id;
+        m.off[j] = sd.offsets[id];
+        m.seg[j] = 0;
+        m.open[j] = 1;
+      } else {
+        m.key[j] = ~0ull;
+        m.idx[j] = 0xFFFFFFFFu;
+        m.off[j] = 0;
+        m.seg[j] = 0xFFFFu;
+        m.open[j] = 0;
+      }
+    }
+    uint32_t* lcp = sd.lcp ? sd.lcp + (t.begin - sd.base) : nullptr;
+    uint32_t depth = t.depth;
+    __syncthreads();
+    bool handoff = false;
+    while (true) {
+      block_sort(m, P);
+      if (threadIdx.x == 0) { s_max_open = 0; s_nlist = 0; }
+      for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+        const bool st = j == 0 || m.seg[j] != m.seg[j - 1] || m.key[j] != m.key[j - 1];
+        if (lcp && m.open[j] && j > 0 && m.seg[j] == m.seg[j - 1] && m.key[j] != m.key[j - 1])
+          lcp[j] = depth + lcp8(m.key[j - 1], m.key[j]);
+        m.nseg[j] = st ? (uint16_t)j : 0;
+        m.aux[j] = 0;
+      }
+      __syncthreads();
+      block_max_scan(m.nseg, n);
+      for (uint32_t j = threadIdx.x; j < n; j += kBlock) atomicAdd(&m.aux[m.nseg[j]], 1u);
+      __syncthreads();
+      for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+        const uint32_t s0 = m.nseg[j];
+        if (m.open[j]) {
+          const uint32_t size = m.aux[s0];
+          if (size == 1) {
+            m.open[j] = 0;
+          } else if (has_nul(m.key[j])) {
+            m.open[j] = 0;
+            if (lcp && j != s0) lcp[j] = depth + nnz_prefix(m.key[j]);
+          } else {
+            atomicMax(&s_max_open, size);
+            if (j == s0) {
+              const uint32_t slot = atomicAdd(&s_nlist, 1u);
+              m.list[slot] = (uint16_t)j;
+            }
+          }
+        }
+        m.seg[j] = (uint16_t)s0;
+      }
+      __syncthreads();
+      if (s_max_open == 0) break;
+      if (depth + 8 > kMaxDepth) {
+        if (threadIdx.x == 0) latch_status(c.status, kStTooDeep);
+        break;
+      }
+      if (s_max_open <= 32) { handoff = true; break; }
+      depth += 8;
+      for (uint32_t j = threadIdx.x; j < n; j += kBlock)
+        if (m.open[j]) m.key[j] = load_cache(sd.chars, m.off[j], depth, sd.cap);
+      __syncthreads();
+    }
+    if (handoff) {
+      const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+      const uint32_t nl = s_nlist;
+      for (uint32_t li = w; li < nl; li += kWarps) {
+        const uint32_t s0 = m.list[li];
+        const uint32_t size = m.aux[s0];
+        uint64_t key = 0, off = 0;
+        uint32_t id = 0;
+        if (lane < size) {
+          off = m.off[s0 + lane];
+          id = m.idx[s0 + lane];
+          key = load_cache(sd.chars, off, depth + 8, sd.cap);
+        }
+        const uint32_t fin = warp_refine(key, id, off, size, depth + 8, sd.cap, sd.chars,
+                                         lcp ? lcp + s0 : nullptr, c.status);
+        if (lane < size) m.idx[s0 + lane] = fin;
+      }
+      __syncthreads();
+    }
+    for (uint32_t j = threadIdx.x; j < n; j += kBlock) sd.perm[t.begin - sd.base + j] = m.idx[j];
+    __syncthreads();
+  }
+}
+
+// Resolves the boundary marks left by the distribution steps: out_lcp[j] =
+// mark | h means the strings at j-1 and j share exactly their first h
+// characters plus the common prefix of their caches at depth h.
+__global__ void __launch_bounds__(kBlock) k_lcp_fix(SortCtx c) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < c.total; r += stride) {
+    const uint32_t s = c.num_sets == 1 ? 0 : find_set(c, r);
+    const SetDesc sd = c.sets[s];
+    if (!sd.lcp) continue;
+    const uint32_t j = r - sd.base;
+    const uint32_t v = sd.lcp[j];
+    if (j == 0 || !(v & kLcpMark)) continue;
+    const uint32_t h = v & ~kLcpMark;
+    const uint64_t a = load_cache(sd.chars, sd.offsets[sd.perm[j - 1]], h, sd.cap);
+    const uint64_t b = load_cache(sd.chars, sd.offsets[sd.perm[j]], h, sd.cap);
+    sd.lcp[j] = h + lcp8(a, b);
+  }
+}
+
+}  // namespace
+
+size_t small_cta_smem(uint32_t pmax) { return (size_t)pmax * (8 + 8 + 4 + 4 + 2 + 2 + 1 + 1); }
+
+cudaError_t launch_init(const SortCtx& c, cudaStream_t st, const LaunchHook& hook) {
+  const uint32_t grid = max(1u, min((c.total + kBlock - 1) / kBlock, 152u * 16u));
+  hook.run("init", [&] { k_init<<<grid, kBlock, 0, st>>>(c); });
+  hook.run("init", [&] { k_roots<<<(c.num_sets + 127) / 128, 128, 0, st>>>(c); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, uint32_t grid_cta,
+                         cudaStream_t st, const LaunchHook& hook) {
+  static uint32_t attr_pmax = 0;
+  if (pmax > attr_pmax) {
+    cudaError_t e = cudaFuncSetAttribute(k_small_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)small_cta_smem(pmax));
+    if (e != cudaSuccess) return e;
+    attr_pmax = pmax;
+  }
+  hook.run("small_warp", [&] { k_small_warp<<<grid_warp, kBlock, 0, st>>>(c); });
+  hook.run("small_cta", [&] { k_small_cta<<<grid_cta, kBlock, small_cta_smem(pmax), st>>>(c, pmax); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lcp_fix(const SortCtx& c, uint32_t grid, cudaStream_t st, const LaunchHook& hook) {
+  hook.run("lcp_fix", [&] { k_lcp_fix<<<grid, kBlock, 0, st>>>(c); });
+  return cudaGetLastError();
+}
+
+}  // namespace ss

@@ -1,0 +1,237 @@
+// Building blocks of one Super Scalar String Sample Sort step (Algorithm 4.1),
+// written for a 256-thread block.  Used by the multi-block step kernels and by
+// the persistent single-block kernel.
+#pragma once
+
+#include "ss_internal.cuh"
+
+namespace ss {
+
+constexpr uint32_t kBlock = 256;
+constexpr uint32_t kWarps = kBlock / 32;
+constexpr uint32_t kMaxRounds = 32;                  // tile = 256 * rounds records
+constexpr uint32_t kMaxTile = kBlock * kMaxRounds;
+constexpr uint32_t kFin = 1u << 31;                  // bucket descriptor: finished
+constexpr uint32_t kNulEq = 1u << 30;                // ... all members equal strings
+constexpr uint32_t kLow30 = (1u << 30) - 1;
+
+// v = 2^LOGV - 1 splitters x_0..x_{v-1}, k = 2v + 1 buckets (Section 4.2.2).
+template <int LOGV>
+struct Geo {
+  static constexpr uint32_t V = (1u << LOGV) - 1;
+  static constexpr uint32_t K = 2 * V + 1;
+  static constexpr uint32_t KP = 2u << LOGV;        // K rounded up to a power of two
+  static constexpr uint32_t S = 2u << LOGV;         // sample size alpha * (v + 1), alpha = 2
+};
+
+// Splitters of one step.
+template <int LOGV>
+struct Splitters {
+  uint64_t tree[Geo<LOGV>::V + 1];  // t[1..v], level order (t[0] unused)
+  uint64_t x[Geo<LOGV>::V + 1];     // x_0..x_{v-1} sorted; x[v] unused
+  uint8_t hp[Geo<LOGV>::V + 1];     // h'_0..h'_v: lcp of neighbouring splitters
+};
+
+// Scratch of the splitter construction (may alias other shared memory).
+template <int LOGV>
+struct BuildScratch {
+  uint64_t sample[Geo<LOGV>::S];
+  uint16_t ra[Geo<LOGV>::V + 1];
+  uint16_t rb[Geo<LOGV>::V + 1];
+};
+
+// Block-wide bitonic sort of N (power of two) uint64 in shared memory, ascending.
+template <uint32_t N>
+__device__ void block_bitonic_u64(uint64_t* a) {
+  for (uint32_t k = 2; k <= N; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
+        uint32_t lo = 2 * i - (i & (j - 1));
+        uint32_t hi = lo + j;
+        bool up = (lo & k) == 0;
+        uint64_t A = a[lo], B = a[hi];
+        if ((A > B) == up) { a[lo] = B; a[hi] = A; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Lines 1-5 of Algorithm 4.1 for the len keys at `keys`: draw a sample of
+// alpha * (v + 1) keys at pseudo-random positions, sort it, select the
+// splitters with the recursive duplicate-skipping rule of Section 4.2.3
+// ("Sampling"): the middle sample of a range becomes the splitter, the ranges
+// left and right of the run of samples equal to it are split recursively.
+// Done level by level, the recursion directly yields the level-order tree t.
+// A node whose range is empty takes the sample just above its range (the
+// nearest splitter on the right among its ancestors), or all-ones past the
+// end, which keeps t a search tree.  Finally h'_i = lcp(x_{i-1}, x_i) with
+// h'_0 = h'_v = 0 (line 5).  Ends with __syncthreads().
+template <int LOGV>
+__device__ void build_splitters(const uint64_t* __restrict__ keys, uint32_t len, uint64_t hseed,
+                                Splitters<LOGV>& sp, BuildScratch<LOGV>& bs) {
+  using G = Geo<LOGV>;
+  for (uint32_t i = threadIdx.x; i < G::S; i += blockDim.x) {
+    uint64_t h = mix64(hseed + i);
+    uint32_t pos = (uint32_t)(((h >> 32) * (uint64_t)len) >> 32);
+    bs.sample[i] = keys[pos];
+  }
+  if (threadIdx.x == 0) { bs.ra[1] = 0; bs.rb[1] = (uint16_t)G::S; }
+  __syncthreads();
+  block_bitonic_u64<G::S>(bs.sample);
+  const uint64_t* s = bs.sample;
+  for (int l = 0; l < LOGV; ++l) {
+    const uint32_t first = 1u << l;
+    for (uint32_t q = threadIdx.x; q < first; q += blockDim.x) {
+      const uint32_t i = first + q;
+      const uint32_t a = bs.ra[i], b = bs.rb[i];
+      uint64_t val;
+      uint32_t la, lb, ra2, rb2;
+      if (a < b) {
+        const uint32_t m = (a + b) >> 1;
+        val = s[m];
+        uint32_t lo = a, hi = m;       // first index in [a, m] with s >= val
+        while (lo < hi) { uint32_t md = (lo + hi) >> 1; if (s[md] < val) lo = md + 1; else hi = md; }
+        const uint32_t left_end = lo;
+        lo = m + 1; hi = b;            // first index in [m+1, b) with s > val, else b
+        while (lo < hi) { uint32_t md = (lo + hi) >> 1; if (s[md] <= val) lo = md + 1; else hi = md; }
+        la = a; lb = left_end; ra2 = lo; rb2 = b;
+      } else {
+        val = (b < G::S) ? s[b] : ~0ull;
+        la = lb = ra2 = rb2 = b;
+      }
+      sp.tree[i] = val;
+      sp.x[(2 * q + 1) * (1u << (LOGV - 1 - l)) - 1] = val;
+      if (l + 1 < LOGV) {
+        bs.ra[2 * i] = (uint16_t)la; bs.rb[2 * i] = (uint16_t)lb;
+        bs.ra[2 * i + 1] = (uint16_t)ra2; bs.rb[2 * i + 1] = (uint16_t)rb2;
+      }
+    }
+    __syncthreads();
+  }
+  for (uint32_t r = threadIdx.x; r <= G::V; r += blockDim.x)
+    sp.hp[r] = (r == 0 || r == G::V) ? 0 : (uint8_t)lcp8(sp.x[r - 1], sp.x[r]);
+  if (threadIdx.x == 0) sp.tree[0] = 0;
+  __syncthreads();
+}
+
+// Lines 7-11 of Algorithm 4.1: branch-free descent of the level-order tree,
+// i := 2i + [c > t_i] (the reading of line 9 under which bucket b_{2r} holds
+// x_{r-1} < c < x_r), then the single equality test with x_r.
+template <int LOGV>
+__device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, const uint64_t* x) {
+  uint32_t i = 1;
+#pragma unroll
+  for (int l = 0; l < LOGV; ++l) i = 2 * i + (c > tree[i] ? 1u : 0u);
+  const uint32_t r = i - (1u << LOGV);
+  return 2 * r + ((r < Geo<LOGV>::V && x[r] == c) ? 1u : 0u);
+}
+
+// What happens to bucket b of a step at depth h (Output of Algorithm 4.1 and
+// Section 4.2.3): an even bucket b_{2r} continues at depth h + h'_r, an
+// equality bucket at h + 8, unless its splitter holds the terminator (then all
+// members are equal strings and the bucket is finished; their LCP is their
+// length); a single string is finished.
+template <int LOGV>
+__device__ __forceinline__ uint32_t bucket_desc(uint32_t b, uint32_t size, uint32_t depth,
+                                                const Splitters<LOGV>& sp) {
+  const uint32_t r = b >> 1;
+  if (b & 1) {
+    const uint64_t xr = sp.x[r];
+    if (has_nul(xr)) return kFin | kNulEq | (depth + nnz_prefix(xr));
+    if (size == 1) return kFin;
+    return depth + 8;
+  }
+  if (size == 1) return kFin;
+  return depth + sp.hp[r];
+}
+
+// Stable distribution of one tile of records (Algorithm 4.1 line 16 with the
+// per-processor bucket arrays of Theorem 4.4, one per warp).
+//   tb[0..tl)    bucket of each record of the tile (shared memory)
+//   base[b]      in: destination of the tile's first record of bucket b;
+//                out: base[b] + number of the tile's records in bucket b
+//   cntw         shared scratch, kWarps * KP uint32
+// Warp w owns records [w * 32R, (w + 1) * 32R) of the tile; inside a warp
+// ranks come from __match_any_sync, so equal buckets keep input order.
+// move(p, b, dest) is called once per record p < tl.  Ends with __syncthreads().
+template <int LOGV, typename Move>
+__device__ void tile_scatter(const uint16_t* tb, uint32_t tl, uint32_t R, uint32_t* base,
+                             uint32_t* cntw, Move&& move) {
+  using G = Geo<LOGV>;
+  const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+  for (uint32_t i = threadIdx.x; i < kWarps * G::KP; i += blockDim.x) cntw[i] = 0;
+  __syncthreads();
+  uint32_t* mine = cntw + w * G::KP;
+  const uint32_t p0 = w * 32 * R;
+  for (uint32_t r = 0; r < R; ++r) {
+    const uint32_t p = p0 + r * 32 + lane;
+    const bool valid = p < tl;
+    const uint32_t b = valid ? tb[p] : 0xFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
+    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) mine[b] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < G::K; b += blockDim.x) {
+    uint32_t run = base[b];
+#pragma unroll
+    for (uint32_t ww = 0; ww < kWarps; ++ww) {
+      const uint32_t c = cntw[ww * G::KP + b];
+      cntw[ww * G::KP + b] = run;
+      run += c;
+    }
+    base[b] = run;
+  }
+  __syncthreads();
+  const uint32_t lt = lanemask_lt();
+  for (uint32_t r = 0; r < R; ++r) {
+    const uint32_t p = p0 + r * 32 + lane;
+    const bool valid = p < tl;
+    const uint32_t b = valid ? tb[p] : 0xFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
+    uint32_t dest = 0;
+    if (valid) dest = mine[b] + __popc(peers & lt);
+    __syncwarp();
+    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) mine[b] += __popc(peers);
+    __syncwarp();
+    if (valid) move(p, b, dest);
+  }
+  __syncthreads();
+}
+
+// Moves one record to its bucket (the body of line 16): a finished record
+// writes its final index (and, inside a bucket of equal strings, its LCP);
+// an open one is copied to the other buffer with its cache reloaded at the
+// bucket's new depth (fused character gather).
+__device__ __forceinline__ void move_record(const SortCtx& c, const SetDesc& sd, uint32_t par,
+                                            uint32_t src, uint32_t dest, uint32_t depth,
+                                            uint32_t desc, uint32_t bucket_first) {
+  const uint32_t id = c.idx[par][src];
+  if (desc & kFin) {
+    sd.perm[dest - sd.base] = id;
+    if (sd.lcp && (desc & kNulEq) && dest != bucket_first) sd.lcp[dest - sd.base] = desc & kLow30;
+    return;
+  }
+  const uint32_t nd = desc & kLow30;
+  uint64_t key = c.key[par][src];
+  if (nd != depth) key = load_cache(sd.chars, sd.offsets[id], nd, sd.cap);
+  c.key[par ^ 1][dest] = key;
+  c.idx[par ^ 1][dest] = id;
+}
+
+// Emits the outcome of one non-empty bucket: its boundary LCP mark (resolved at
+// the end, Section 4.2.8 "LCP Calculation": the LCP with the previous bucket is
+// depth + lcp of the two strings' caches at this depth) and, if it is not
+// finished, a new task.
+__device__ __forceinline__ void emit_bucket(const SortCtx& c, const SetDesc& sd, const Task& t,
+                                            uint32_t start, uint32_t size, uint32_t desc,
+                                            uint32_t next_big) {
+  if (start > 0 && sd.lcp) sd.lcp[t.begin + start - sd.base] = kLcpMark | t.depth;
+  if (!(desc & kFin)) {
+    Task ch{t.begin + start, size, desc & kLow30, make_meta(task_set(t), task_par(t) ^ 1)};
+    route_task(c, ch, next_big);
+  }
+}
+
+}  // namespace ss

@@ -1,0 +1,83 @@
+"""The C-ABI library: it builds for sm_103a, loads, exports every function
+include/ss_sort.h declares, and rejects bad arguments before touching a GPU."""
+import ctypes
+import re
+
+import pytest
+
+import paper_1808_00963_gb300 as ss
+
+
+@pytest.fixture(scope="module")
+def lib():
+    ss.build()
+    return ss.load()
+
+
+def declared_functions():
+    text = open(ss.HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w\s\*]*?\b(ss_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert lib.ss_status_string(code)
+    assert lib.ss_status_string(0) == b"ok"
+
+
+def _has_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def test_host_side_argument_checks(lib):
+    o = ss.make_options()
+    dummy = ctypes.c_void_p(16)
+    # n = 0 is a no-op, n >= 2^32 is too large, NULL inputs are invalid
+    assert lib.ss_sort_ex(None, None, 0, None, None, ctypes.byref(o), None) == 0
+    assert lib.ss_sort_ex(dummy, dummy, 1 << 32, dummy, None, ctypes.byref(o), None) == 4
+    assert lib.ss_sort_ex(None, dummy, 5, dummy, None, ctypes.byref(o), None) == 1
+    assert lib.ss_sort_ex(dummy, dummy, 5, None, None, ctypes.byref(o), None) == 1
+    # option ranges
+    for bad in (dict(splitters_log2=7), dict(splitters_log2=11), dict(small_cutoff=32),
+                dict(small_cutoff=8192), dict(tile_rounds=64), dict(flags=1),
+                dict(small_cutoff=1024, big_threshold=512)):
+        ob = ss.make_options(**bad)
+        assert lib.ss_sort_ex(dummy, dummy, 5, dummy, None, ctypes.byref(ob), None) == 1, bad
+        assert lib.ss_workspace_size(1000, ctypes.byref(ob)) == 0
+    # misaligned caller workspace
+    ob = ss.make_options(workspace=ctypes.c_void_p(4096 + 8), workspace_bytes=1 << 20)
+    assert lib.ss_sort_ex(dummy, dummy, 5, dummy, None, ctypes.byref(ob), None) == 1
+    if not _has_gpu():
+        assert lib.ss_sort_ex(dummy, dummy, 5, dummy, None, ctypes.byref(o), None) == 7
+
+
+def test_workspace_size(lib):
+    o = ss.make_options()
+    small = lib.ss_workspace_size(1000, ctypes.byref(o))
+    big = lib.ss_workspace_size(10_000_000, ctypes.byref(o))
+    assert 0 < small < big
+    # records (2 x 12 B) + bucket array, plus task lists: tens of bytes per string
+    assert 26 * 10_000_000 < big < 80 * 10_000_000
+    sets = (ss.SetDesc * 2)()
+    sets[0].n, sets[1].n = 500, 700
+    sets[0].chars = sets[0].offsets = sets[0].out_perm = 64
+    sets[1].chars = sets[1].offsets = sets[1].out_perm = 64
+    assert lib.ss_batch_workspace_size(sets, 2, ctypes.byref(o)) > 0
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    with pytest.raises(RuntimeError):
+        ss.load(str(tmp_path / "nope.so"))
