@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Benchmark of the GPU string sample sort (sorted order + LCP array).
+
+Default workload (one GPU): the plain sort of 20 M synthetic URL-like strings
+(~59 B mean, Zipf hosts, 1.19 GB of characters), inputs resident in HBM.  One
+step = one complete sort through the C-ABI (ss_sort_ex), producing the
+permutation and the LCP array.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--config c1|c2|c3|c4]
+
+--impl reference times the CPU oracle (single thread) on a bounded sample of
+the same workload.  Under torchrun (N > 1) every rank sorts its own copy of
+the workload (independent replicas, weak scaling): the sort has no exchange
+step, so ranks share nothing but the timing barrier.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import gen  # noqa: E402
+
+METRIC = "strings/s & D-bytes/s vs HBM roofline; batched/served vs plain p99 + throughput"
+CPU_SAMPLE = 2_000_000
+
+
+# ---- distributed plumbing ------------------------------------------------------------------
+
+def dist_init():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- clocks during the timed region ---------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ---- workloads ----------------------------------------------------------------------------------
+
+def workload(name: str):
+    if name == "c1":
+        return gen.config1(), "plain sort, 100k random strings (length 8-32, a-z)"
+    if name == "c2":
+        return gen.config2(), "plain sort, 20M URL-like strings (~59 B mean, Zipf(1.1) over 2000 hosts)"
+    if name == "c3":
+        return gen.config3(), "plain sort, all 4M suffixes of a DNA-like text, capped at 500 B"
+    raise ValueError(name)
+
+
+def d_and_l(lcp: np.ndarray):
+    """D and L from an LCP array: d_i = max(h_i, h_{i+1}) + 1 with h_0 = h_n = 0."""
+    h = lcp.astype(np.int64)
+    if h.size == 0:
+        return 0, 0
+    h[0] = 0
+    nxt = np.append(h[1:], 0)
+    return int(np.maximum(h, nxt).sum() + h.size), int(h[1:].sum())
+
+
+def source_hash():
+    d = os.path.join(ROOT, "paper_1808_00963_gb300", "csrc")
+    hsh = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            hsh.update(f.encode() + fh.read())
+    return hsh.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def ncu_traffic(kernel: str, config: str):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, if it
+    was taken on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    e = t.get(config, {}).get(kernel)
+    if not e or e.get("source_hash") != source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---- reference arm: the CPU oracle ----------------------------------------------------------
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    s, desc = workload(args.config)
+    sample = min(CPU_SAMPLE if args.config == "c2" else s.n, s.n)
+    offs = np.ascontiguousarray(s.offsets[:sample])
+    oracle.load()
+    for _ in range(args.warmup):
+        oracle.sort(s.chars, offs, s.max_len)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sort(s.chars, offs, s.max_len)
+    dt = time.perf_counter() - t0
+    v = sample * args.steps / dt
+    cores = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "strings/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": desc, "n": s.n, "sample_strings": sample, "parallelism": "cpu, 1 thread"},
+        "cpu_baseline": {"value": v, "unit": "strings/s", "cores": cores, "kind": "oracle",
+                         "sample": f"first {sample} of the {s.n} strings (generated i.i.d.), same buffer"},
+        "e2e": {"value": v, "unit": "strings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(s, config):
+    import oracle
+    sample = min(CPU_SAMPLE if config == "c2" else s.n, s.n)
+    offs = np.ascontiguousarray(s.offsets[:sample])
+    oracle.load()
+    times = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        oracle.sort(s.chars, offs, s.max_len)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return {"value": sample / t, "unit": "strings/s", "cores": 1, "kind": "oracle",
+            "sample": (f"first {sample} of the {s.n} strings (generated i.i.d.), median of 3 runs, "
+                       f"single thread of {os.cpu_count()} host cores")}
+
+
+# ---- our arm --------------------------------------------------------------------------------------
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    ss.load()
+    s, desc = workload(args.config)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    chars = torch.from_numpy(s.chars).to(dev)
+    offsets = torch.from_numpy(s.offsets.view(np.int64)).to(dev)
+    n = s.n
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    wsb = ss.workspace_size(n, s.max_len)
+    work = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    opts = dict(workspace=work.data_ptr(), workspace_bytes=wsb)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ss.sort(chars, offsets, max_len=s.max_len, out=(perm, lcp), **opts)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    D, L = d_and_l(lcp.cpu().numpy().view(np.uint32))
+
+    ss.reset_kernel_stats()
+    ss.set_profiling(True)
+    sampler = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = ss.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = ss.launch_count() - launches0
+    barrier(ws)
+    clocks = sampler.stop()
+    ss.set_profiling(False)
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms, ws)
+    stats = ss.kernel_stats()
+    secs = ms / 1e3
+    value = ws * n * args.steps / secs
+    d_rate = ws * D * args.steps / secs
+
+    # roofline of the dominant kernel (largest share of device time)
+    peak, peak_kind = measured_peaks()
+    dom = max(stats.items(), key=lambda kv: kv[1][1]) if stats else None
+    roof = None
+    if dom:
+        name, (nl, kms, kbytes) = dom
+        achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if kms > 0 else 0.0
+        path_bytes = D + 16 * n
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": ncu_traffic(name, args.config),
+                "alg_bytes_per_launch": kbytes / nl, "launches": nl, "ms_per_launch": kms / nl,
+                "path_alg_bytes_per_step": path_bytes,
+                "path_frac": (path_bytes / (ms / args.steps / 1e3)) / 1e9 / peak,
+                "kernel_share": {k: round(v[1] / sum(x[1] for x in stats.values()), 4) for k, v in stats.items()}}
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hchars = torch.from_numpy(s.chars).pin_memory()
+        hoffs = torch.from_numpy(s.offsets.view(np.int64)).pin_memory()
+        hperm = torch.empty(n, dtype=torch.int32).pin_memory()
+        hlcp = torch.empty(n, dtype=torch.int32).pin_memory()
+        ss.sort_host(hchars, hoffs, s.max_len, perm=hperm, lcp=hlcp)
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ss.sort_host(hchars, hoffs, s.max_len, perm=hperm, lcp=hlcp)
+        torch.cuda.synchronize()
+        et = max_over_ranks(time.perf_counter() - t0, ws)
+        e2e = {"value": ws * n * args.steps / et, "unit": "strings/s",
+               "h2d_bytes_per_step": int(s.N + 8 * n), "d2h_bytes_per_step": int(8 * n),
+               "ms_per_step": et / args.steps * 1e3}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(s, args.config)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "strings/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": desc, "n": n, "N": s.N, "D": D, "L": L, "max_len": s.max_len,
+                       "l2": f"inputs larger than L2 (characters {s.N / 1e9:.2f} GB, offsets {8 * n / 1e6:.0f} MB)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "per_step": "one sort: permutation + LCP array"},
+            "d_bytes_per_s": d_rate,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 4), "alg_bytes": v[2]} for k, v in stats.items()},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), rank)
+        return
+    ws, rank, local = dist_init()
+    run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

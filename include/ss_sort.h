@@ -64,7 +64,8 @@ typedef struct ss_options {
                                   single-block steps; 8..10 (default 9).        */
     uint32_t big_splitters_log2; /* d for the multi-block steps; 8..10 (default 10). */
     uint32_t tile_rounds;      /* multi-block tile = 256 * tile_rounds strings;
-                                  4..32 (default: chosen from n).               */
+                                  8..32 (default: chosen per step from the
+                                  number of strings in big subsets).            */
     uint32_t small_cutoff;     /* subsets of at most this many strings are
                                   finished in shared memory; 64..4096
                                   (default 2048).                               */
@@ -99,8 +100,10 @@ size_t ss_workspace_size(uint64_t n, const ss_options* opt);
 
 /* Same as ss_sort_ex, but chars / offsets / outputs are HOST buffers:
  * chars_len bytes of chars and n offsets are copied to the device, sorted,
- * and the results copied back, all inside the call.  The device buffers come
- * from a per-device cache that grows as needed and is kept until exit. */
+ * and the results copied back, all inside the call (pinned host buffers make
+ * the copies fastest).  The device buffers are stream-ordered allocations
+ * from the device's default memory pool, returned to the pool at the end of
+ * the call. */
 ss_status ss_sort_host(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets,
                        uint64_t n, uint32_t* out_perm, uint32_t* out_lcp,
                        const ss_options* opt, void* stream);
@@ -156,12 +159,15 @@ uint64_t ss_launch_count(void);
 
 /* Per-kernel device timing.  When enabled, the library records CUDA events
  * around each of its kernel launches on the launching stream and accumulates
- * the elapsed time per kernel class once the call has waited for its work.
- * ss_kernel_stats fills up to `cap` entries (name, launches, total ms) and
- * returns the number of kernel classes. */
+ * the elapsed time per kernel class once the call has waited for its work,
+ * together with the algorithmic bytes the kernels of that class moved (the
+ * bytes their task requires, counted on the device: each record read and
+ * written once, 8 bytes per character-window gather).  ss_kernel_stats fills
+ * up to `cap` entries (name, launches, total ms, algorithmic bytes; any output
+ * array may be NULL) and returns the number of kernel classes. */
 void ss_set_profiling(int enabled);
 uint32_t ss_kernel_stats(const char** names, uint64_t* launches, double* total_ms,
-                         uint32_t cap);
+                         uint64_t* alg_bytes, uint32_t cap);
 void ss_reset_kernel_stats(void);
 
 #ifdef __cplusplus

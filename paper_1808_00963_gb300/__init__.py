@@ -150,7 +150,7 @@ def load(path: str | None = None):
     lib.ss_set_profiling.argtypes = [i32]
     lib.ss_set_profiling.restype = None
     lib.ss_kernel_stats.argtypes = [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(u64),
-                                    ctypes.POINTER(ctypes.c_double), u32]
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), u32]
     lib.ss_kernel_stats.restype = u32
     lib.ss_reset_kernel_stats.argtypes = []
     lib.ss_reset_kernel_stats.restype = None
@@ -293,11 +293,13 @@ def reset_kernel_stats():
 
 
 def kernel_stats():
-    """{kernel class: (launches, total_ms)} recorded while profiling was on."""
+    """{kernel class: (launches, total_ms, algorithmic_bytes)} recorded while
+    profiling was on."""
     lib = load()
     cap = 64
     names = (ctypes.c_char_p * cap)()
     la = (ctypes.c_uint64 * cap)()
     ms = (ctypes.c_double * cap)()
-    k = lib.ss_kernel_stats(names, la, ms, cap)
-    return {names[i].decode(): (int(la[i]), float(ms[i])) for i in range(min(k, cap))}
+    by = (ctypes.c_uint64 * cap)()
+    k = lib.ss_kernel_stats(names, la, ms, by, cap)
+    return {names[i].decode(): (int(la[i]), float(ms[i]), int(by[i])) for i in range(min(k, cap))}

@@ -37,6 +37,8 @@ __global__ void __launch_bounds__(kBlock) k_big_sample(SortCtx c, const GenTask*
   const uint64_t* src = reinterpret_cast<const uint64_t*>(&sp);
   uint64_t* dst = reinterpret_cast<uint64_t*>(out + blockIdx.x);
   for (uint32_t i = threadIdx.x; i < sizeof(Splitters<LOGV>) / 8; i += blockDim.x) dst[i] = src[i];
+  // sample reads + splitter writes
+  account(c, kKBigSample, threadIdx.x == 0 ? Geo<LOGV>::S * 8ull + sizeof(Splitters<LOGV>) : 0ull);
 }
 
 template <int LOGV>
@@ -75,6 +77,10 @@ __global__ void __launch_bounds__(kBlock) k_big_classify(SortCtx c, const GenTas
   __syncthreads();
   uint32_t* cnt = counters + cnt_base(g) + tile;
   for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) cnt[(uint64_t)b * g.tiles] = hist[b];
+  // per record: cache 8 read + bucket index 2 written; per tile: K counters written
+  unsigned long long bytes = 10ull * ((tl > threadIdx.x) ? (tl - threadIdx.x + kBlock - 1) / kBlock : 0);
+  if (threadIdx.x == 0) bytes += 4ull * Gm::K;
+  account(c, kKBigClassify, bytes);
 }
 
 template <int LOGV>
@@ -88,7 +94,9 @@ __global__ void __launch_bounds__(kBlock) k_big_emit(SortCtx c, const GenTask* _
   const Splitters<LOGV>& sp = spl[blockIdx.x];
   const SetDesc sd = c.sets[task_set(g.t)];
   const uint32_t* sc = scanned + cnt_base(g);
+  unsigned long long bytes = 0;
   for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) {
+    bytes += 16;  // two bucket offsets read, start and descriptor written
     const uint32_t s = sc[(uint64_t)b * g.tiles] - g.rec_base;
     const uint32_t e = (b + 1 < Gm::K) ? sc[(uint64_t)(b + 1) * g.tiles] - g.rec_base : g.t.len;
     const uint32_t size = e - s;
@@ -100,6 +108,7 @@ __global__ void __launch_bounds__(kBlock) k_big_emit(SortCtx c, const GenTask* _
     }
     gdesc[(uint64_t)blockIdx.x * Gm::KP + b] = desc;
   }
+  account(c, kKBigEmit, bytes);
 }
 
 template <int LOGV>
@@ -136,9 +145,11 @@ __global__ void __launch_bounds__(kBlock) k_big_scatter(SortCtx c, const GenTask
   __syncthreads();
   const uint32_t src0 = g.t.begin + t0;
   const uint32_t depth = g.t.depth;
+  unsigned long long bytes = threadIdx.x == 0 ? 12ull * Gm::K : 0ull;  // per-bucket tile offsets
   tile_scatter<LOGV>(tb, tl, R, base, cntw, [&](uint32_t p, uint32_t b, uint32_t dest) {
-    move_record(c, sd, par, src0 + p, dest, depth, desc[b], bfirst[b]);
+    bytes += move_record(c, sd, par, src0 + p, dest, depth, desc[b], bfirst[b]);
   });
+  account(c, kKBigScatter, bytes);
 }
 
 // ---- exclusive prefix sum over uint32 (three phases) ----------------------------
@@ -175,7 +186,7 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& excl) 
 }
 
 __global__ void __launch_bounds__(kBlock) k_scan_reduce(const uint32_t* __restrict__ a, uint64_t n,
-                                                        uint32_t* __restrict__ part) {
+                                                        uint32_t* __restrict__ part, SortCtx c) {
   const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk;
   uint32_t s = 0;
   for (uint32_t i = threadIdx.x; i < kScanChunk; i += kBlock) {
@@ -185,6 +196,8 @@ __global__ void __launch_bounds__(kBlock) k_scan_reduce(const uint32_t* __restri
   uint32_t ex;
   const uint32_t total = block_excl_scan(s, ex);
   if (threadIdx.x == 0) part[blockIdx.x] = total;
+  const uint64_t left = n > b0 ? n - b0 : 0;
+  account(c, kKScan, threadIdx.x == 0 ? 4ull * (left < kScanChunk ? left : kScanChunk) : 0ull);
 }
 
 __global__ void __launch_bounds__(kBlock) k_scan_partials(uint32_t* __restrict__ part, uint32_t m) {
@@ -200,7 +213,7 @@ __global__ void __launch_bounds__(kBlock) k_scan_partials(uint32_t* __restrict__
 }
 
 __global__ void __launch_bounds__(kBlock) k_scan_down(uint32_t* __restrict__ a, uint64_t n,
-                                                      const uint32_t* __restrict__ part) {
+                                                      const uint32_t* __restrict__ part, SortCtx c) {
   const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
   uint32_t v[kScanItems];
   uint32_t s = 0;
@@ -219,6 +232,8 @@ __global__ void __launch_bounds__(kBlock) k_scan_down(uint32_t* __restrict__ a, 
     if (k < n) a[k] = run;
     run += v[j];
   }
+  const uint64_t left = n > b0 ? n - b0 : 0;
+  account(c, kKScan, 8ull * (left < kScanItems ? left : kScanItems));
 }
 
 }  // namespace
@@ -252,9 +267,9 @@ static cudaError_t launch_big_step_t(const BigStepArgs& a, cudaStream_t st, cons
     k_big_classify<LOGV><<<a.tiles, kBlock, 0, st>>>(a.c, a.gt, a.G, spl, a.counters, a.R);
   });
   const uint32_t nb = (uint32_t)((a.ncounters + kScanChunk - 1) / kScanChunk);
-  hook.run("scan", [&] { k_scan_reduce<<<nb, kBlock, 0, st>>>(a.counters, a.ncounters, a.partials); });
+  hook.run("scan", [&] { k_scan_reduce<<<nb, kBlock, 0, st>>>(a.counters, a.ncounters, a.partials, a.c); });
   hook.run("scan", [&] { k_scan_partials<<<1, kBlock, 0, st>>>(a.partials, nb); });
-  hook.run("scan", [&] { k_scan_down<<<nb, kBlock, 0, st>>>(a.counters, a.ncounters, a.partials); });
+  hook.run("scan", [&] { k_scan_down<<<nb, kBlock, 0, st>>>(a.counters, a.ncounters, a.partials, a.c); });
   hook.run("big_emit", [&] {
     k_big_emit<LOGV><<<a.G, kBlock, 0, st>>>(a.c, a.gt, spl, a.counters, a.gstart, a.gdesc, a.next_big);
   });

@@ -33,6 +33,10 @@ static std::atomic<uint64_t> g_launches{0};
 static std::atomic<int> g_profiling{0};
 static std::mutex g_stats_mu;
 static std::map<std::string, std::pair<uint64_t, double>> g_stats;
+static std::map<std::string, unsigned long long> g_bytes;
+static const char* const kClassNames[kKClasses] = {"init",      "big_sample", "big_classify", "scan",
+                                                   "big_emit",  "big_scatter", "queue",       "small_warp",
+                                                   "small_cta", "lcp_fix"};
 
 struct PendingEvent {
   const char* name;
@@ -165,7 +169,8 @@ static uint32_t pmax_of(uint32_t cutoff) {
   return p;
 }
 
-constexpr uint32_t kCtrlWords = 64;
+constexpr uint32_t kCtrlWords = 64;                          // status and list counters
+constexpr size_t kCtrlBytes = kCtrlWords * 4 + kKClasses * 8;  // + algorithmic byte counters
 enum Ctrl : uint32_t { kCStatus = 0, kCBig0 = 1, kCBig1 = 2, kCHead = 3, kCTail = 4, kCPending = 5,
                        kCSmallW = 6, kCSmallC = 7 };
 
@@ -187,7 +192,7 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   const uint64_t KP = 2ull << o.logv_big;
   const uint64_t tiles_max = big ? M / (kBlock * 8) + L.cap_big : 0;
   L.ncounters_max = big ? KP * (tiles_max + L.cap_big) : 0;
-  L.ctrl = take(kCtrlWords * 4);
+  L.ctrl = take(kCtrlBytes);
   L.sets = take((size_t)num_sets * sizeof(SetDesc));
   L.key0 = take(M * 8);
   L.key1 = take(M * 8);
@@ -222,6 +227,7 @@ static SortCtx make_ctx(uint8_t* ws, const Layout& L, uint32_t num_sets, uint32_
   c.idx[1] = reinterpret_cast<uint32_t*>(ws + L.idx1);
   c.bucket_of = reinterpret_cast<uint16_t*>(ws + L.bucket_of);
   c.status = ctrl + kCStatus;
+  c.abytes = reinterpret_cast<unsigned long long*>(ctrl + kCtrlWords);
   c.big[0] = TaskList{reinterpret_cast<Task*>(ws + L.big0), ctrl + kCBig0, L.cap_big};
   c.big[1] = TaskList{reinterpret_cast<Task*>(ws + L.big1), ctrl + kCBig1, L.cap_big};
   c.mq = WorkQueue{reinterpret_cast<Task*>(ws + L.mq_items), reinterpret_cast<uint32_t*>(ws + L.mq_ready),
@@ -273,7 +279,7 @@ static thread_local Pinned t_down, t_up;
 static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o, const DevInfo& dev,
                           bool big, cudaStream_t st) {
   const LaunchHook hook{st};
-  SS_CUDA(cudaMemsetAsync(ws + L.ctrl, 0, kCtrlWords * 4, st));
+  SS_CUDA(cudaMemsetAsync(ws + L.ctrl, 0, kCtrlBytes, st));
   SS_CUDA(cudaMemsetAsync(ws + L.mq_ready, 0, (size_t)L.cap_mq * 4, st));
   SS_CUDA(launch_init(c, st, hook));
   if (big) {
@@ -347,11 +353,17 @@ static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o
 }
 
 static ss_status read_status(uint8_t* ws, const Layout& L, cudaStream_t st) {
-  if (t_down.reserve(64) != SS_OK) return SS_ERR_OOM;
+  if (t_down.reserve(kCtrlBytes) != SS_OK) return SS_ERR_OOM;
   uint32_t* h = static_cast<uint32_t*>(t_down.p);
-  SS_CUDA(cudaMemcpyAsync(h, ws + L.ctrl, 4, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaMemcpyAsync(h, ws + L.ctrl, kCtrlBytes, cudaMemcpyDeviceToHost, st));
   SS_CUDA(cudaStreamSynchronize(st));
   collect_profile();
+  if (g_profiling.load()) {
+    const unsigned long long* ab = reinterpret_cast<const unsigned long long*>(h + kCtrlWords);
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    for (uint32_t k = 0; k < kKClasses; ++k)
+      if (ab[k]) g_bytes[kClassNames[k]] += ab[k];
+  }
   return map_status(h[kCStatus]);
 }
 
@@ -442,9 +454,11 @@ void ss_set_profiling(int enabled) { g_profiling.store(enabled ? 1 : 0); }
 void ss_reset_kernel_stats(void) {
   std::lock_guard<std::mutex> lk(g_stats_mu);
   g_stats.clear();
+  g_bytes.clear();
 }
 
-uint32_t ss_kernel_stats(const char** names, uint64_t* launches, double* total_ms, uint32_t cap) {
+uint32_t ss_kernel_stats(const char** names, uint64_t* launches, double* total_ms, uint64_t* alg_bytes,
+                         uint32_t cap) {
   std::lock_guard<std::mutex> lk(g_stats_mu);
   uint32_t i = 0;
   for (auto& kv : g_stats) {
@@ -452,6 +466,10 @@ uint32_t ss_kernel_stats(const char** names, uint64_t* launches, double* total_m
       if (names) names[i] = kv.first.c_str();
       if (launches) launches[i] = kv.second.first;
       if (total_ms) total_ms[i] = kv.second.second;
+      if (alg_bytes) {
+        auto it = g_bytes.find(kv.first);
+        alg_bytes[i] = it == g_bytes.end() ? 0 : it->second;
+      }
     }
     ++i;
   }

@@ -79,6 +79,10 @@ struct WorkQueue {
   uint32_t epoch;
 };
 
+// Kernel classes for launch statistics and algorithmic-byte accounting.
+enum KernelClass : uint32_t { kKInit = 0, kKBigSample, kKBigClassify, kKScan, kKBigEmit, kKBigScatter, kKQueue,
+                              kKSmallWarp, kKSmallCta, kKLcpFix, kKClasses };
+
 // Everything a kernel needs about the sort in flight.
 struct SortCtx {
   const SetDesc* sets;
@@ -88,6 +92,7 @@ struct SortCtx {
   uint32_t* idx[2];
   uint16_t* bucket_of;     // bucket index of each record (array o of Algorithm 4.1)
   uint32_t* status;
+  unsigned long long* abytes;  // [kKClasses] algorithmic bytes moved, per kernel class
   TaskList big[2];         // multi-block tasks, ping-pong by step
   WorkQueue mq;            // tasks for the persistent single-block kernel
   TaskList small_warp;     // 2..32 records
@@ -210,6 +215,14 @@ __device__ __forceinline__ void route_task(const SortCtx& c, const Task& t, uint
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Adds a thread's algorithmic byte count to its kernel class (one atomic per
+// warp; every lane of the warp must call it).
+__device__ __forceinline__ void account(const SortCtx& c, uint32_t cls, unsigned long long bytes) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xFFFFFFFFu, bytes, o);
+  if ((threadIdx.x & 31u) == 0 && bytes) atomicAdd(c.abytes + cls, bytes);
+}
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
   asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));

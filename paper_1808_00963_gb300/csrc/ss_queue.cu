@@ -97,13 +97,17 @@ __device__ void block_excl_scan_smem(const uint32_t* in, uint32_t* out, uint32_t
 }
 
 // One S^5 step on task t by this block.
+// Returns this thread's share of the step's algorithmic bytes: the sample,
+// cache 8 read + bucket index 2 written per record while classifying, and the
+// bytes of each record's move.
 template <int LOGV>
-__device__ void queue_step(const SortCtx& c, const Task& t, QueueSmem<LOGV>& s, uint32_t R) {
+__device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueSmem<LOGV>& s, uint32_t R) {
   using Gm = Geo<LOGV>;
   const SetDesc sd = c.sets[task_set(t)];
   const uint32_t par = task_par(t);
   const uint64_t* keys = c.key[par] + t.begin;
   build_splitters<LOGV>(keys, t.len, mix64(c.seed ^ ((uint64_t)t.begin << 20) ^ t.depth), s.sp, s.u.bs);
+  unsigned long long bytes = threadIdx.x == 0 ? Gm::S * 8ull : 0ull;
 
   // lines 6-14: classify into the array o and count
   for (uint32_t b = threadIdx.x; b < Gm::KP; b += kBlock) s.hist[b] = 0;
@@ -116,6 +120,7 @@ __device__ void queue_step(const SortCtx& c, const Task& t, QueueSmem<LOGV>& s, 
     if (valid) {
       b = classify<LOGV>(keys[p], s.sp.tree, s.sp.x);
       bo[p] = (uint16_t)b;
+      bytes += 10;
     }
     const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
     if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s.hist[b], (uint32_t)__popc(peers));
@@ -139,7 +144,7 @@ __device__ void queue_step(const SortCtx& c, const Task& t, QueueSmem<LOGV>& s, 
     __syncthreads();
     const uint32_t src0 = t.begin + t0;
     tile_scatter<LOGV>(s.u.sc.tb, tl, R, s.hist, s.u.sc.cntw, [&](uint32_t p, uint32_t b, uint32_t dest) {
-      move_record(c, sd, par, src0 + p, dest, t.depth, s.desc[b], t.begin + s.bstart[b]);
+      bytes += move_record(c, sd, par, src0 + p, dest, t.depth, s.desc[b], t.begin + s.bstart[b]);
     });
   }
   __threadfence();
@@ -151,24 +156,27 @@ __device__ void queue_step(const SortCtx& c, const Task& t, QueueSmem<LOGV>& s, 
     const uint32_t size = s.bstart[b + 1] - start;
     if (size) emit_bucket(c, sd, t, start, size, s.desc[b], 0);
   }
+  return bytes;
 }
 
 template <int LOGV>
 __global__ void __launch_bounds__(kBlock) k_queue(SortCtx c, uint32_t R) {
   extern __shared__ __align__(16) uint8_t smem[];
   QueueSmem<LOGV>& s = *reinterpret_cast<QueueSmem<LOGV>*>(smem);
+  unsigned long long bytes = 0;
   while (true) {
     if (threadIdx.x == 0) s.got = claim_task(c.mq, &s.task, c.status) ? 1u : 0u;
     __syncthreads();
     if (!s.got) break;
     const Task t = s.task;
-    queue_step<LOGV>(c, t, s, R);
+    bytes += queue_step<LOGV>(c, t, s, R);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
       atomicSub(c.mq.pending, 1u);
     }
   }
+  account(c, kKQueue, bytes);
 }
 
 template <int LOGV>

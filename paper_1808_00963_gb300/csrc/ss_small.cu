@@ -30,13 +30,16 @@ __device__ __forceinline__ uint32_t find_set(const SortCtx& c, uint32_t r) {
 // Records of every set at depth 0, in index order (the stable starting point).
 __global__ void __launch_bounds__(kBlock) k_init(SortCtx c) {
   const uint32_t stride = gridDim.x * blockDim.x;
+  unsigned long long bytes = 0;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < c.total; r += stride) {
     const uint32_t s = c.num_sets == 1 ? 0 : find_set(c, r);
     const SetDesc sd = c.sets[s];
     const uint32_t i = r - sd.base;
     c.idx[0][r] = i;
     c.key[0][r] = load_cache(sd.chars, sd.offsets[i], 0, sd.cap);
+    bytes += 28;  // offset 8 + 8 characters read, cache 8 + index 4 written
   }
+  account(c, kKInit, bytes);
 }
 
 // One root task per set.
@@ -86,7 +89,8 @@ __device__ __forceinline__ void warp_sort(uint32_t& seg, uint64_t& key, uint32_t
 // 1 <= j < n (if lcp_out is not null) and returns the index at sorted
 // position lane.
 __device__ uint32_t warp_refine(uint64_t key, uint32_t idx, uint64_t off, uint32_t n, uint32_t d0,
-                                uint32_t cap, const uint8_t* chars, uint32_t* lcp_out, uint32_t* status) {
+                                uint32_t cap, const uint8_t* chars, uint32_t* lcp_out, uint32_t* status,
+                                unsigned long long& bytes) {
   const uint32_t lane = lane_id();
   const bool active = lane < n;
   uint32_t seg = active ? 0u : 0xFFFFFFFFu;
@@ -120,7 +124,10 @@ __device__ uint32_t warp_refine(uint64_t key, uint32_t idx, uint64_t off, uint32
       break;
     }
     depth += 8;
-    if (active && open) key = load_cache(chars, off, depth, cap);
+    if (active && open) {
+      key = load_cache(chars, off, depth, cap);
+      bytes += 8;
+    }
   }
   return idx;
 }
@@ -130,6 +137,7 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t count = min(*c.small_warp.count, c.small_warp.cap);
   const uint32_t lane = lane_id();
+  unsigned long long bytes = 0;
   for (uint32_t ti = warp; ti < count; ti += nwarps) {
     const Task t = c.small_warp.items[ti];
     const SetDesc sd = c.sets[task_set(t)];
@@ -142,9 +150,13 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
       off = sd.offsets[id];
     }
     uint32_t* lo = sd.lcp ? sd.lcp + (t.begin - sd.base) : nullptr;
-    const uint32_t fin = warp_refine(key, id, off, t.len, t.depth, sd.cap, sd.chars, lo, c.status);
-    if (lane < t.len) sd.perm[t.begin - sd.base + lane] = fin;
+    const uint32_t fin = warp_refine(key, id, off, t.len, t.depth, sd.cap, sd.chars, lo, c.status, bytes);
+    if (lane < t.len) {
+      sd.perm[t.begin - sd.base + lane] = fin;
+      bytes += sd.lcp ? 28 : 24;  // cache 8 + index 4 + offset 8 read; perm 4 (+ lcp 4) written
+    }
   }
+  account(c, kKSmallWarp, bytes);
 }
 
 // ---- block-level refinement -------------------------------------------------------
@@ -234,6 +246,7 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
   m.list = m.nseg + pmax;
   m.open = reinterpret_cast<uint8_t*>(m.list + pmax / 2);
   __shared__ uint32_t s_max_open, s_nlist;
+  unsigned long long bytes = 0;
   const uint32_t count = min(*c.small_cta.count, c.small_cta.cap);
   for (uint32_t ti = blockIdx.x; ti < count; ti += gridDim.x) {
     const Task t = c.small_cta.items[ti];
@@ -304,7 +317,10 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
       if (s_max_open <= 32) { handoff = true; break; }
       depth += 8;
       for (uint32_t j = threadIdx.x; j < n; j += kBlock)
-        if (m.open[j]) m.key[j] = load_cache(sd.chars, m.off[j], depth, sd.cap);
+        if (m.open[j]) {
+          m.key[j] = load_cache(sd.chars, m.off[j], depth, sd.cap);
+          bytes += 8;
+        }
       __syncthreads();
     }
     if (handoff) {
@@ -319,16 +335,21 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
           off = m.off[s0 + lane];
           id = m.idx[s0 + lane];
           key = load_cache(sd.chars, off, depth + 8, sd.cap);
+          bytes += 8;
         }
         const uint32_t fin = warp_refine(key, id, off, size, depth + 8, sd.cap, sd.chars,
-                                         lcp ? lcp + s0 : nullptr, c.status);
+                                         lcp ? lcp + s0 : nullptr, c.status, bytes);
         if (lane < size) m.idx[s0 + lane] = fin;
       }
       __syncthreads();
     }
-    for (uint32_t j = threadIdx.x; j < n; j += kBlock) sd.perm[t.begin - sd.base + j] = m.idx[j];
+    for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+      sd.perm[t.begin - sd.base + j] = m.idx[j];
+      bytes += sd.lcp ? 28 : 24;  // cache 8 + index 4 + offset 8 read; perm 4 (+ lcp 4) written
+    }
     __syncthreads();
   }
+  account(c, kKSmallCta, bytes);
 }
 
 // Resolves the boundary marks left by the distribution steps: out_lcp[j] =
@@ -336,18 +357,22 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
 // characters plus the common prefix of their caches at depth h.
 __global__ void __launch_bounds__(kBlock) k_lcp_fix(SortCtx c) {
   const uint32_t stride = gridDim.x * blockDim.x;
+  unsigned long long bytes = 0;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < c.total; r += stride) {
     const uint32_t s = c.num_sets == 1 ? 0 : find_set(c, r);
     const SetDesc sd = c.sets[s];
     if (!sd.lcp) continue;
     const uint32_t j = r - sd.base;
     const uint32_t v = sd.lcp[j];
+    bytes += 4;
     if (j == 0 || !(v & kLcpMark)) continue;
     const uint32_t h = v & ~kLcpMark;
     const uint64_t a = load_cache(sd.chars, sd.offsets[sd.perm[j - 1]], h, sd.cap);
     const uint64_t b = load_cache(sd.chars, sd.offsets[sd.perm[j]], h, sd.cap);
     sd.lcp[j] = h + lcp8(a, b);
+    bytes += 44;  // lcp 4 written; per string: perm 4 + offset 8 + 8 characters read
   }
+  account(c, kKLcpFix, bytes);
 }
 
 }  // namespace

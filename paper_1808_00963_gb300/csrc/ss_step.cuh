@@ -204,20 +204,31 @@ __device__ void tile_scatter(const uint16_t* tb, uint32_t tl, uint32_t R, uint32
 // writes its final index (and, inside a bucket of equal strings, its LCP);
 // an open one is copied to the other buffer with its cache reloaded at the
 // bucket's new depth (fused character gather).
-__device__ __forceinline__ void move_record(const SortCtx& c, const SetDesc& sd, uint32_t par,
-                                            uint32_t src, uint32_t dest, uint32_t depth,
-                                            uint32_t desc, uint32_t bucket_first) {
+// Returns the algorithmic bytes of the move: bucket index 2 + idx 4 read;
+// finished: perm 4 (+ lcp 4) written; open: key 8 read, key 8 + idx 4
+// written, plus offset 8 + 8 characters read when the cache is reloaded.
+__device__ __forceinline__ uint32_t move_record(const SortCtx& c, const SetDesc& sd, uint32_t par,
+                                                uint32_t src, uint32_t dest, uint32_t depth,
+                                                uint32_t desc, uint32_t bucket_first) {
   const uint32_t id = c.idx[par][src];
   if (desc & kFin) {
     sd.perm[dest - sd.base] = id;
-    if (sd.lcp && (desc & kNulEq) && dest != bucket_first) sd.lcp[dest - sd.base] = desc & kLow30;
-    return;
+    if (sd.lcp && (desc & kNulEq) && dest != bucket_first) {
+      sd.lcp[dest - sd.base] = desc & kLow30;
+      return 14;
+    }
+    return 10;
   }
   const uint32_t nd = desc & kLow30;
   uint64_t key = c.key[par][src];
-  if (nd != depth) key = load_cache(sd.chars, sd.offsets[id], nd, sd.cap);
+  uint32_t bytes = 26;
+  if (nd != depth) {
+    key = load_cache(sd.chars, sd.offsets[id], nd, sd.cap);
+    bytes += 16;
+  }
   c.key[par ^ 1][dest] = key;
   c.idx[par ^ 1][dest] = id;
+  return bytes;
 }
 
 // Emits the outcome of one non-empty bucket: its boundary LCP mark (resolved at
