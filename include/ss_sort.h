@@ -149,6 +149,34 @@ ss_status ss_batch_destroy(ss_batch* b);
 ss_status ss_sort_batch(const ss_set* sets, uint32_t num_sets, const ss_options* opt,
                         void* stream);
 
+/* ---- sorting without allocation -------------------------------------------------- */
+
+#define SS_NOALLOC_MAX_STRINGS 65536u
+#define SS_NOALLOC_SCRATCH_BYTES (4u << 20)
+
+/* The paper has no counterpart to this call; it exists for callers that may
+ * not allocate device memory while they run (a service that reserves all its
+ * GPU memory at start-up, code whose device memory belongs to another
+ * allocator, or a latency-critical path on which cudaMalloc / cudaFree, which
+ * can synchronise the whole device, are not allowed).
+ *
+ * Sorts n <= SS_NOALLOC_MAX_STRINGS strings exactly as ss_sort_ex does with
+ * default options and this max_len, but calls no cudaMalloc, cudaFree, stream-
+ * ordered or pinned allocation: its workspace is a fixed SS_NOALLOC_SCRATCH_BYTES
+ * array in the library's device data, which every GPU that loads the library
+ * holds until the process exits.  Inputs and outputs are the caller's device
+ * buffers, as for ss_sort.  Waits for the sort and returns its status.
+ *   - n > SS_NOALLOC_MAX_STRINGS: SS_ERR_TOO_LARGE, nothing is enqueued.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (the call clears what must start at zero).  Calls that overlap on the GPU
+ *     race with each other: issue them on one stream, or wait for one to end
+ *     before the next starts.
+ *   - Returns SS_ERR_INVALID while kernel profiling (ss_set_profiling) is on. */
+ss_status ss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, uint64_t n,
+                          uint32_t max_len, uint32_t* out_perm, uint32_t* out_lcp, void* stream);
+
 /* ---- diagnostics --------------------------------------------------------------- */
 
 /* Static description of a status code. */

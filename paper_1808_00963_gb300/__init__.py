@@ -154,6 +154,8 @@ def load(path: str | None = None):
     lib.ss_kernel_stats.restype = u32
     lib.ss_reset_kernel_stats.argtypes = []
     lib.ss_reset_kernel_stats.restype = None
+    lib.ss_sort_noalloc.argtypes = [vp, vp, u64, u32, vp, vp, vp]
+    lib.ss_sort_noalloc.restype = i32
     if path is None:
         _lib = lib
     return lib
@@ -229,6 +231,28 @@ def sort_host(chars, offsets, max_len: int = 0, with_lcp: bool = True, perm=None
                           ctypes.byref(o), _stream_ptr(stream))
     _check(rc, "ss_sort_host")
     return perm, (lcp if with_lcp else None)
+
+
+NOALLOC_MAX_STRINGS = 65536
+
+
+def sort_noalloc(chars, offsets, max_len: int = 0, out=None, stream=None):
+    """ss_sort_noalloc: sort up to 65536 strings without any allocation by the
+    library (its workspace is a fixed array in the library's device data).
+    ``out`` = (perm, lcp) preallocated int32 CUDA tensors (lcp may be None);
+    callers that may not allocate pass their own.  Returns (perm, lcp)."""
+    import torch
+    lib = load()
+    n = int(offsets.numel())
+    if out is None:
+        out = (torch.empty(n, dtype=torch.int32, device=offsets.device),
+               torch.empty(n, dtype=torch.int32, device=offsets.device))
+    perm, lcp = out
+    rc = lib.ss_sort_noalloc(ctypes.c_void_p(chars.data_ptr()), ctypes.c_void_p(offsets.data_ptr()), n, max_len,
+                             ctypes.c_void_p(perm.data_ptr()),
+                             ctypes.c_void_p(lcp.data_ptr()) if lcp is not None else None, _stream_ptr(stream))
+    _check(rc, "ss_sort_noalloc")
+    return perm, lcp
 
 
 def workspace_size(n: int, max_len: int = 0, **opts) -> int:

@@ -611,3 +611,76 @@ ss_status ss_sort_batch(const ss_set* sets, uint32_t num_sets, const ss_options*
 }
 
 }  // extern "C"
+
+// ---- sorting without any allocation ------------------------------------------------------
+//
+// For callers that cannot allocate device memory while they run: for example a
+// service that reserves all of its GPU memory at start-up and forbids later
+// allocation, code whose device memory belongs to another allocator, or a
+// latency-critical path where cudaMalloc / cudaFree (which may synchronise the
+// device) are not allowed.  The workspace of these sorts is a fixed array in
+// the library's device data, so the call itself allocates nothing.
+
+namespace ss {
+
+// Scratch of ss_sort_noalloc.  Every GPU that loads this library holds it
+// until the process exits.
+static __device__ __align__(256) uint8_t g_noalloc_scratch[SS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static uint8_t* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Writes the set descriptor into the scratch (no host staging buffer needed).
+__global__ void k_noalloc_set(SetDesc* dst, SetDesc v) { *dst = v; }
+
+// Device address of the scratch on the current device, looked up once per
+// device.  Host code only ever passes this address to kernels: the name
+// g_noalloc_scratch in host code is a host-side stand-in, not device memory.
+static ss_status noalloc_scratch(uint8_t** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SS_ERR_NO_DEVICE;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return SS_ERR_NO_DEVICE;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return SS_ERR_CUDA;
+    g_noalloc_ptr[dev] = static_cast<uint8_t*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return SS_OK;
+}
+
+}  // namespace ss
+
+extern "C" ss_status ss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, uint64_t n,
+                                     uint32_t max_len, uint32_t* out_perm, uint32_t* out_lcp, void* stream) {
+  using namespace ss;
+  if (n > SS_NOALLOC_MAX_STRINGS) return SS_ERR_TOO_LARGE;
+  if (n == 0) return SS_OK;
+  if (!chars || !offsets || !out_perm) return SS_ERR_INVALID;
+  if (g_profiling.load()) return SS_ERR_INVALID;  // profiling would create CUDA events
+  Opts o;
+  if (max_len) o.cap = max_len;
+  const Layout L = make_layout(n, 1, o, false);
+  if (L.total > SS_NOALLOC_SCRATCH_BYTES) return SS_ERR_TOO_LARGE;
+  DevInfo dev;
+  ss_status s = device_info(dev);
+  if (s != SS_OK) return s;
+  uint8_t* ws = nullptr;
+  if ((s = noalloc_scratch(&ws)) != SS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const SetDesc sd{chars, offsets, out_perm, out_lcp, (uint32_t)n, o.cap, 0, 0};
+  const LaunchHook hook{st};
+  hook.run("init", [&] { k_noalloc_set<<<1, 1, 0, st>>>(reinterpret_cast<SetDesc*>(ws + L.sets), sd); });
+  if (cudaGetLastError() != cudaSuccess) return SS_ERR_CUDA;
+  // run_sort clears the control words and the queue flags, the only scratch
+  // that must start at zero; everything else is written before it is read.
+  s = run_sort(ws, L, make_ctx(ws, L, 1, (uint32_t)n, o, false), o, dev, false, st);
+  if (s != SS_OK) return s;
+  uint32_t status = 0;
+  if (cudaMemcpyAsync(&status, ws + L.ctrl, sizeof(status), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return SS_ERR_CUDA;
+  return map_status(status);
+}
