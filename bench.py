@@ -129,9 +129,11 @@ class ClockSampler:
 
 # ---- workloads ----------------------------------------------------------------------------------
 
-def workload(name: str):
+def workload(name: str, n: int | None = None):
     if name == "c1":
         return gen.config1(), "plain sort, 100k random strings (length 8-32, a-z)"
+    if name == "c2" and n:  # reduced size, for profiler captures
+        return gen.config2(n), f"plain sort, {n} URL-like strings (reduced configuration 2, for profiling)"
     if name == "c2":
         return gen.config2(), "plain sort, 20M URL-like strings (~59 B mean, Zipf(1.1) over 2000 hosts)"
     if name == "c3":
@@ -236,7 +238,7 @@ def run_ours(args, ws, rank, local):
 
     import paper_1808_00963_gb300 as ss
     ss.load()
-    s, desc = workload(args.config)
+    s, desc = workload(args.config, args.n)
     dev = torch.device("cuda", torch.cuda.current_device())
     chars = torch.from_numpy(s.chars).to(dev)
     offsets = torch.from_numpy(s.offsets.view(np.int64)).to(dev)
@@ -349,6 +351,7 @@ def main():
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=None, help="reduced string count (c2 only; profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))

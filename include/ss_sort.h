@@ -61,16 +61,16 @@ typedef struct ss_options {
                                   ends after max_len bytes: a byte at position
                                   >= max_len reads as the terminator.           */
     uint32_t splitters_log2;   /* d with v = 2^d - 1 splitters per step in the
-                                  single-block steps; 8..10 (default 9).        */
-    uint32_t big_splitters_log2; /* d for the multi-block steps; 8..10 (default 10). */
+                                  single-block steps; 8..10 (default 8).        */
+    uint32_t big_splitters_log2; /* d for the multi-block steps; 8..10 (default 9). */
     uint32_t tile_rounds;      /* multi-block tile = 256 * tile_rounds strings;
                                   8..32 (default: chosen per step from the
                                   number of strings in big subsets).            */
     uint32_t small_cutoff;     /* subsets of at most this many strings are
                                   finished in shared memory; 64..4096
-                                  (default 2048).                               */
+                                  (default 1024).                               */
     uint32_t big_threshold;    /* subsets larger than this use multi-block
-                                  steps; >= small_cutoff (default 65536).        */
+                                  steps; >= small_cutoff (default 8192).         */
     uint32_t seed;             /* seed of the splitter sample (output does not
                                   depend on it).                                */
     uint32_t flags;            /* reserved, must be 0                           */

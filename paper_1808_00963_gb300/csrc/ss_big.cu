@@ -146,8 +146,9 @@ __global__ void __launch_bounds__(kBlock) k_big_scatter(SortCtx c, const GenTask
   const uint32_t src0 = g.t.begin + t0;
   const uint32_t depth = g.t.depth;
   unsigned long long bytes = threadIdx.x == 0 ? 12ull * Gm::K : 0ull;  // per-bucket tile offsets
-  tile_scatter<LOGV>(tb, tl, R, base, cntw, [&](uint32_t p, uint32_t b, uint32_t dest) {
-    bytes += move_record(c, sd, par, src0 + p, dest, depth, desc[b], bfirst[b]);
+  tile_scatter<LOGV>(tb, tl, R, base, cntw, [&](const uint32_t(&pp)[kMoveBatch], const uint32_t(&bb)[kMoveBatch],
+                                                const uint32_t(&dd)[kMoveBatch]) {
+    bytes += move_batch(c, sd, par, src0, depth, desc, [&](uint32_t b) { return bfirst[b]; }, pp, bb, dd);
   });
   account(c, kKBigScatter, bytes);
 }

@@ -124,11 +124,11 @@ static ss_status device_info(DevInfo& out) {
 
 struct Opts {
   uint32_t cap = kNoCap;
-  int logv = 9;        // single-block steps
-  int logv_big = 10;   // multi-block steps
+  int logv = 8;        // single-block steps
+  int logv_big = 9;    // multi-block steps
   uint32_t R = 0;      // 0 = choose per step
-  uint32_t cutoff = 2048;
-  uint32_t big_thr = 65536;
+  uint32_t cutoff = 1024;
+  uint32_t big_thr = 8192;
   uint32_t seed = 0x5EED;
   uint32_t mq_factor = 16;
 };

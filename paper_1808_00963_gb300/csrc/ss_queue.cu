@@ -143,9 +143,12 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
     for (uint32_t p = threadIdx.x; p < tl; p += kBlock) s.u.sc.tb[p] = bo[t0 + p];
     __syncthreads();
     const uint32_t src0 = t.begin + t0;
-    tile_scatter<LOGV>(s.u.sc.tb, tl, R, s.hist, s.u.sc.cntw, [&](uint32_t p, uint32_t b, uint32_t dest) {
-      bytes += move_record(c, sd, par, src0 + p, dest, t.depth, s.desc[b], t.begin + s.bstart[b]);
-    });
+    tile_scatter<LOGV>(s.u.sc.tb, tl, R, s.hist, s.u.sc.cntw,
+                       [&](const uint32_t(&pp)[kMoveBatch], const uint32_t(&bb)[kMoveBatch],
+                           const uint32_t(&dd)[kMoveBatch]) {
+                         bytes += move_batch(c, sd, par, src0, t.depth, s.desc,
+                                             [&](uint32_t b) { return t.begin + s.bstart[b]; }, pp, bb, dd);
+                       });
   }
   __threadfence();
   __syncthreads();
@@ -160,7 +163,7 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
 }
 
 template <int LOGV>
-__global__ void __launch_bounds__(kBlock) k_queue(SortCtx c, uint32_t R) {
+__global__ void __launch_bounds__(kBlock, 3) k_queue(SortCtx c, uint32_t R) {
   extern __shared__ __align__(16) uint8_t smem[];
   QueueSmem<LOGV>& s = *reinterpret_cast<QueueSmem<LOGV>*>(smem);
   unsigned long long bytes = 0;

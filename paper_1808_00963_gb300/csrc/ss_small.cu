@@ -62,9 +62,10 @@ __device__ __forceinline__ bool less3(uint32_t sa, uint64_t ka, uint32_t ia, uin
   return sa < sb || (sa == sb && (ka < kb || (ka == kb && ia < ib)));
 }
 
-// Bitonic sort of one element per lane by (seg, key, idx), ascending in lane order.
+// Bitonic sort of one element per lane by (seg, key, idx), ascending in lane
+// order; off, depth and open travel with the element.
 __device__ __forceinline__ void warp_sort(uint32_t& seg, uint64_t& key, uint32_t& idx, uint64_t& off,
-                                          uint32_t& open) {
+                                          uint32_t& depth, uint32_t& open) {
   const uint32_t lane = lane_id();
 #pragma unroll
   for (uint32_t k = 2; k <= 32; k <<= 1) {
@@ -74,63 +75,173 @@ __device__ __forceinline__ void warp_sort(uint32_t& seg, uint64_t& key, uint32_t
       const uint64_t ok = __shfl_xor_sync(kFull, key, j);
       const uint32_t oi = __shfl_xor_sync(kFull, idx, j);
       const uint64_t oo = __shfl_xor_sync(kFull, off, j);
+      const uint32_t od = __shfl_xor_sync(kFull, depth, j);
       const uint32_t op = __shfl_xor_sync(kFull, open, j);
       const bool up = (lane & k) == 0;
       const bool lower = (lane & j) == 0;
       const bool take = (lower == up) ? less3(os, ok, oi, seg, key, idx) : less3(seg, key, idx, os, ok, oi);
-      if (take) { seg = os; key = ok; idx = oi; off = oo; open = op; }
+      if (take) { seg = os; key = ok; idx = oi; off = oo; depth = od; open = op; }
     }
   }
 }
 
-// Sorts n (2..32) strings held one per lane (lanes >= n are ignored) that share
-// their first d0 characters and arrive in ascending index order; key is the
-// cache at depth d0, off the string's offset.  Writes lcp_out[j] for
-// 1 <= j < n (if lcp_out is not null) and returns the index at sorted
-// position lane.
-__device__ uint32_t warp_refine(uint64_t key, uint32_t idx, uint64_t off, uint32_t n, uint32_t d0,
-                                uint32_t cap, const uint8_t* chars, uint32_t* lcp_out, uint32_t* status,
-                                unsigned long long& bytes) {
+constexpr int kLookWindows = 8;  // look-ahead: 8 windows = 64 characters per round
+
+// Look-ahead read for the refinement of long common prefixes: the KW windows
+// of 8 characters at depths h, h + 8, ..., h + 8(KW-1) (first character most
+// significant, zero at/after the terminator or the cap).  Precondition: the
+// string has no terminator before h, so the byte at h belongs to the string
+// (or is its terminator).  All KW + 1 aligned words are issued at once, but
+// only words inside the 4 KiB-aligned block that holds byte h are read: memory
+// is mapped in blocks of at least 4 KiB, so these reads cannot fault, and bytes
+// past the terminator are discarded.  Returns how many leading windows are
+// fully determined (windows past the block, before a terminator was seen, are
+// not).
+template <int KW>
+__device__ __forceinline__ uint32_t load_windows(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
+                                                 uint64_t (&w)[KW]) {
+#pragma unroll
+  for (int j = 0; j < KW; ++j) w[j] = 0;
+  if (h >= cap) return KW;
+  const uintptr_t a = (uintptr_t)(chars + off + h);
+  const uintptr_t blk_end = (a & ~(uintptr_t)4095) + 4096;
+  const uintptr_t p0 = a & ~(uintptr_t)7;
+  const uint32_t sh = (uint32_t)(a & 7);
+  uint64_t word[KW + 1];
+#pragma unroll
+  for (int i = 0; i <= KW; ++i) {
+    const uintptr_t q = p0 + 8 * (uintptr_t)i;
+    word[i] = q < blk_end ? __ldg(reinterpret_cast<const uint64_t*>(q)) : 0ull;
+  }
+  const uint64_t known_total = (uint64_t)(blk_end - a);  // bytes from h that may be read (>= 1)
+  const uint64_t room_total = (uint64_t)cap - h;         // bytes from h before the cap (>= 1)
+  uint32_t nwin = KW;
+  bool ended = false;
+#pragma unroll
+  for (int j = 0; j < KW; ++j) {
+    if (ended || (uint32_t)j >= nwin) continue;
+    uint64_t v = sh ? ((word[j] >> (8 * sh)) | (word[j + 1] << (64 - 8 * sh))) : word[j];
+    const uint64_t ws = 8ull * j;
+    const uint32_t known = known_total > ws ? (known_total - ws >= 8 ? 8u : (uint32_t)(known_total - ws)) : 0u;
+    const uint32_t room = room_total > ws ? (room_total - ws >= 8 ? 8u : (uint32_t)(room_total - ws)) : 0u;
+    const uint32_t z = first_zero_byte(known < 8 ? (v | (~0ull << (8 * known))) : v);
+    if (z < known || room <= known) {
+      const uint32_t keep = z < room ? z : room;
+      if (keep < 8) {
+        v &= keep ? (~0ull >> (64 - 8 * keep)) : 0ull;
+        ended = true;
+      }
+      w[j] = bswap64(v);
+    } else {
+      nwin = (uint32_t)j;  // bytes past the block decide this window
+    }
+  }
+  return nwin;
+}
+
+// Finishes the subsets ("groups") held by a warp, one string per lane.  Lanes
+// [g0, g0 + glen) hold one group: strings with a common prefix of their
+// `depth` characters, in ascending index order, with key = their cache at that
+// depth.  Lane-static (they do not move): active, g0, chars/cap of the group's
+// set and lcp_g, the LCP output at the group's first position.  Sorting by
+// (segment, cache, index) splits a group into runs of equal caches; a run of
+// one string or of equal strings (cache holds the terminator) is finished;
+// every other run jumps over the characters all its members share, found with
+// a 64-character look-ahead, and is sorted again.  Writes lcp_g[j] for every
+// position j > 0 of each group and returns the index at the lane's position.
+__device__ uint32_t warp_refine(bool active, uint32_t g0, uint32_t nact, uint64_t key, uint32_t idx,
+                                uint64_t off, uint32_t depth, uint32_t cap, const uint8_t* chars,
+                                uint32_t* lcp_g, uint32_t* status, unsigned long long& bytes) {
   const uint32_t lane = lane_id();
-  const bool active = lane < n;
-  uint32_t seg = active ? 0u : 0xFFFFFFFFu;
+  uint32_t seg = active ? g0 : 0xFFFFFFFFu;
   uint32_t open = active ? 1u : 0u;
-  if (!active) { key = ~0ull; idx = 0xFFFFFFFFu; off = 0; }
-  uint32_t depth = d0;
+  if (!active) { key = ~0ull; idx = 0xFFFFFFFFu; off = 0; depth = 0; }
   const uint32_t upto = (lane == 31) ? kFull : ((2u << lane) - 1);
   while (true) {
-    warp_sort(seg, key, idx, off, open);
+    warp_sort(seg, key, idx, off, depth, open);
     const uint32_t ps = __shfl_up_sync(kFull, seg, 1);
     const uint64_t pk = __shfl_up_sync(kFull, key, 1);
     const bool start = lane == 0 || seg != ps || key != pk;
-    if (active && open && lane > 0 && seg == ps && key != pk && lcp_out) lcp_out[lane] = depth + lcp8(pk, key);
+    if (active && open && lane > g0 && seg == ps && key != pk && lcp_g) lcp_g[lane - g0] = depth + lcp8(pk, key);
     const uint32_t starts = __ballot_sync(kFull, active && start);
     const uint32_t my_start = 31 - __clz(starts & upto);
     const uint32_t above = starts & ~upto;
-    const uint32_t next = above ? (uint32_t)(__ffs(above) - 1) : n;
-    const uint32_t size = next - my_start;
+    const uint32_t next = above ? (uint32_t)(__ffs(above) - 1) : nact;
     if (active && open) {
-      if (size == 1) {
+      if (next - my_start == 1) {
         open = 0;
       } else if (has_nul(key)) {
         open = 0;
-        if (lane != my_start && lcp_out) lcp_out[lane] = depth + nnz_prefix(key);
+        if (lane != my_start && lcp_g) lcp_g[lane - g0] = depth + nnz_prefix(key);
       }
     }
     if (active) seg = my_start;
     if (!__any_sync(kFull, active && open)) break;
-    if (depth + 8 > kMaxDepth) {
-      if (lane == 0) latch_status(status, kStTooDeep);
-      break;
+    // look-ahead: the first window (8, 16, ... characters deeper) where the
+    // members of the run differ or end; the run continues there
+    uint64_t w[kLookWindows];
+    uint32_t nwin = 0;
+    if (active && open) nwin = load_windows<kLookWindows>(chars, off, depth + 8, cap, w);
+    const uint32_t segmask = (next >= 32 ? kFull : ((1u << next) - 1)) & ~((1u << my_start) - 1);
+    uint32_t jstop = kLookWindows - 1;
+    bool found = false;
+#pragma unroll
+    for (int j = 0; j < kLookWindows; ++j) {
+      const uint64_t lw = __shfl_sync(kFull, w[j], my_start);
+      const bool stop = active && open && ((uint32_t)j >= nwin || w[j] != lw || has_nul(w[j]));
+      const uint32_t b = __ballot_sync(kFull, stop) & segmask;
+      if (!found && b) { jstop = (uint32_t)j; found = true; }
     }
-    depth += 8;
     if (active && open) {
-      key = load_cache(chars, off, depth, cap);
-      bytes += 8;
+      const uint32_t nd = depth + 8 * (jstop + 1);
+      if (nd > kMaxDepth) {
+        latch_status(status, kStTooDeep);
+        open = 0;
+      } else {
+        uint64_t k = w[0];
+#pragma unroll
+        for (int j = 1; j < kLookWindows; ++j) if ((uint32_t)j == jstop) k = w[j];
+        key = jstop < nwin ? k : load_cache(chars, off, nd, cap);
+        depth = nd;
+        bytes += 8ull * (jstop + 1);
+      }
     }
   }
   return idx;
 }
+
+// Packs up to 16 items (lane k < nt holds item k's length, 1..32) into rounds
+// of whole items that fit into 32 lanes, in order.  For each round calls
+// round(active, g0, nact, k): the lane belongs to item k, whose first lane is
+// g0; nact lanes are in use.
+template <typename Round>
+__device__ __forceinline__ void pack_rounds(uint32_t nt, uint32_t my_len, Round&& round) {
+  const uint32_t lane = lane_id();
+  const uint32_t upto = (lane == 31) ? kFull : ((2u << lane) - 1);
+  uint32_t a = 0;
+  while (a < nt) {
+    const uint32_t mine = (lane < nt && lane >= a) ? my_len : 0u;
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= (uint32_t)o) incl += t;
+    }
+    const uint32_t fits = __ballot_sync(kFull, lane >= a && lane < nt && incl <= 32);
+    const uint32_t b = 32 - __clz(fits);
+    const uint32_t excl = incl - mine;
+    const uint32_t startbits = __reduce_or_sync(kFull, (lane >= a && lane < b) ? (1u << excl) : 0u);
+    const uint32_t nact = __shfl_sync(kFull, incl, b - 1);
+    const uint32_t k = a + __popc(startbits & upto) - 1;
+    const uint32_t g0 = 31 - __clz(startbits & upto);
+    round(lane < nact, g0, nact, k);
+    a = b;
+  }
+}
+
+// Warps take runs of up to 16 consecutive small tasks and pack as many whole
+// tasks as fit into 32 lanes per round.
+constexpr uint32_t kPackChunk = 16;
 
 __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -138,23 +249,40 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
   const uint32_t count = min(*c.small_warp.count, c.small_warp.cap);
   const uint32_t lane = lane_id();
   unsigned long long bytes = 0;
-  for (uint32_t ti = warp; ti < count; ti += nwarps) {
-    const Task t = c.small_warp.items[ti];
-    const SetDesc sd = c.sets[task_set(t)];
-    const uint32_t par = task_par(t);
-    uint64_t key = 0, off = 0;
-    uint32_t id = 0;
-    if (lane < t.len) {
-      key = c.key[par][t.begin + lane];
-      id = c.idx[par][t.begin + lane];
-      off = sd.offsets[id];
-    }
-    uint32_t* lo = sd.lcp ? sd.lcp + (t.begin - sd.base) : nullptr;
-    const uint32_t fin = warp_refine(key, id, off, t.len, t.depth, sd.cap, sd.chars, lo, c.status, bytes);
-    if (lane < t.len) {
-      sd.perm[t.begin - sd.base + lane] = fin;
-      bytes += sd.lcp ? 28 : 24;  // cache 8 + index 4 + offset 8 read; perm 4 (+ lcp 4) written
-    }
+  // few tasks: one per warp (parallelism); many: up to 16 per warp (packing)
+  const uint32_t chunk = min(kPackChunk, max(1u, (count + nwarps - 1) / nwarps));
+  for (uint32_t c0 = warp * chunk; c0 < count; c0 += nwarps * chunk) {
+    const uint32_t nt = min(chunk, count - c0);
+    Task mt{0, 0, 0, 0};
+    if (lane < nt) mt = c.small_warp.items[c0 + lane];
+    pack_rounds(nt, mt.len, [&](bool active, uint32_t g0, uint32_t nact, uint32_t k) {
+      const uint32_t tb = __shfl_sync(kFull, mt.begin, k & 31);
+      const uint32_t tdepth = __shfl_sync(kFull, mt.depth, k & 31);
+      const uint32_t tmeta = __shfl_sync(kFull, mt.meta, k & 31);
+      uint64_t key = 0, off = 0;
+      uint32_t id = 0, cap = kNoCap;
+      const uint8_t* chars = nullptr;
+      uint32_t* lcp_g = nullptr;
+      uint32_t* perm = nullptr;
+      if (active) {
+        const SetDesc sd = c.sets[tmeta & 0x7FFFFFFFu];
+        const uint32_t par = tmeta >> 31;
+        const uint32_t e = lane - g0;
+        key = c.key[par][tb + e];
+        id = c.idx[par][tb + e];
+        off = sd.offsets[id];
+        cap = sd.cap;
+        chars = sd.chars;
+        lcp_g = sd.lcp ? sd.lcp + (tb - sd.base) : nullptr;
+        perm = sd.perm + (tb - sd.base);
+      }
+      const uint32_t fin = warp_refine(active, g0, nact, key, id, off, tdepth, cap, chars, lcp_g, c.status,
+                                       bytes);
+      if (active) {
+        perm[lane - g0] = fin;
+        bytes += lcp_g ? 28 : 24;  // cache 8 + index 4 + offset 8 read; perm 4 (+ lcp 4) written
+      }
+    });
   }
   account(c, kKSmallWarp, bytes);
 }
@@ -324,22 +452,30 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
       __syncthreads();
     }
     if (handoff) {
+      // runs of at most 32 strings, packed into warps; each continues at its
+      // own pace with the warp refinement (cache still at `depth`)
       const uint32_t w = threadIdx.x >> 5, lane = lane_id();
       const uint32_t nl = s_nlist;
-      for (uint32_t li = w; li < nl; li += kWarps) {
-        const uint32_t s0 = m.list[li];
-        const uint32_t size = m.aux[s0];
-        uint64_t key = 0, off = 0;
-        uint32_t id = 0;
-        if (lane < size) {
-          off = m.off[s0 + lane];
-          id = m.idx[s0 + lane];
-          key = load_cache(sd.chars, off, depth + 8, sd.cap);
-          bytes += 8;
-        }
-        const uint32_t fin = warp_refine(key, id, off, size, depth + 8, sd.cap, sd.chars,
-                                         lcp ? lcp + s0 : nullptr, c.status, bytes);
-        if (lane < size) m.idx[s0 + lane] = fin;
+      const uint32_t chunk = min(kPackChunk, max(1u, (nl + kWarps - 1) / kWarps));
+      for (uint32_t l0 = w * chunk; l0 < nl; l0 += kWarps * chunk) {
+        const uint32_t nt = min(chunk, nl - l0);
+        const uint32_t my_s0 = lane < nt ? m.list[l0 + lane] : 0u;
+        const uint32_t my_len = lane < nt ? m.aux[my_s0] : 0u;
+        pack_rounds(nt, my_len, [&](bool active, uint32_t g0, uint32_t nact, uint32_t k) {
+          const uint32_t s0 = __shfl_sync(kFull, my_s0, k & 31);
+          uint64_t key = 0, off = 0;
+          uint32_t id = 0;
+          if (active) {
+            const uint32_t e = lane - g0;
+            key = m.key[s0 + e];
+            off = m.off[s0 + e];
+            id = m.idx[s0 + e];
+          }
+          const uint32_t fin = warp_refine(active, g0, nact, key, id, off, depth, sd.cap, sd.chars,
+                                           (lcp && active) ? lcp + s0 : nullptr, c.status, bytes);
+          __syncwarp();
+          if (active) m.idx[s0 + lane - g0] = fin;
+        });
       }
       __syncthreads();
     }

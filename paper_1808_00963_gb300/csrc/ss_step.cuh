@@ -146,6 +146,12 @@ __device__ __forceinline__ uint32_t bucket_desc(uint32_t b, uint32_t size, uint3
   return depth + sp.hp[r];
 }
 
+// Records moved per batch of one warp in the distribution: the loads of a
+// batch are issued together so that each warp keeps kMoveBatch rounds of
+// memory accesses in flight.
+constexpr int kMoveBatch = 8;
+constexpr uint32_t kInvalid = 0xFFFFFFFFu;
+
 // Stable distribution of one tile of records (Algorithm 4.1 line 16 with the
 // per-processor bucket arrays of Theorem 4.4, one per warp).
 //   tb[0..tl)    bucket of each record of the tile (shared memory)
@@ -154,7 +160,8 @@ __device__ __forceinline__ uint32_t bucket_desc(uint32_t b, uint32_t size, uint3
 //   cntw         shared scratch, kWarps * KP uint32
 // Warp w owns records [w * 32R, (w + 1) * 32R) of the tile; inside a warp
 // ranks come from __match_any_sync, so equal buckets keep input order.
-// move(p, b, dest) is called once per record p < tl.  Ends with __syncthreads().
+// move(p[], b[], dest[]) is called with kMoveBatch rounds of one warp at a time
+// (p = kInvalid for lanes without a record).  Ends with __syncthreads().
 template <int LOGV, typename Move>
 __device__ void tile_scatter(const uint16_t* tb, uint32_t tl, uint32_t R, uint32_t* base,
                              uint32_t* cntw, Move&& move) {
@@ -185,49 +192,85 @@ __device__ void tile_scatter(const uint16_t* tb, uint32_t tl, uint32_t R, uint32
   }
   __syncthreads();
   const uint32_t lt = lanemask_lt();
-  for (uint32_t r = 0; r < R; ++r) {
-    const uint32_t p = p0 + r * 32 + lane;
-    const bool valid = p < tl;
-    const uint32_t b = valid ? tb[p] : 0xFFFFu;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
-    uint32_t dest = 0;
-    if (valid) dest = mine[b] + __popc(peers & lt);
-    __syncwarp();
-    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) mine[b] += __popc(peers);
-    __syncwarp();
-    if (valid) move(p, b, dest);
+  for (uint32_t r0 = 0; r0 < R; r0 += kMoveBatch) {
+    uint32_t pp[kMoveBatch], bb[kMoveBatch], dd[kMoveBatch];
+#pragma unroll
+    for (int u = 0; u < kMoveBatch; ++u) {
+      const uint32_t r = r0 + u;
+      const uint32_t p = p0 + r * 32 + lane;
+      const bool valid = r < R && p < tl;
+      const uint32_t b = valid ? tb[p] : 0xFFFFu;
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
+      uint32_t dest = 0;
+      if (valid) dest = mine[b] + __popc(peers & lt);
+      __syncwarp();
+      if (valid && lane == (uint32_t)(__ffs(peers) - 1)) mine[b] += __popc(peers);
+      __syncwarp();
+      pp[u] = valid ? p : kInvalid;
+      bb[u] = b;
+      dd[u] = dest;
+    }
+    move(pp, bb, dd);
   }
   __syncthreads();
 }
 
-// Moves one record to its bucket (the body of line 16): a finished record
-// writes its final index (and, inside a bucket of equal strings, its LCP);
-// an open one is copied to the other buffer with its cache reloaded at the
-// bucket's new depth (fused character gather).
-// Returns the algorithmic bytes of the move: bucket index 2 + idx 4 read;
-// finished: perm 4 (+ lcp 4) written; open: key 8 read, key 8 + idx 4
-// written, plus offset 8 + 8 characters read when the cache is reloaded.
-__device__ __forceinline__ uint32_t move_record(const SortCtx& c, const SetDesc& sd, uint32_t par,
-                                                uint32_t src, uint32_t dest, uint32_t depth,
-                                                uint32_t desc, uint32_t bucket_first) {
-  const uint32_t id = c.idx[par][src];
-  if (desc & kFin) {
-    sd.perm[dest - sd.base] = id;
-    if (sd.lcp && (desc & kNulEq) && dest != bucket_first) {
-      sd.lcp[dest - sd.base] = desc & kLow30;
-      return 14;
+// Moves a batch of records to their buckets (the body of line 16): a finished
+// record writes its final index (and, inside a bucket of equal strings, its
+// LCP); an open one is copied to the other buffer with its cache reloaded at
+// the bucket's new depth (fused character gather).  All loads of the batch
+// are issued before any of them is used.  bucket_first(b) is the position of
+// the first record of bucket b.  Returns the algorithmic bytes: bucket index 2
+// + idx 4 read; finished: perm 4 (+ lcp 4) written; open: key 8 read, key 8 +
+// idx 4 written, plus offset 8 + 8 characters read when the cache is reloaded.
+template <typename First>
+__device__ __forceinline__ uint32_t move_batch(const SortCtx& c, const SetDesc& sd, uint32_t par, uint32_t src0,
+                                               uint32_t depth, const uint32_t* desc, First&& bucket_first,
+                                               const uint32_t (&pp)[kMoveBatch], const uint32_t (&bb)[kMoveBatch],
+                                               const uint32_t (&dd)[kMoveBatch]) {
+  uint32_t id[kMoveBatch], ds[kMoveBatch];
+  uint64_t key[kMoveBatch], off[kMoveBatch];
+  uint32_t bytes = 0;
+#pragma unroll
+  for (int u = 0; u < kMoveBatch; ++u) {
+    id[u] = 0;
+    ds[u] = kFin;
+    key[u] = 0;
+    if (pp[u] != kInvalid) {
+      ds[u] = desc[bb[u]];
+      id[u] = c.idx[par][src0 + pp[u]];
+      if (!(ds[u] & kFin)) key[u] = c.key[par][src0 + pp[u]];
     }
-    return 10;
   }
-  const uint32_t nd = desc & kLow30;
-  uint64_t key = c.key[par][src];
-  uint32_t bytes = 26;
-  if (nd != depth) {
-    key = load_cache(sd.chars, sd.offsets[id], nd, sd.cap);
-    bytes += 16;
+#pragma unroll
+  for (int u = 0; u < kMoveBatch; ++u) {
+    off[u] = 0;
+    if (pp[u] != kInvalid && !(ds[u] & kFin) && (ds[u] & kLow30) != depth) off[u] = sd.offsets[id[u]];
   }
-  c.key[par ^ 1][dest] = key;
-  c.idx[par ^ 1][dest] = id;
+#pragma unroll
+  for (int u = 0; u < kMoveBatch; ++u) {
+    if (pp[u] == kInvalid) continue;
+    const uint32_t d = ds[u];
+    const uint32_t dest = dd[u];
+    if (d & kFin) {
+      sd.perm[dest - sd.base] = id[u];
+      bytes += 10;
+      if (sd.lcp && (d & kNulEq) && dest != bucket_first(bb[u])) {
+        sd.lcp[dest - sd.base] = d & kLow30;
+        bytes += 4;
+      }
+      continue;
+    }
+    const uint32_t nd = d & kLow30;
+    uint64_t k = key[u];
+    bytes += 26;
+    if (nd != depth) {
+      k = load_cache(sd.chars, off[u], nd, sd.cap);
+      bytes += 16;
+    }
+    c.key[par ^ 1][dest] = k;
+    c.idx[par ^ 1][dest] = id[u];
+  }
   return bytes;
 }
 
