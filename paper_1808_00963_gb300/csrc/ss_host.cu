@@ -187,7 +187,7 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
   L.cap_big = big ? (uint32_t)(M / ((uint64_t)o.big_thr + 1) + 2) : 0;
   L.cap_mq = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, std::max<uint64_t>(4096, o.mq_factor * (M / o.cutoff) + 1024));
-  L.cap_sw = (uint32_t)(M / 2 + 2);
+  L.cap_sw = (uint32_t)(M + 2);  // direct warp tasks (<= M/2) plus runs passed on by the block sort (<= M/2)
   L.cap_sc = (uint32_t)(M / 33 + 2);
   const uint64_t KP = 2ull << o.logv_big;
   const uint64_t tiles_max = big ? M / (kBlock * 8) + L.cap_big : 0;

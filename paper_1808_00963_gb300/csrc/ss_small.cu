@@ -289,44 +289,65 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
 
 // ---- block-level refinement -------------------------------------------------------
 
-struct CtaSmem {  // carved from dynamic shared memory, P = pmax elements
-  uint64_t* key;
-  uint64_t* off;
-  uint32_t* idx;
+// Element tags of the block sort: handed (1 bit) << 25 | segment (12 bits)
+// << 13 | original position (12 bits) << 1 | open (1 bit).  Sorting by (segment, cache, tag)
+// orders each segment by cache and, among equal caches, by original position
+// (= ascending index).  Index and offset stay at the original position.
+__device__ __forceinline__ uint32_t tag_seg(uint32_t t) { return (t >> 13) & 0xFFFu; }
+constexpr uint32_t kHanded = 1u << 25;  // run passed on to the warp list
+__device__ __forceinline__ uint32_t tag_pos(uint32_t t) { return (t >> 1) & 0xFFFu; }
+__device__ __forceinline__ uint32_t make_tag(uint32_t seg, uint32_t pos, uint32_t open) {
+  return (seg << 13) | (pos << 1) | open;
+}
+
+struct CtaSmem {  // carved from dynamic shared memory, pmax elements
+  uint64_t* key;    // cache, in sorted position
+  uint64_t* off;    // string offset, by original position
+  uint32_t* tag;    // in sorted position
+  uint32_t* idx;    // index, by original position
   uint32_t* aux;    // segment sizes
-  uint16_t* seg;
-  uint16_t* nseg;
-  uint16_t* list;   // open segment starts (at most pmax / 2: each has >= 2 members)
-  uint8_t* open;
+  uint16_t* nseg;   // segment start of each position
 };
 
-__device__ __forceinline__ bool lessc(const CtaSmem& m, uint32_t a, uint32_t b) {
-  return less3(m.seg[a], m.key[a], m.idx[a], m.seg[b], m.key[b], m.idx[b]);
+__device__ __forceinline__ void cmp_swap(const CtaSmem& m, uint32_t lo, uint32_t hi) {
+  const uint64_t ka = m.key[lo], kb = m.key[hi];
+  const uint32_t ta = m.tag[lo], tb = m.tag[hi];
+  const uint32_t sa = tag_seg(ta), sb = tag_seg(tb);
+  const bool gt = sa > sb || (sa == sb && (ka > kb || (ka == kb && ta > tb)));
+  if (gt) {
+    m.key[lo] = kb; m.key[hi] = ka;
+    m.tag[lo] = tb; m.tag[hi] = ta;
+  }
 }
 
-__device__ __forceinline__ void swapc(const CtaSmem& m, uint32_t a, uint32_t b) {
-  uint64_t k = m.key[a]; m.key[a] = m.key[b]; m.key[b] = k;
-  uint64_t o = m.off[a]; m.off[a] = m.off[b]; m.off[b] = o;
-  uint32_t i = m.idx[a]; m.idx[a] = m.idx[b]; m.idx[b] = i;
-  uint16_t s = m.seg[a]; m.seg[a] = m.seg[b]; m.seg[b] = s;
-  uint8_t p = m.open[a]; m.open[a] = m.open[b]; m.open[b] = p;
-}
-
-__device__ void block_sort(const CtaSmem& m, uint32_t P) {
-  for (uint32_t k = 2; k <= P; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+// Ascending bitonic sort of positions [0, n) where every comparator points the
+// same way (the first step of each merge compares mirrored positions), so a
+// comparator whose upper position is >= n can be skipped: it would compare
+// against +infinity.
+__device__ void block_sort(const CtaSmem& m, uint32_t n) {
+  uint32_t P = 2;
+  while (P < n) P <<= 1;
+  for (uint32_t k = 2, lh = 0; k <= P; k <<= 1, ++lh) {
+    const uint32_t h = k >> 1;  // = 1 << lh
+    for (uint32_t i = threadIdx.x; i < P / 2; i += kBlock) {
+      const uint32_t blk = (i >> lh) << (lh + 1);
+      const uint32_t r = i & (h - 1);
+      const uint32_t hi = blk + k - 1 - r;
+      if (hi < n) cmp_swap(m, blk + r, hi);
+    }
+    __syncthreads();
+    for (uint32_t j = h >> 1; j > 0; j >>= 1) {
       for (uint32_t i = threadIdx.x; i < P / 2; i += kBlock) {
         const uint32_t lo = 2 * i - (i & (j - 1));
         const uint32_t hi = lo + j;
-        const bool up = (lo & k) == 0;
-        if (lessc(m, hi, lo) == up) swapc(m, lo, hi);
+        if (hi < n) cmp_swap(m, lo, hi);
       }
       __syncthreads();
     }
   }
 }
 
-// Inclusive max-scan of nseg[0..n) in place (n <= pmax).
+// Inclusive max-scan of a[0..n) in place.
 __device__ void block_max_scan(uint16_t* a, uint32_t n) {
   __shared__ uint32_t wmax[kWarps];
   const uint32_t per = (n + kBlock - 1) / kBlock;
@@ -367,13 +388,12 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
   CtaSmem m;
   m.key = reinterpret_cast<uint64_t*>(smem);
   m.off = m.key + pmax;
-  m.idx = reinterpret_cast<uint32_t*>(m.off + pmax);
+  m.tag = reinterpret_cast<uint32_t*>(m.off + pmax);
+  m.idx = m.tag + pmax;
   m.aux = m.idx + pmax;
-  m.seg = reinterpret_cast<uint16_t*>(m.aux + pmax);
-  m.nseg = m.seg + pmax;
-  m.list = m.nseg + pmax;
-  m.open = reinterpret_cast<uint8_t*>(m.list + pmax / 2);
-  __shared__ uint32_t s_max_open, s_nlist;
+  m.nseg = reinterpret_cast<uint16_t*>(m.aux + pmax);
+  __shared__ uint32_t s_max_open, s_jstop, s_neq;
+  __shared__ uint64_t s_lead[kLookWindows];
   unsigned long long bytes = 0;
   const uint32_t count = min(*c.small_cta.count, c.small_cta.cap);
   for (uint32_t ti = blockIdx.x; ti < count; ti += gridDim.x) {
@@ -381,34 +401,66 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
     const SetDesc sd = c.sets[task_set(t)];
     const uint32_t par = task_par(t);
     const uint32_t n = t.len;
-    uint32_t P = 64;
-    while (P < n) P <<= 1;
-    for (uint32_t j = threadIdx.x; j < P; j += kBlock) {
-      if (j < n) {
-        const uint32_t id = c.idx[par][t.begin + j];
-        m.key[j] = c.key[par][t.begin + j];
-        m.idx[j] = id;
-        m.off[j] = sd.offsets[id];
-        m.seg[j] = 0;
-        m.open[j] = 1;
-      } else {
-        m.key[j] = ~0ull;
-        m.idx[j] = 0xFFFFFFFFu;
-        m.off[j] = 0;
-        m.seg[j] = 0xFFFFu;
-        m.open[j] = 0;
-      }
+    for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+      const uint32_t id = c.idx[par][t.begin + j];
+      m.key[j] = c.key[par][t.begin + j];
+      m.idx[j] = id;
+      m.off[j] = sd.offsets[id];
+      m.tag[j] = make_tag(0, j, 1);
     }
     uint32_t* lcp = sd.lcp ? sd.lcp + (t.begin - sd.base) : nullptr;
     uint32_t depth = t.depth;
     __syncthreads();
-    bool handoff = false;
+
+    // While every string of the subset has the same cache (and it holds no
+    // terminator), jump over the common prefix: compare each string's next 64
+    // characters with the first string's and continue at the first window
+    // where some string differs or ends.
     while (true) {
-      block_sort(m, P);
-      if (threadIdx.x == 0) { s_max_open = 0; s_nlist = 0; }
+      if (threadIdx.x == 0) s_neq = 0;
+      __syncthreads();
+      const uint64_t k0 = m.key[0];
+      for (uint32_t j = threadIdx.x; j < n; j += kBlock)
+        if (m.key[j] != k0) s_neq = 1;
+      __syncthreads();
+      if (s_neq || has_nul(k0) || depth + 8 * kLookWindows > kMaxDepth) break;
+      if (threadIdx.x == 0) {
+        uint64_t w[kLookWindows];
+        const uint32_t nwin = load_windows<kLookWindows>(sd.chars, m.off[0], depth + 8, sd.cap, w);
+        uint32_t js = kLookWindows - 1;
+        for (int j = kLookWindows - 1; j >= 0; --j) {
+          s_lead[j] = w[j];
+          if ((uint32_t)j >= nwin || has_nul(w[j])) js = (uint32_t)j;
+        }
+        s_jstop = js;
+      }
+      __syncthreads();
+      for (uint32_t j = threadIdx.x + 1; j < n; j += kBlock) {
+        uint64_t w[kLookWindows];
+        const uint32_t nwin = load_windows<kLookWindows>(sd.chars, m.off[j], depth + 8, sd.cap, w);
+        uint32_t js = kLookWindows;
+#pragma unroll
+        for (int q = kLookWindows - 1; q >= 0; --q)
+          if ((uint32_t)q >= nwin || w[q] != s_lead[q]) js = (uint32_t)q;
+        if (js < kLookWindows) atomicMin(&s_jstop, js);
+      }
+      __syncthreads();
+      const uint32_t nd = depth + 8 * (s_jstop + 1);
       for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
-        const bool st = j == 0 || m.seg[j] != m.seg[j - 1] || m.key[j] != m.key[j - 1];
-        if (lcp && m.open[j] && j > 0 && m.seg[j] == m.seg[j - 1] && m.key[j] != m.key[j - 1])
+        m.key[j] = load_cache(sd.chars, m.off[j], nd, sd.cap);
+        bytes += 8ull * (s_jstop + 1);
+      }
+      depth = nd;
+      __syncthreads();
+    }
+
+    while (true) {
+      block_sort(m, n);
+      if (threadIdx.x == 0) s_max_open = 0;
+      for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+        const uint32_t tg = m.tag[j];
+        const bool st = j == 0 || tag_seg(tg) != tag_seg(m.tag[j - 1]) || m.key[j] != m.key[j - 1];
+        if (lcp && (tg & 1u) && j > 0 && tag_seg(tg) == tag_seg(m.tag[j - 1]) && m.key[j] != m.key[j - 1])
           lcp[j] = depth + lcp8(m.key[j - 1], m.key[j]);
         m.nseg[j] = st ? (uint16_t)j : 0;
         m.aux[j] = 0;
@@ -417,24 +469,32 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
       block_max_scan(m.nseg, n);
       for (uint32_t j = threadIdx.x; j < n; j += kBlock) atomicAdd(&m.aux[m.nseg[j]], 1u);
       __syncthreads();
+      // Runs of one string or of equal strings are finished; runs of at most
+      // 32 strings go back to the record buffer as new warp tasks (a warp
+      // finishes them without holding this block); larger runs continue here.
       for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
         const uint32_t s0 = m.nseg[j];
-        if (m.open[j]) {
+        uint32_t tg = m.tag[j];
+        uint32_t open = tg & 1u, handed = tg & kHanded;
+        if (open) {
           const uint32_t size = m.aux[s0];
           if (size == 1) {
-            m.open[j] = 0;
+            open = 0;
           } else if (has_nul(m.key[j])) {
-            m.open[j] = 0;
+            open = 0;
             if (lcp && j != s0) lcp[j] = depth + nnz_prefix(m.key[j]);
+          } else if (size <= 32) {
+            open = 0;
+            handed = kHanded;
+            c.key[par][t.begin + j] = m.key[j];
+            c.idx[par][t.begin + j] = m.idx[tag_pos(tg)];
+            bytes += 12;
+            if (j == s0) list_push(c.small_warp, Task{t.begin + j, size, depth, t.meta}, c.status);
           } else {
             atomicMax(&s_max_open, size);
-            if (j == s0) {
-              const uint32_t slot = atomicAdd(&s_nlist, 1u);
-              m.list[slot] = (uint16_t)j;
-            }
           }
         }
-        m.seg[j] = (uint16_t)s0;
+        m.tag[j] = handed | make_tag(s0, tag_pos(tg), open);
       }
       __syncthreads();
       if (s_max_open == 0) break;
@@ -442,45 +502,17 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
         if (threadIdx.x == 0) latch_status(c.status, kStTooDeep);
         break;
       }
-      if (s_max_open <= 32) { handoff = true; break; }
       depth += 8;
       for (uint32_t j = threadIdx.x; j < n; j += kBlock)
-        if (m.open[j]) {
-          m.key[j] = load_cache(sd.chars, m.off[j], depth, sd.cap);
+        if (m.tag[j] & 1u) {
+          m.key[j] = load_cache(sd.chars, m.off[tag_pos(m.tag[j])], depth, sd.cap);
           bytes += 8;
         }
       __syncthreads();
     }
-    if (handoff) {
-      // runs of at most 32 strings, packed into warps; each continues at its
-      // own pace with the warp refinement (cache still at `depth`)
-      const uint32_t w = threadIdx.x >> 5, lane = lane_id();
-      const uint32_t nl = s_nlist;
-      const uint32_t chunk = min(kPackChunk, max(1u, (nl + kWarps - 1) / kWarps));
-      for (uint32_t l0 = w * chunk; l0 < nl; l0 += kWarps * chunk) {
-        const uint32_t nt = min(chunk, nl - l0);
-        const uint32_t my_s0 = lane < nt ? m.list[l0 + lane] : 0u;
-        const uint32_t my_len = lane < nt ? m.aux[my_s0] : 0u;
-        pack_rounds(nt, my_len, [&](bool active, uint32_t g0, uint32_t nact, uint32_t k) {
-          const uint32_t s0 = __shfl_sync(kFull, my_s0, k & 31);
-          uint64_t key = 0, off = 0;
-          uint32_t id = 0;
-          if (active) {
-            const uint32_t e = lane - g0;
-            key = m.key[s0 + e];
-            off = m.off[s0 + e];
-            id = m.idx[s0 + e];
-          }
-          const uint32_t fin = warp_refine(active, g0, nact, key, id, off, depth, sd.cap, sd.chars,
-                                           (lcp && active) ? lcp + s0 : nullptr, c.status, bytes);
-          __syncwarp();
-          if (active) m.idx[s0 + lane - g0] = fin;
-        });
-      }
-      __syncthreads();
-    }
     for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
-      sd.perm[t.begin - sd.base + j] = m.idx[j];
+      const uint32_t tg = m.tag[j];
+      if (!(tg & kHanded)) sd.perm[t.begin - sd.base + j] = m.idx[tag_pos(tg)];
       bytes += sd.lcp ? 28 : 24;  // cache 8 + index 4 + offset 8 read; perm 4 (+ lcp 4) written
     }
     __syncthreads();
@@ -513,7 +545,7 @@ __global__ void __launch_bounds__(kBlock) k_lcp_fix(SortCtx c) {
 
 }  // namespace
 
-size_t small_cta_smem(uint32_t pmax) { return (size_t)pmax * (8 + 8 + 4 + 4 + 2 + 2 + 1 + 1); }
+size_t small_cta_smem(uint32_t pmax) { return (size_t)pmax * (8 + 8 + 4 + 4 + 4 + 2); }
 
 cudaError_t launch_init(const SortCtx& c, cudaStream_t st, const LaunchHook& hook) {
   const uint32_t grid = max(1u, min((c.total + kBlock - 1) / kBlock, 152u * 16u));
@@ -531,8 +563,8 @@ cudaError_t launch_small(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, ui
     if (e != cudaSuccess) return e;
     attr_pmax = pmax;
   }
-  hook.run("small_warp", [&] { k_small_warp<<<grid_warp, kBlock, 0, st>>>(c); });
   hook.run("small_cta", [&] { k_small_cta<<<grid_cta, kBlock, small_cta_smem(pmax), st>>>(c, pmax); });
+  hook.run("small_warp", [&] { k_small_warp<<<grid_warp, kBlock, 0, st>>>(c); });
   return cudaGetLastError();
 }
 
