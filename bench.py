@@ -342,13 +342,97 @@ def run_ours(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ---- batched workload (configuration 4) ---------------------------------------------------------
+
+def run_batch(args, ws, rank, local):
+    """4096 independent string sets (log-uniform 100..200k strings, random /
+    URL / DNA generators) sorted as one batch (one persistent launch sequence,
+    captured into a CUDA graph) against 4096 plain calls on one stream."""
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    ss.load()
+    num = args.sets
+    specs = gen.batch_specs(num, 4)
+    sets = [gen.make_set(k, n, sd) for (k, n, sd) in specs]
+    chars, offsets, cbase, first, mls = gen.concat(sets)
+    total = int(offsets.shape[0])
+    dev = torch.device("cuda", torch.cuda.current_device())
+    chars_d = torch.from_numpy(chars).to(dev)
+    offs_d = torch.from_numpy(offsets.view(np.int64)).to(dev)
+    perm_d = torch.empty(total, dtype=torch.int32, device=dev)
+    lcp_d = torch.empty(total, dtype=torch.int32, device=dev)
+    descs = []
+    for i, st in enumerate(sets):
+        a, b = int(first[i]), int(first[i]) + st.n
+        descs.append((chars_d[int(cbase[i]):], offs_d[a:b], int(mls[i]), perm_d[a:b], lcp_d[a:b]))
+    batch = ss.Batch(descs)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            batch.run()
+    batch.status(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        batch.run()
+
+    def timed(fn, k):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    launches0 = ss.launch_count()
+    ms_graph = timed(graph.replay, args.steps)
+    batch.status()
+    with torch.cuda.stream(stream):
+        ms_nograph = timed(lambda: batch.run(stream), args.steps)
+    batch.status(stream)
+    launches = ss.launch_count() - launches0
+    # plain: one ss_sort call per set, one after another
+    lat = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (ch, of, ml, p, l) in descs:
+        a = time.perf_counter()
+        ss.sort(ch, of, max_len=ml, out=(p, l))
+        lat.append((time.perf_counter() - a) * 1e3)
+    plain_s = time.perf_counter() - t0
+    lat = np.array(lat)
+    line = {
+        "metric": METRIC, "value": total / (ms_graph / 1e3), "unit": "strings/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_graph, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"batched: {num} sets, log-uniform 100-200k strings, random/URL/DNA generators",
+                   "sets": num, "strings": total, "chars_bytes": int(chars.shape[0]),
+                   "per_step": "one batch (all sets sorted, perm + LCP), CUDA graph replay"},
+        "batched_graph": {"ms": ms_graph, "strings_per_s": total / (ms_graph / 1e3),
+                          "latency_ms_every_set": ms_graph},
+        "batched_no_graph": {"ms": ms_nograph, "strings_per_s": total / (ms_nograph / 1e3)},
+        "plain_loop": {"ms": plain_s * 1e3, "strings_per_s": total / plain_s,
+                       "per_call_ms_p50": float(np.percentile(lat, 50)),
+                       "per_call_ms_p99": float(np.percentile(lat, 99)),
+                       "completion_ms_p50": float(np.percentile(np.cumsum(lat), 50)),
+                       "completion_ms_p99": float(np.percentile(np.cumsum(lat), 99))},
+        "speedup_vs_plain": plain_s * 1e3 / ms_graph,
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--sets", type=int, default=4096, help="number of sets (c4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n", type=int, default=None, help="reduced string count (c2 only; profiler captures)")
@@ -358,7 +442,10 @@ def main():
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), rank)
         return
     ws, rank, local = dist_init()
-    run_ours(args, ws, rank, local)
+    if args.config == "c4":
+        run_batch(args, ws, rank, local)
+    else:
+        run_ours(args, ws, rank, local)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
