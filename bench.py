@@ -425,13 +425,72 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ---- served workload (configuration 5) ----------------------------------------------------------
+
+def run_served(args, ws, rank, local):
+    """A Poisson stream of sort requests (log-uniform 1k..5M strings, mixed
+    generators) replayed against the serving loop (admission by a 30 GB HBM
+    budget, continuous batching on 4 streams) and against a one-at-a-time
+    plain loop on the same trace.  Arrival rate: 0.8 x the plain loop's
+    measured capacity."""
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    from paper_1808_00963_gb300.serve import Server, make_request
+    ss.load()
+    spec = gen.trace(args.requests, 5, 1.0, smin=1000, smax=5_000_000)
+    reqs = []
+    for i, (t, kind, size, sd) in enumerate(spec):
+        st = gen.make_set(kind, size, sd)
+        reqs.append(make_request(i, t, st.chars, st.offsets, st.max_len))
+    total = sum(r.n for r in reqs)
+
+    def reset(arrivals):
+        for r, a in zip(reqs, arrivals):
+            r.arrival, r.start, r.done, r.batch_size = a, -1.0, -1.0, 0
+
+    # warm-up and capacity of the plain loop (all requests available at once)
+    reset([0.0] * len(reqs))
+    Server(mode="plain").run(reqs)
+    reset([0.0] * len(reqs))
+    cap = Server(mode="plain").run(reqs)
+    capacity = cap["strings_per_s"]
+    reset([0.0] * len(reqs))
+    cap_served = Server(mode="served", budget_bytes=30 << 30, streams=4).run(reqs)
+    rate = 0.8 * capacity / (total / len(reqs))  # requests per second
+    arrivals = [t / rate for (t, _, _, _) in spec]
+    reset(arrivals)
+    plain = Server(mode="plain").run(reqs)
+    reset(arrivals)
+    served = Server(mode="served", budget_bytes=30 << 30, streams=4).run(reqs)
+    line = {
+        "metric": METRIC, "value": served["strings_per_s"], "unit": "strings/s", "n_gpus": ws, "steps": 1,
+        "warmup": 1, "ms_per_step": served["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"served: Poisson stream of {len(reqs)} sort requests, log-uniform 1k-5M strings, "
+                               "mixed generators, 30 GB HBM budget",
+                   "requests": len(reqs), "strings": total, "offered_load": 0.8,
+                   "plain_capacity_strings_per_s": capacity, "arrival_rate_per_s": rate,
+                   "per_step": "the whole trace; latency = completion (results on the host) - arrival"},
+        "served": served, "plain": plain,
+        "saturated": {"plain_strings_per_s": capacity, "served_strings_per_s": cap_served["strings_per_s"],
+                      "served_mean_batch": cap_served["mean_batch"],
+                      "throughput_ratio": cap_served["strings_per_s"] / capacity},
+        "p99_speedup": plain["latency_ms_p99"] / served["latency_ms_p99"],
+        "throughput_ratio": served["strings_per_s"] / plain["strings_per_s"],
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--requests", type=int, default=150, help="number of requests (c5)")
     ap.add_argument("--sets", type=int, default=4096, help="number of sets (c4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -444,6 +503,8 @@ def main():
     ws, rank, local = dist_init()
     if args.config == "c4":
         run_batch(args, ws, rank, local)
+    elif args.config == "c5":
+        run_served(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

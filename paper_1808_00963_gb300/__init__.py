@@ -268,7 +268,7 @@ class Batch:
     captured into a CUDA graph; ``status()`` waits and reports errors.
     """
 
-    def __init__(self, sets, **opts):
+    def __init__(self, sets, own_workspace: bool = False, **opts):
         self.lib = load()
         self.keep = sets
         arr = (SetDesc * max(1, len(sets)))()
@@ -281,6 +281,14 @@ class Batch:
             arr[i].out_lcp = l.data_ptr() if l is not None else None
         self.arr = arr
         self.opts = make_options(0, **opts)
+        self.work = None
+        if own_workspace:
+            # workspace from the caller's (torch's) allocator instead of the library's
+            import torch
+            nb = int(self.lib.ss_batch_workspace_size(arr, len(sets), ctypes.byref(self.opts)))
+            self.work = torch.empty(max(nb, 256), dtype=torch.uint8, device="cuda")
+            self.opts.workspace = self.work.data_ptr()
+            self.opts.workspace_bytes = nb
         h = ctypes.c_void_p()
         _check(self.lib.ss_batch_create(arr, len(sets), ctypes.byref(self.opts), ctypes.byref(h)),
                "ss_batch_create")

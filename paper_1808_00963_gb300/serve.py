@@ -1,0 +1,194 @@
+"""Serving loop for sort requests on one GPU.
+
+Requests (a host string set each) arrive over time.  They are admitted in
+arrival order while their device footprint (characters, offsets, outputs and
+workspace) fits the HBM budget; admitted requests keep their buffers on the
+device until they complete.  Continuous batching: each of several worker
+streams takes everything admitted so far (up to a cap) and sorts it as one
+batch (ss_batch_*), so requests that arrive while other batches are on the
+GPU are admitted as memory frees up and their work overlaps with the running
+batches on the device.  A request above ``big`` strings is sorted alone with
+the multi-block path (ss_sort_ex).  Results are copied back to pinned host
+memory before a request counts as complete.
+
+``mode="plain"`` is the one-at-a-time baseline: a single worker sorts one
+request after the other with ss_sort_ex, under the same admission rule.
+
+The sorting itself runs in the library's CUDA kernels; this module only
+schedules, allocates (through torch) and copies.
+"""
+from __future__ import annotations
+
+import collections
+import threading
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import Batch, sort, workspace_size
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float                 # seconds after the start of the run
+    chars: object                  # pinned torch.uint8 (host)
+    offsets: object                # pinned torch.int64 (host)
+    max_len: int = 0
+    n: int = 0
+    footprint: int = 0
+    start: float = -1.0
+    done: float = -1.0
+    batch_size: int = 0
+    perm: object = None            # pinned torch.int32 result (host)
+    lcp: object = None
+    meta: dict = field(default_factory=dict)
+
+
+def device_footprint(n: int, nchars: int, max_len: int = 0) -> int:
+    """Bytes a request holds on the device while admitted."""
+    return nchars + 16 + 8 * n + 8 * n + workspace_size(max(n, 1), max_len)
+
+
+def make_request(rid: int, arrival: float, chars: np.ndarray, offsets: np.ndarray, max_len: int = 0) -> Request:
+    import torch
+    ch = torch.from_numpy(np.ascontiguousarray(chars) if chars.size else np.zeros(1, np.uint8)).pin_memory()
+    of = torch.from_numpy(np.ascontiguousarray(offsets).view(np.int64)).pin_memory()
+    n = int(of.numel())
+    r = Request(rid, arrival, ch, of, max_len, n, device_footprint(n, int(ch.numel()), max_len))
+    r.perm = torch.empty(n, dtype=torch.int32).pin_memory()
+    r.lcp = torch.empty(n, dtype=torch.int32).pin_memory()
+    return r
+
+
+class Server:
+    def __init__(self, budget_bytes: int = 30 << 30, streams: int = 4, batch_max: int = 512,
+                 big: int = 65536, mode: str = "served"):
+        assert mode in ("served", "plain")
+        self.budget = budget_bytes
+        self.nstreams = 1 if mode == "plain" else streams
+        self.batch_max = 1 if mode == "plain" else batch_max
+        self.big = big
+        self.mode = mode
+        self.cv = threading.Condition()
+        self.pending = collections.deque()
+        self.admitted = collections.deque()
+        self.free = budget_bytes
+        self.arrivals_done = False
+        self.in_flight_peak = 0
+        self.in_flight = 0
+        self.errors = []
+
+    # -- scheduling (call with self.cv held) --------------------------------------------------
+    def _admit(self):
+        while self.pending and self.pending[0].footprint <= self.free:
+            r = self.pending.popleft()
+            self.free -= r.footprint
+            self.admitted.append(r)
+
+    def _take(self):
+        first = self.admitted.popleft()
+        group = [first]
+        if self.mode == "plain" or first.n > self.big:
+            return group
+        while self.admitted and len(group) < self.batch_max and self.admitted[0].n <= self.big:
+            group.append(self.admitted.popleft())
+        return group
+
+    # -- execution ---------------------------------------------------------------------------
+    def _process(self, group, stream, t0):
+        import torch
+        with torch.cuda.stream(stream):
+            now = time.perf_counter() - t0
+            dev = []
+            for r in group:
+                r.start = now
+                r.batch_size = len(group)
+                ch = torch.empty(r.chars.numel() + 16, dtype=torch.uint8, device="cuda")
+                ch[: r.chars.numel()].copy_(r.chars, non_blocking=True)
+                of = r.offsets.to("cuda", non_blocking=True)
+                p = torch.empty(r.n, dtype=torch.int32, device="cuda")
+                l = torch.empty(r.n, dtype=torch.int32, device="cuda")
+                dev.append((ch, of, r.max_len, p, l))
+            if len(group) == 1 and (self.mode == "plain" or group[0].n > self.big):
+                ch, of, ml, p, l = dev[0]
+                sort(ch, of, max_len=ml, out=(p, l), stream=stream)
+            else:
+                b = Batch(dev, own_workspace=True)
+                b.run(stream)
+                b.status(stream)
+                b.close()
+            for r, (_, _, _, p, l) in zip(group, dev):
+                r.perm.copy_(p, non_blocking=True)
+                r.lcp.copy_(l, non_blocking=True)
+            stream.synchronize()
+            now = time.perf_counter() - t0
+            for r in group:
+                r.done = now
+            del dev
+
+    def _worker(self, t0):
+        import torch
+        stream = torch.cuda.Stream()
+        while True:
+            with self.cv:
+                while True:
+                    self._admit()
+                    if self.admitted:
+                        group = self._take()
+                        self.in_flight += 1
+                        self.in_flight_peak = max(self.in_flight_peak, self.in_flight)
+                        break
+                    if self.arrivals_done and not self.pending:
+                        return
+                    self.cv.wait()
+            try:
+                self._process(group, stream, t0)
+            except Exception as e:  # report, never hang the loop
+                self.errors.append(repr(e))
+                for r in group:
+                    r.done = float("nan")
+            with self.cv:
+                self.free += sum(r.footprint for r in group)
+                self.in_flight -= 1
+                self.cv.notify_all()
+
+    def run(self, requests):
+        """Replays the requests at their arrival times; returns per-request
+        (arrival, start, done) and summary statistics."""
+        import torch
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        workers = [threading.Thread(target=self._worker, args=(t0,), daemon=True) for _ in range(self.nstreams)]
+        for w in workers:
+            w.start()
+        for r in sorted(requests, key=lambda x: x.arrival):
+            delay = r.arrival - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            with self.cv:
+                self.pending.append(r)
+                self.cv.notify_all()
+        with self.cv:
+            self.arrivals_done = True
+            self.cv.notify_all()
+        for w in workers:
+            w.join()
+        return summarize(requests, self)
+
+
+def summarize(requests, server=None):
+    lat = np.array([r.done - r.arrival for r in requests]) * 1e3
+    n = sum(r.n for r in requests)
+    span = max(r.done for r in requests) - min(r.arrival for r in requests)
+    out = {
+        "requests": len(requests), "strings": n,
+        "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+        "latency_ms_max": float(lat.max()), "strings_per_s": n / span, "span_s": span,
+        "mean_batch": float(np.mean([r.batch_size for r in requests])),
+    }
+    if server is not None:
+        out["peak_batches_in_flight"] = server.in_flight_peak
+        out["errors"] = server.errors
+    return out

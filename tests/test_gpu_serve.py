@@ -1,0 +1,58 @@
+"""The serving loop: requests admitted by HBM footprint and sorted in
+continuous batches on several streams give, for every request, exactly the
+result of sorting it alone (and the oracle's)."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(num, seed, rate, smax):
+    from paper_1808_00963_gb300.serve import make_request
+    out = []
+    for i, (t, kind, size, sd) in enumerate(gen.trace(num, seed, rate, smin=1000, smax=smax)):
+        s = gen.make_set(kind, size, sd)
+        r = make_request(i, t, s.chars, s.offsets, s.max_len)
+        r.meta["set"] = s
+        out.append(r)
+    return out
+
+
+@pytest.mark.parametrize("mode", ["served", "plain"])
+def test_each_result_same_alone_and_in_the_mix(mode):
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    from paper_1808_00963_gb300.serve import Server
+    reqs = _requests(36, 5, rate=3000.0, smax=60000)
+    srv = Server(budget_bytes=2 << 30, streams=3, batch_max=16, big=30000, mode=mode)
+    stats = srv.run(reqs)
+    assert not stats["errors"]
+    for r in reqs:
+        s = r.meta["set"]
+        gp = r.perm.numpy().view(np.uint32)
+        gl = r.lcp.numpy().view(np.uint32)
+        wp, wl = oracle.sort(s.chars, s.offsets, s.max_len)
+        assert np.array_equal(gp, wp) and np.array_equal(gl, wl), r.rid
+        # alone, on its own
+        ch = torch.from_numpy(s.chars).cuda()
+        of = torch.from_numpy(s.offsets.view(np.int64)).cuda()
+        p, l = ss.sort(ch, of, max_len=s.max_len)
+        assert np.array_equal(p.cpu().numpy().view(np.uint32), gp)
+        assert np.array_equal(l.cpu().numpy().view(np.uint32), gl)
+    if mode == "served":
+        assert stats["mean_batch"] > 1.0
+
+
+def test_admission_respects_budget():
+    from paper_1808_00963_gb300.serve import Server
+    reqs = _requests(12, 6, rate=1e6, smax=20000)
+    budget = max(r.footprint for r in reqs) + 1  # room for about one request at a time
+    srv = Server(budget_bytes=budget, streams=4, batch_max=8, big=10**9, mode="served")
+    stats = srv.run(reqs)
+    assert not stats["errors"]
+    assert srv.free == budget
+    assert all(r.done >= r.start >= 0 for r in reqs)
