@@ -34,6 +34,7 @@ import numpy as np  # noqa: E402
 import gen  # noqa: E402
 
 METRIC = "strings/s & D-bytes/s vs HBM roofline; batched/served vs plain p99 + throughput"
+KIND = {"c1": "random", "c2": "url", "c3": "dna"}
 CPU_SAMPLE = 2_000_000
 
 
@@ -245,9 +246,11 @@ def run_ours(args, ws, rank, local):
     n = s.n
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     lcp = torch.empty(n, dtype=torch.int32, device=dev)
-    wsb = ss.workspace_size(n, s.max_len)
+    from paper_1808_00963_gb300 import tune
+    tuned = {k: v for k, v in tune.options_for(KIND[args.config]).items() if v}
+    wsb = ss.workspace_size(n, s.max_len, **tuned)
     work = torch.empty(wsb, dtype=torch.uint8, device=dev)
-    opts = dict(workspace=work.data_ptr(), workspace_bytes=wsb)
+    opts = dict(workspace=work.data_ptr(), workspace_bytes=wsb, **tuned)
     stream = torch.cuda.current_stream()
 
     def step():
@@ -306,12 +309,12 @@ def run_ours(args, ws, rank, local):
         hoffs = torch.from_numpy(s.offsets.view(np.int64)).pin_memory()
         hperm = torch.empty(n, dtype=torch.int32).pin_memory()
         hlcp = torch.empty(n, dtype=torch.int32).pin_memory()
-        ss.sort_host(hchars, hoffs, s.max_len, perm=hperm, lcp=hlcp)
+        ss.sort_host(hchars, hoffs, s.max_len, perm=hperm, lcp=hlcp, **tuned)
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            ss.sort_host(hchars, hoffs, s.max_len, perm=hperm, lcp=hlcp)
+            ss.sort_host(hchars, hoffs, s.max_len, perm=hperm, lcp=hlcp, **tuned)
         torch.cuda.synchronize()
         et = max_over_ranks(time.perf_counter() - t0, ws)
         e2e = {"value": ws * n * args.steps / et, "unit": "strings/s",
@@ -330,7 +333,8 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": desc, "n": n, "N": s.N, "D": D, "L": L, "max_len": s.max_len,
                        "l2": f"inputs larger than L2 (characters {s.N / 1e9:.2f} GB, offsets {8 * n / 1e6:.0f} MB)",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "per_step": "one sort: permutation + LCP array"},
+                       "per_step": "one sort: permutation + LCP array",
+                       "options": tuned or "compiled defaults", "options_source": "autotuner table (tuned.json)"},
             "d_bytes_per_s": d_rate,
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -366,7 +370,9 @@ def run_batch(args, ws, rank, local):
     for i, st in enumerate(sets):
         a, b = int(first[i]), int(first[i]) + st.n
         descs.append((chars_d[int(cbase[i]):], offs_d[a:b], int(mls[i]), perm_d[a:b], lcp_d[a:b]))
-    batch = ss.Batch(descs)
+    from paper_1808_00963_gb300 import tune
+    tuned = {k: v for k, v in tune.options_for(batched=True).items() if v}
+    batch = ss.Batch(descs, **tuned)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
@@ -409,7 +415,8 @@ def run_batch(args, ws, rank, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": f"batched: {num} sets, log-uniform 100-200k strings, random/URL/DNA generators",
                    "sets": num, "strings": total, "chars_bytes": int(chars.shape[0]),
-                   "per_step": "one batch (all sets sorted, perm + LCP), CUDA graph replay"},
+                   "per_step": "one batch (all sets sorted, perm + LCP), CUDA graph replay",
+                   "options": tuned or "compiled defaults", "options_source": "autotuner table (tuned.json)"},
         "batched_graph": {"ms": ms_graph, "strings_per_s": total / (ms_graph / 1e3),
                           "latency_ms_every_set": ms_graph},
         "batched_no_graph": {"ms": ms_nograph, "strings_per_s": total / (ms_nograph / 1e3)},

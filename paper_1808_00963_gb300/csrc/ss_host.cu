@@ -24,6 +24,7 @@
 #include "../../include/ss_sort.h"
 #include "ss_kernels.h"
 #include "ss_step.cuh"
+#include "ss_tuned.h"
 
 namespace ss {
 
@@ -122,13 +123,14 @@ static ss_status device_info(DevInfo& out) {
 
 // ---- options and workspace layout -----------------------------------------------------
 
+// Defaults come from the autotuner's table (ss_tuned.h).
 struct Opts {
   uint32_t cap = kNoCap;
-  int logv = 8;        // single-block steps
-  int logv_big = 9;    // multi-block steps
-  uint32_t R = 0;      // 0 = choose per step
-  uint32_t cutoff = 1024;
-  uint32_t big_thr = 8192;
+  int logv = SS_TUNED_SPLITTERS_LOG2;           // single-block steps
+  int logv_big = SS_TUNED_BIG_SPLITTERS_LOG2;   // multi-block steps
+  uint32_t R = SS_TUNED_TILE_ROUNDS;            // 0 = choose per step
+  uint32_t cutoff = SS_TUNED_SMALL_CUTOFF;
+  uint32_t big_thr = SS_TUNED_BIG_THRESHOLD;
   uint32_t seed = 0x5EED;
   uint32_t mq_factor = 16;
 };
