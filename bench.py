@@ -40,17 +40,19 @@ CPU_SAMPLE = 2_000_000
 
 # ---- distributed plumbing ------------------------------------------------------------------
 
-def dist_init():
+def dist_init(backend: str = "nccl"):
+    """One process per GPU (torchrun sets RANK / LOCAL_RANK / WORLD_SIZE /
+    MASTER_*); the process group only carries the timing barrier and the
+    max-over-ranks reduction (gloo on CPU in the tests)."""
     import torch
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    if backend == "nccl":
+        torch.cuda.set_device(local if ws > 1 else 0)
     if ws > 1:
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        torch.cuda.set_device(0)
+        dist.init_process_group(backend)
     return ws, rank, local
 
 
@@ -65,9 +67,17 @@ def max_over_ranks(x, ws):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(local_ms: float, ws: int, units_per_rank: int, steps: int):
+    """(slowest rank's ms, whole-job units/s): every rank processes the same
+    number of units, the job takes as long as its slowest rank."""
+    ms = max_over_ranks(local_ms, ws)
+    return ms, ws * units_per_rank * steps / (ms / 1e3)
 
 
 # ---- clocks during the timed region ---------------------------------------------------------
@@ -279,12 +289,9 @@ def run_ours(args, ws, rank, local):
     barrier(ws)
     clocks = sampler.stop()
     ss.set_profiling(False)
-    ms = e0.elapsed_time(e1)
-    ms = max_over_ranks(ms, ws)
+    ms, value = weak_scaling_value(e0.elapsed_time(e1), ws, n, args.steps)
     stats = ss.kernel_stats()
-    secs = ms / 1e3
-    value = ws * n * args.steps / secs
-    d_rate = ws * D * args.steps / secs
+    d_rate = ws * D * args.steps / (ms / 1e3)
 
     # roofline of the dominant kernel (largest share of device time)
     peak, peak_kind = measured_peaks()

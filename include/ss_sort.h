@@ -142,6 +142,11 @@ ss_status ss_batch_run(ss_batch* b, void* stream);
  * ss_batch_run of this plan. */
 ss_status ss_batch_status(ss_batch* b, void* stream);
 
+/* Wait for `stream` and return the device status latched by the last
+ * ss_batch_run enqueued on it (SS_OK if none is known; ss_sort, ss_sort_ex
+ * and ss_sort_host return their status directly). */
+ss_status ss_stream_status(void* stream);
+
 /* Release a plan (and its workspace if the library allocated it). */
 ss_status ss_batch_destroy(ss_batch* b);
 

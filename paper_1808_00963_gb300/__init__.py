@@ -154,6 +154,8 @@ def load(path: str | None = None):
     lib.ss_kernel_stats.restype = u32
     lib.ss_reset_kernel_stats.argtypes = []
     lib.ss_reset_kernel_stats.restype = None
+    lib.ss_stream_status.argtypes = [vp]
+    lib.ss_stream_status.restype = i32
     lib.ss_sort_noalloc.argtypes = [vp, vp, u64, u32, vp, vp, vp]
     lib.ss_sort_noalloc.restype = i32
     if path is None:
@@ -299,6 +301,10 @@ class Batch:
 
     def status(self, stream=None):
         _check(self.lib.ss_batch_status(self.h, _stream_ptr(stream)), "ss_batch_status")
+
+    def stream_status(self, stream=None):
+        """ss_stream_status on the stream this batch last ran on."""
+        _check(self.lib.ss_stream_status(_stream_ptr(stream)), "ss_stream_status")
 
     def close(self):
         if self.h:

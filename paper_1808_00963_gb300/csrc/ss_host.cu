@@ -16,6 +16,7 @@
 #include <atomic>
 #include <cstdio>
 #include <cstring>
+#include <iterator>
 #include <map>
 #include <mutex>
 #include <string>
@@ -433,6 +434,10 @@ struct ss_batch {
 
 using namespace ss;
 
+// Last asynchronous run enqueued on each stream (for ss_stream_status).
+static std::mutex g_stream_mu;
+static std::map<void*, ss_batch*> g_stream_last;
+
 extern "C" {
 
 const char* ss_status_string(ss_status s) {
@@ -584,6 +589,10 @@ ss_status ss_batch_create(const ss_set* sets, uint32_t num_sets, const ss_option
 ss_status ss_batch_run(ss_batch* b, void* stream) {
   if (!b) return SS_ERR_INVALID;
   if (b->num_sets == 0) return SS_OK;
+  {
+    std::lock_guard<std::mutex> lk(g_stream_mu);
+    g_stream_last[stream] = b;
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SortCtx c = make_ctx(b->ws, b->L, b->num_sets, b->total, b->o, false);
   return run_sort(b->ws, b->L, c, b->o, b->dev, false, st);
@@ -597,9 +606,25 @@ ss_status ss_batch_status(ss_batch* b, void* stream) {
 
 ss_status ss_batch_destroy(ss_batch* b) {
   if (!b) return SS_ERR_INVALID;
+  {
+    std::lock_guard<std::mutex> lk(g_stream_mu);
+    for (auto it = g_stream_last.begin(); it != g_stream_last.end();)
+      it = (it->second == b) ? g_stream_last.erase(it) : std::next(it);
+  }
   if (b->owned) cudaFree(b->ws);
   delete b;
   return SS_OK;
+}
+
+ss_status ss_stream_status(void* stream) {
+  ss_batch* b = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_stream_mu);
+    auto it = g_stream_last.find(stream);
+    if (it != g_stream_last.end()) b = it->second;
+  }
+  if (b) return ss_batch_status(b, stream);
+  return cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) == cudaSuccess ? SS_OK : SS_ERR_CUDA;
 }
 
 ss_status ss_sort_batch(const ss_set* sets, uint32_t num_sets, const ss_options* opt, void* stream) {

@@ -103,7 +103,7 @@ def test_batch_per_set_caps():
     dev = _device_sets(sets)
     b = ss.Batch(dev)
     b.run()
-    b.status()
+    b.stream_status()
     _check(sets, dev)
     b.close()
 
