@@ -63,22 +63,12 @@ __global__ void __launch_bounds__(kBlock) k_big_classify(SortCtx c, const GenTas
   const uint32_t tl = min(T, g.t.len - t0);
   const uint64_t* keys = c.key[task_par(g.t)] + g.t.begin + t0;
   uint16_t* bo = c.bucket_of + g.t.begin + t0;
-  const uint32_t lim = (tl + kBlock - 1) / kBlock * kBlock;
-  for (uint32_t p = threadIdx.x; p < lim; p += kBlock) {
-    const bool valid = p < tl;
-    uint32_t b = 0xFFFFu;
-    if (valid) {
-      b = classify<LOGV>(keys[p], tree, x);
-      bo[p] = (uint16_t)b;
-    }
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
-    if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
-  }
+  const uint32_t mine = classify_count<LOGV>(keys, bo, tl, tree, x, hist);
   __syncthreads();
   uint32_t* cnt = counters + cnt_base(g) + tile;
   for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) cnt[(uint64_t)b * g.tiles] = hist[b];
   // per record: cache 8 read + bucket index 2 written; per tile: K counters written
-  unsigned long long bytes = 10ull * ((tl > threadIdx.x) ? (tl - threadIdx.x + kBlock - 1) / kBlock : 0);
+  unsigned long long bytes = 10ull * mine;
   if (threadIdx.x == 0) bytes += 4ull * Gm::K;
   account(c, kKBigClassify, bytes);
 }

@@ -150,6 +150,60 @@ __device__ __forceinline__ uint64_t load_cache(const uint8_t* chars, uint64_t of
   return bswap64(v);
 }
 
+constexpr int kLookWindows = 8;  // look-ahead: 8 windows = 64 characters per round
+
+// Look-ahead read for the refinement of long common prefixes: the KW windows
+// of 8 characters at depths h, h + 8, ..., h + 8(KW-1) (first character most
+// significant, zero at/after the terminator or the cap).  Precondition: the
+// string has no terminator before h, so the byte at h belongs to the string
+// (or is its terminator).  All KW + 1 aligned words are issued at once, but
+// only words inside the 4 KiB-aligned block that holds byte h are read: memory
+// is mapped in blocks of at least 4 KiB, so these reads cannot fault, and bytes
+// past the terminator are discarded.  Returns how many leading windows are
+// fully determined (windows past the block, before a terminator was seen, are
+// not).
+template <int KW>
+__device__ __forceinline__ uint32_t load_windows(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
+                                                 uint64_t (&w)[KW]) {
+#pragma unroll
+  for (int j = 0; j < KW; ++j) w[j] = 0;
+  if (h >= cap) return KW;
+  const uintptr_t a = (uintptr_t)(chars + off + h);
+  const uintptr_t blk_end = (a & ~(uintptr_t)4095) + 4096;
+  const uintptr_t p0 = a & ~(uintptr_t)7;
+  const uint32_t sh = (uint32_t)(a & 7);
+  uint64_t word[KW + 1];
+#pragma unroll
+  for (int i = 0; i <= KW; ++i) {
+    const uintptr_t q = p0 + 8 * (uintptr_t)i;
+    word[i] = q < blk_end ? __ldg(reinterpret_cast<const uint64_t*>(q)) : 0ull;
+  }
+  const uint64_t known_total = (uint64_t)(blk_end - a);  // bytes from h that may be read (>= 1)
+  const uint64_t room_total = (uint64_t)cap - h;         // bytes from h before the cap (>= 1)
+  uint32_t nwin = KW;
+  bool ended = false;
+#pragma unroll
+  for (int j = 0; j < KW; ++j) {
+    if (ended || (uint32_t)j >= nwin) continue;
+    uint64_t v = sh ? ((word[j] >> (8 * sh)) | (word[j + 1] << (64 - 8 * sh))) : word[j];
+    const uint64_t ws = 8ull * j;
+    const uint32_t known = known_total > ws ? (known_total - ws >= 8 ? 8u : (uint32_t)(known_total - ws)) : 0u;
+    const uint32_t room = room_total > ws ? (room_total - ws >= 8 ? 8u : (uint32_t)(room_total - ws)) : 0u;
+    const uint32_t z = first_zero_byte(known < 8 ? (v | (~0ull << (8 * known))) : v);
+    if (z < known || room <= known) {
+      const uint32_t keep = z < room ? z : room;
+      if (keep < 8) {
+        v &= keep ? (~0ull >> (64 - 8 * keep)) : 0ull;
+        ended = true;
+      }
+      w[j] = bswap64(v);
+    } else {
+      nwin = (uint32_t)j;  // bytes past the block decide this window
+    }
+  }
+  return nwin;
+}
+
 // Length of the common prefix of two caches, in characters (8 if equal).
 __device__ __forceinline__ uint32_t lcp8(uint64_t a, uint64_t b) {
   uint64_t x = a ^ b;

@@ -113,18 +113,7 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
   for (uint32_t b = threadIdx.x; b < Gm::KP; b += kBlock) s.hist[b] = 0;
   __syncthreads();
   uint16_t* bo = c.bucket_of + t.begin;
-  const uint32_t lim = (t.len + kBlock - 1) / kBlock * kBlock;
-  for (uint32_t p = threadIdx.x; p < lim; p += kBlock) {
-    const bool valid = p < t.len;
-    uint32_t b = 0xFFFFu;
-    if (valid) {
-      b = classify<LOGV>(keys[p], s.sp.tree, s.sp.x);
-      bo[p] = (uint16_t)b;
-      bytes += 10;
-    }
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
-    if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&s.hist[b], (uint32_t)__popc(peers));
-  }
+  bytes += 10ull * classify_count<LOGV>(keys, bo, t.len, s.sp.tree, s.sp.x, s.hist);
   __syncthreads();
 
   // line 15: prefix sum; bucket outcomes

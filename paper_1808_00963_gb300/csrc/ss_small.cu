@@ -85,60 +85,6 @@ __device__ __forceinline__ void warp_sort(uint32_t& seg, uint64_t& key, uint32_t
   }
 }
 
-constexpr int kLookWindows = 8;  // look-ahead: 8 windows = 64 characters per round
-
-// Look-ahead read for the refinement of long common prefixes: the KW windows
-// of 8 characters at depths h, h + 8, ..., h + 8(KW-1) (first character most
-// significant, zero at/after the terminator or the cap).  Precondition: the
-// string has no terminator before h, so the byte at h belongs to the string
-// (or is its terminator).  All KW + 1 aligned words are issued at once, but
-// only words inside the 4 KiB-aligned block that holds byte h are read: memory
-// is mapped in blocks of at least 4 KiB, so these reads cannot fault, and bytes
-// past the terminator are discarded.  Returns how many leading windows are
-// fully determined (windows past the block, before a terminator was seen, are
-// not).
-template <int KW>
-__device__ __forceinline__ uint32_t load_windows(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
-                                                 uint64_t (&w)[KW]) {
-#pragma unroll
-  for (int j = 0; j < KW; ++j) w[j] = 0;
-  if (h >= cap) return KW;
-  const uintptr_t a = (uintptr_t)(chars + off + h);
-  const uintptr_t blk_end = (a & ~(uintptr_t)4095) + 4096;
-  const uintptr_t p0 = a & ~(uintptr_t)7;
-  const uint32_t sh = (uint32_t)(a & 7);
-  uint64_t word[KW + 1];
-#pragma unroll
-  for (int i = 0; i <= KW; ++i) {
-    const uintptr_t q = p0 + 8 * (uintptr_t)i;
-    word[i] = q < blk_end ? __ldg(reinterpret_cast<const uint64_t*>(q)) : 0ull;
-  }
-  const uint64_t known_total = (uint64_t)(blk_end - a);  // bytes from h that may be read (>= 1)
-  const uint64_t room_total = (uint64_t)cap - h;         // bytes from h before the cap (>= 1)
-  uint32_t nwin = KW;
-  bool ended = false;
-#pragma unroll
-  for (int j = 0; j < KW; ++j) {
-    if (ended || (uint32_t)j >= nwin) continue;
-    uint64_t v = sh ? ((word[j] >> (8 * sh)) | (word[j + 1] << (64 - 8 * sh))) : word[j];
-    const uint64_t ws = 8ull * j;
-    const uint32_t known = known_total > ws ? (known_total - ws >= 8 ? 8u : (uint32_t)(known_total - ws)) : 0u;
-    const uint32_t room = room_total > ws ? (room_total - ws >= 8 ? 8u : (uint32_t)(room_total - ws)) : 0u;
-    const uint32_t z = first_zero_byte(known < 8 ? (v | (~0ull << (8 * known))) : v);
-    if (z < known || room <= known) {
-      const uint32_t keep = z < room ? z : room;
-      if (keep < 8) {
-        v &= keep ? (~0ull >> (64 - 8 * keep)) : 0ull;
-        ended = true;
-      }
-      w[j] = bswap64(v);
-    } else {
-      nwin = (uint32_t)j;  // bytes past the block decide this window
-    }
-  }
-  return nwin;
-}
-
 // Finishes the subsets ("groups") held by a warp, one string per lane.  Lanes
 // [g0, g0 + glen) hold one group: strings with a common prefix of their
 // `depth` characters, in ascending index order, with key = their cache at that
@@ -302,6 +248,8 @@ __device__ __forceinline__ uint32_t make_tag(uint32_t seg, uint32_t pos, uint32_
 
 struct CtaSmem {  // carved from dynamic shared memory, pmax elements
   uint64_t* key;    // cache, in sorted position
+  uint64_t* key2;   // second buffer of the merge sort
+  uint32_t* tag2;
   uint64_t* off;    // string offset, by original position
   uint32_t* tag;    // in sorted position
   uint32_t* idx;    // index, by original position
@@ -309,41 +257,84 @@ struct CtaSmem {  // carved from dynamic shared memory, pmax elements
   uint16_t* nseg;   // segment start of each position
 };
 
-__device__ __forceinline__ void cmp_swap(const CtaSmem& m, uint32_t lo, uint32_t hi) {
-  const uint64_t ka = m.key[lo], kb = m.key[hi];
-  const uint32_t ta = m.tag[lo], tb = m.tag[hi];
+// Order of the block sort: (segment, cache, tag).
+__device__ __forceinline__ bool elem_less(uint64_t ka, uint32_t ta, uint64_t kb, uint32_t tb) {
   const uint32_t sa = tag_seg(ta), sb = tag_seg(tb);
-  const bool gt = sa > sb || (sa == sb && (ka > kb || (ka == kb && ta > tb)));
-  if (gt) {
-    m.key[lo] = kb; m.key[hi] = ka;
-    m.tag[lo] = tb; m.tag[hi] = ta;
-  }
+  return sa < sb || (sa == sb && (ka < kb || (ka == kb && ta < tb)));
 }
 
-// Ascending bitonic sort of positions [0, n) where every comparator points the
-// same way (the first step of each merge compares mirrored positions), so a
-// comparator whose upper position is >= n can be skipped: it would compare
-// against +infinity.
-__device__ void block_sort(const CtaSmem& m, uint32_t n) {
-  uint32_t P = 2;
-  while (P < n) P <<= 1;
-  for (uint32_t k = 2, lh = 0; k <= P; k <<= 1, ++lh) {
-    const uint32_t h = k >> 1;  // = 1 << lh
-    for (uint32_t i = threadIdx.x; i < P / 2; i += kBlock) {
-      const uint32_t blk = (i >> lh) << (lh + 1);
-      const uint32_t r = i & (h - 1);
-      const uint32_t hi = blk + k - 1 - r;
-      if (hi < n) cmp_swap(m, blk + r, hi);
+// Stable block merge sort of (key, tag) at positions [0, n), n <= pmax.
+// Each thread first sorts its own chunk of ipt positions (insertion sort);
+// then every merge pass doubles the run length, each thread producing ipt
+// outputs of one merged pair of runs: it finds where its outputs start with a
+// binary search along the merge path and merges sequentially.  Uses
+// (key2, tag2) as the second buffer; the result ends in (m.key, m.tag).
+__device__ void block_sort(CtaSmem& m, uint32_t n) {
+  uint32_t ipt = 1;
+  while (ipt * kBlock < n) ipt <<= 1;
+  {
+    const uint32_t a = threadIdx.x * ipt;
+    const uint32_t e = min(n, a + ipt);
+    for (uint32_t i = a + 1; i < e; ++i) {
+      const uint64_t k = m.key[i];
+      const uint32_t t = m.tag[i];
+      uint32_t j = i;
+      while (j > a && elem_less(k, t, m.key[j - 1], m.tag[j - 1])) {
+        m.key[j] = m.key[j - 1];
+        m.tag[j] = m.tag[j - 1];
+        --j;
+      }
+      m.key[j] = k;
+      m.tag[j] = t;
+    }
+  }
+  __syncthreads();
+  uint64_t* sk = m.key;
+  uint32_t* st = m.tag;
+  uint64_t* dk = m.key2;
+  uint32_t* dt = m.tag2;
+  for (uint32_t run = ipt; run < n; run <<= 1) {
+    const uint32_t out = threadIdx.x * ipt;
+    if (out < n) {
+      const uint32_t base = (out / (2 * run)) * (2 * run);
+      const uint32_t la = min(run, n - base);
+      const uint32_t lb = base + run < n ? min(run, n - base - run) : 0u;
+      const uint64_t* ak = sk + base;
+      const uint32_t* at = st + base;
+      const uint64_t* bk = sk + base + run;
+      const uint32_t* bt = st + base + run;
+      const uint32_t d = out - base;
+      uint32_t lo = d > lb ? d - lb : 0u, hi = min(d, la);
+      while (lo < hi) {  // number of A elements among the first d outputs
+        const uint32_t mid = (lo + hi) >> 1;
+        if (!elem_less(bk[d - mid - 1], bt[d - mid - 1], ak[mid], at[mid])) lo = mid + 1;
+        else hi = mid;
+      }
+      uint32_t i = lo, j = d - lo;
+      const uint32_t cnt = min(ipt, n - out);
+      for (uint32_t q = 0; q < cnt; ++q) {
+        const bool take_a = i < la && (j >= lb || !elem_less(bk[j], bt[j], ak[i], at[i]));
+        if (take_a) {
+          dk[out + q] = ak[i];
+          dt[out + q] = at[i];
+          ++i;
+        } else {
+          dk[out + q] = bk[j];
+          dt[out + q] = bt[j];
+          ++j;
+        }
+      }
     }
     __syncthreads();
-    for (uint32_t j = h >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < P / 2; i += kBlock) {
-        const uint32_t lo = 2 * i - (i & (j - 1));
-        const uint32_t hi = lo + j;
-        if (hi < n) cmp_swap(m, lo, hi);
-      }
-      __syncthreads();
+    uint64_t* tk = sk; sk = dk; dk = tk;
+    uint32_t* tt = st; st = dt; dt = tt;
+  }
+  if (sk != m.key) {
+    for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+      m.key[j] = sk[j];
+      m.tag[j] = st[j];
     }
+    __syncthreads();
   }
 }
 
@@ -387,9 +378,11 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
   extern __shared__ __align__(16) uint8_t smem[];
   CtaSmem m;
   m.key = reinterpret_cast<uint64_t*>(smem);
-  m.off = m.key + pmax;
+  m.key2 = m.key + pmax;
+  m.off = m.key2 + pmax;
   m.tag = reinterpret_cast<uint32_t*>(m.off + pmax);
-  m.idx = m.tag + pmax;
+  m.tag2 = m.tag + pmax;
+  m.idx = m.tag2 + pmax;
   m.aux = m.idx + pmax;
   m.nseg = reinterpret_cast<uint16_t*>(m.aux + pmax);
   __shared__ uint32_t s_max_open, s_jstop, s_neq;
@@ -545,7 +538,7 @@ __global__ void __launch_bounds__(kBlock) k_lcp_fix(SortCtx c) {
 
 }  // namespace
 
-size_t small_cta_smem(uint32_t pmax) { return (size_t)pmax * (8 + 8 + 4 + 4 + 4 + 2); }
+size_t small_cta_smem(uint32_t pmax) { return (size_t)pmax * (8 + 8 + 8 + 4 + 4 + 4 + 4 + 2); }
 
 cudaError_t launch_init(const SortCtx& c, cudaStream_t st, const LaunchHook& hook) {
   const uint32_t grid = max(1u, min((c.total + kBlock - 1) / kBlock, 152u * 16u));

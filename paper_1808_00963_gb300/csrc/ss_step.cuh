@@ -127,6 +127,42 @@ __device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, c
   return 2 * r + ((r < Geo<LOGV>::V && x[r] == c) ? 1u : 0u);
 }
 
+// Classifies n keys (lines 6-14 of Algorithm 4.1): writes the bucket of
+// keys[p] to bo[p] and counts it in hist (shared memory, warp-aggregated
+// atomics).  Each thread loads 8 keys before descending the tree for them,
+// so that the loads of a batch overlap.  Returns this thread's records.
+template <int LOGV>
+__device__ __forceinline__ uint32_t classify_count(const uint64_t* __restrict__ keys, uint16_t* __restrict__ bo,
+                                                   uint32_t n, const uint64_t* tree, const uint64_t* x,
+                                                   uint32_t* hist) {
+  constexpr int U = 8;
+  uint32_t mine = 0;
+  const uint32_t lim = (n + kBlock - 1) / kBlock * kBlock;
+  for (uint32_t p0 = threadIdx.x; p0 < lim; p0 += U * kBlock) {
+    uint64_t k[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t p = p0 + u * kBlock;
+      k[u] = p < n ? keys[p] : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const uint32_t p = p0 + u * kBlock;
+      if (p >= lim) break;  // uniform across the block
+      const bool valid = p < n;
+      uint32_t b = 0xFFFFu;
+      if (valid) {
+        b = classify<LOGV>(k[u], tree, x);
+        bo[p] = (uint16_t)b;
+        ++mine;
+      }
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
+      if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
+    }
+  }
+  return mine;
+}
+
 // What happens to bucket b of a step at depth h (Output of Algorithm 4.1 and
 // Section 4.2.3): an even bucket b_{2r} continues at depth h + h'_r, an
 // equality bucket at h + 8, unless its splitter holds the terminator (then all
