@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(kBlock) k_big_sample(SortCtx c, const GenTask*
   __shared__ __align__(16) Splitters<LOGV> sp;
   __shared__ __align__(16) BuildScratch<LOGV> bs;
   const GenTask g = gt[blockIdx.x];
-  const uint64_t* keys = c.key[task_par(g.t)] + g.t.begin;
-  build_splitters<LOGV>(keys, g.t.len, mix64(c.seed ^ ((uint64_t)g.t.begin << 20) ^ g.t.depth), sp, bs);
+  const Rec* recs = c.rec[task_par(g.t)] + g.t.begin;
+  build_splitters<LOGV>(recs, g.t.len, mix64(c.seed ^ ((uint64_t)g.t.begin << 20) ^ g.t.depth), sp, bs);
   const uint64_t* src = reinterpret_cast<const uint64_t*>(&sp);
   uint64_t* dst = reinterpret_cast<uint64_t*>(out + blockIdx.x);
   for (uint32_t i = threadIdx.x; i < sizeof(Splitters<LOGV>) / 8; i += blockDim.x) dst[i] = src[i];
@@ -61,9 +61,9 @@ __global__ void __launch_bounds__(kBlock) k_big_classify(SortCtx c, const GenTas
   const uint32_t T = kBlock * R;
   const uint32_t t0 = tile * T;
   const uint32_t tl = min(T, g.t.len - t0);
-  const uint64_t* keys = c.key[task_par(g.t)] + g.t.begin + t0;
+  const Rec* recs = c.rec[task_par(g.t)] + g.t.begin + t0;
   uint16_t* bo = c.bucket_of + g.t.begin + t0;
-  const uint32_t mine = classify_count<LOGV>(keys, bo, tl, tree, x, hist);
+  const uint32_t mine = classify_count<LOGV>(recs, bo, tl, tree, x, hist);
   __syncthreads();
   uint32_t* cnt = counters + cnt_base(g) + tile;
   for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) cnt[(uint64_t)b * g.tiles] = hist[b];
@@ -135,10 +135,11 @@ __global__ void __launch_bounds__(kBlock) k_big_scatter(SortCtx c, const GenTask
   __syncthreads();
   const uint32_t src0 = g.t.begin + t0;
   const uint32_t depth = g.t.depth;
+  const uint32_t wide = c.wide[task_set(g.t)];
   unsigned long long bytes = threadIdx.x == 0 ? 12ull * Gm::K : 0ull;  // per-bucket tile offsets
   tile_scatter<LOGV>(tb, tl, R, base, cntw, [&](const uint32_t(&pp)[kMoveBatch], const uint32_t(&bb)[kMoveBatch],
                                                 const uint32_t(&dd)[kMoveBatch]) {
-    bytes += move_batch(c, sd, par, src0, depth, desc, [&](uint32_t b) { return bfirst[b]; }, pp, bb, dd);
+    bytes += move_batch(c, sd, wide, par, src0, depth, desc, [&](uint32_t b) { return bfirst[b]; }, pp, bb, dd);
   });
   account(c, kKBigScatter, bytes);
 }

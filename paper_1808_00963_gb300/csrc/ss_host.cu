@@ -178,7 +178,7 @@ enum Ctrl : uint32_t { kCStatus = 0, kCBig0 = 1, kCBig1 = 2, kCHead = 3, kCTail 
                        kCSmallW = 6, kCSmallC = 7 };
 
 struct Layout {
-  size_t ctrl, sets, key0, key1, idx0, idx1, bucket_of, big0, big1, gen, spl, counters, partials, gstart, gdesc,
+  size_t ctrl, sets, wide, rec0, rec1, bucket_of, big0, big1, gen, spl, counters, partials, gstart, gdesc,
       mq_items, mq_ready, sw_items, sc_items, total;
   uint32_t cap_big, cap_mq, cap_sw, cap_sc;
   uint64_t ncounters_max;
@@ -197,10 +197,9 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   L.ncounters_max = big ? KP * (tiles_max + L.cap_big) : 0;
   L.ctrl = take(kCtrlBytes);
   L.sets = take((size_t)num_sets * sizeof(SetDesc));
-  L.key0 = take(M * 8);
-  L.key1 = take(M * 8);
-  L.idx0 = take(M * 4);
-  L.idx1 = take(M * 4);
+  L.wide = take((size_t)num_sets * 4);
+  L.rec0 = take(M * sizeof(Rec));
+  L.rec1 = take(M * sizeof(Rec));
   L.bucket_of = take(M * 2);
   L.big0 = take((size_t)L.cap_big * sizeof(Task));
   L.big1 = take((size_t)L.cap_big * sizeof(Task));
@@ -224,10 +223,9 @@ static SortCtx make_ctx(uint8_t* ws, const Layout& L, uint32_t num_sets, uint32_
   c.sets = reinterpret_cast<const SetDesc*>(ws + L.sets);
   c.num_sets = num_sets;
   c.total = total;
-  c.key[0] = reinterpret_cast<uint64_t*>(ws + L.key0);
-  c.key[1] = reinterpret_cast<uint64_t*>(ws + L.key1);
-  c.idx[0] = reinterpret_cast<uint32_t*>(ws + L.idx0);
-  c.idx[1] = reinterpret_cast<uint32_t*>(ws + L.idx1);
+  c.wide = reinterpret_cast<uint32_t*>(ws + L.wide);
+  c.rec[0] = reinterpret_cast<Rec*>(ws + L.rec0);
+  c.rec[1] = reinterpret_cast<Rec*>(ws + L.rec1);
   c.bucket_of = reinterpret_cast<uint16_t*>(ws + L.bucket_of);
   c.status = ctrl + kCStatus;
   c.abytes = reinterpret_cast<unsigned long long*>(ctrl + kCtrlWords);
@@ -284,6 +282,7 @@ static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o
   const LaunchHook hook{st};
   SS_CUDA(cudaMemsetAsync(ws + L.ctrl, 0, kCtrlBytes, st));
   SS_CUDA(cudaMemsetAsync(ws + L.mq_ready, 0, (size_t)L.cap_mq * 4, st));
+  SS_CUDA(cudaMemsetAsync(ws + L.wide, 0, (size_t)c.num_sets * 4, st));
   SS_CUDA(launch_init(c, st, hook));
   if (big) {
     if (t_down.reserve(64 + (size_t)L.cap_big * sizeof(Task)) != SS_OK) return SS_ERR_OOM;

@@ -1,9 +1,10 @@
 // Internal definitions shared by the CUDA translation units of ss_sort.
 //
-// Records: every string that is still being sorted is one record
-// (key, idx) in structure-of-arrays form: key is the string's 8-byte character
-// cache at its subset's current depth (chars_h of Algorithm 4.1, first
-// character in the most significant byte), idx its index in its set.  Records
+// Records: every string that is still being sorted is one 16-byte record
+// (key, idx, off): key is the string's 8-byte character cache at its subset's
+// current depth (chars_h of Algorithm 4.1, first character in the most
+// significant byte), idx its index in its set, off the low 32 bits of its
+// offset (the whole offset unless the set has offsets of 2^32 or more).  Records
 // of one subset ("task") sit contiguously at [begin, begin + len) in one of
 // two record buffers; a distribution step moves them to the same range of the
 // other buffer (out-of-place redistribution with alternating roles,
@@ -36,6 +37,22 @@ struct SetDesc {
   uint32_t base;     // first record position of this set
   uint32_t pad;
 };
+
+// One string being sorted (moved with one 16-byte load and store).
+struct __align__(16) Rec {
+  uint64_t key;
+  uint32_t idx;
+  uint32_t off;
+};
+
+__device__ __forceinline__ Rec load_rec(const Rec* p) {
+  const uint4 v = *reinterpret_cast<const uint4*>(p);
+  return Rec{((uint64_t)v.y << 32) | v.x, v.z, v.w};
+}
+
+__device__ __forceinline__ void store_rec(Rec* p, uint64_t key, uint32_t idx, uint32_t off) {
+  *reinterpret_cast<uint4*>(p) = make_uint4((uint32_t)key, (uint32_t)(key >> 32), idx, off);
+}
 
 // A subset of records with a common prefix of `depth` characters.
 struct Task {
@@ -88,8 +105,8 @@ struct SortCtx {
   const SetDesc* sets;
   uint32_t num_sets;
   uint32_t total;          // records over all sets
-  uint64_t* key[2];
-  uint32_t* idx[2];
+  Rec* rec[2];
+  uint32_t* wide;          // per set: 1 if some offset is 2^32 or more (then off is not enough)
   uint16_t* bucket_of;     // bucket index of each record (array o of Algorithm 4.1)
   uint32_t* status;
   unsigned long long* abytes;  // [kKClasses] algorithmic bytes moved, per kernel class
@@ -202,6 +219,11 @@ __device__ __forceinline__ uint32_t load_windows(const uint8_t* chars, uint64_t 
     }
   }
   return nwin;
+}
+
+// Offset of a record's string.
+__device__ __forceinline__ uint64_t rec_offset(const SetDesc& sd, uint32_t wide, uint32_t idx, uint32_t off) {
+  return wide ? sd.offsets[idx] : (uint64_t)off;
 }
 
 // Length of the common prefix of two caches, in characters (8 if equal).

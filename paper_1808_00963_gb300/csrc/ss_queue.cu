@@ -105,15 +105,16 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
   using Gm = Geo<LOGV>;
   const SetDesc sd = c.sets[task_set(t)];
   const uint32_t par = task_par(t);
-  const uint64_t* keys = c.key[par] + t.begin;
-  build_splitters<LOGV>(keys, t.len, mix64(c.seed ^ ((uint64_t)t.begin << 20) ^ t.depth), s.sp, s.u.bs);
+  const Rec* recs = c.rec[par] + t.begin;
+  const uint32_t wide = c.wide[task_set(t)];
+  build_splitters<LOGV>(recs, t.len, mix64(c.seed ^ ((uint64_t)t.begin << 20) ^ t.depth), s.sp, s.u.bs);
   unsigned long long bytes = threadIdx.x == 0 ? Gm::S * 8ull : 0ull;
 
   // lines 6-14: classify into the array o and count
   for (uint32_t b = threadIdx.x; b < Gm::KP; b += kBlock) s.hist[b] = 0;
   __syncthreads();
   uint16_t* bo = c.bucket_of + t.begin;
-  bytes += 10ull * classify_count<LOGV>(keys, bo, t.len, s.sp.tree, s.sp.x, s.hist);
+  bytes += 10ull * classify_count<LOGV>(recs, bo, t.len, s.sp.tree, s.sp.x, s.hist);
   __syncthreads();
 
   // line 15: prefix sum; bucket outcomes
@@ -135,7 +136,7 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
     tile_scatter<LOGV>(s.u.sc.tb, tl, R, s.hist, s.u.sc.cntw,
                        [&](const uint32_t(&pp)[kMoveBatch], const uint32_t(&bb)[kMoveBatch],
                            const uint32_t(&dd)[kMoveBatch]) {
-                         bytes += move_batch(c, sd, par, src0, t.depth, s.desc,
+                         bytes += move_batch(c, sd, wide, par, src0, t.depth, s.desc,
                                              [&](uint32_t b) { return t.begin + s.bstart[b]; }, pp, bb, dd);
                        });
   }

@@ -35,9 +35,10 @@ __global__ void __launch_bounds__(kBlock) k_init(SortCtx c) {
     const uint32_t s = c.num_sets == 1 ? 0 : find_set(c, r);
     const SetDesc sd = c.sets[s];
     const uint32_t i = r - sd.base;
-    c.idx[0][r] = i;
-    c.key[0][r] = load_cache(sd.chars, sd.offsets[i], 0, sd.cap);
-    bytes += 28;  // offset 8 + 8 characters read, cache 8 + index 4 written
+    const uint64_t off = sd.offsets[i];
+    if ((off >> 32) && !c.wide[s]) atomicOr(c.wide + s, 1u);
+    store_rec(c.rec[0] + r, load_cache(sd.chars, off, 0, sd.cap), i, (uint32_t)off);
+    bytes += 32;  // offset 8 + 8 characters read, record 16 written
   }
   account(c, kKInit, bytes);
 }
@@ -214,9 +215,10 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
         const SetDesc sd = c.sets[tmeta & 0x7FFFFFFFu];
         const uint32_t par = tmeta >> 31;
         const uint32_t e = lane - g0;
-        key = c.key[par][tb + e];
-        id = c.idx[par][tb + e];
-        off = sd.offsets[id];
+        const Rec r = load_rec(c.rec[par] + tb + e);
+        key = r.key;
+        id = r.idx;
+        off = rec_offset(sd, c.wide[tmeta & 0x7FFFFFFFu], r.idx, r.off);
         cap = sd.cap;
         chars = sd.chars;
         lcp_g = sd.lcp ? sd.lcp + (tb - sd.base) : nullptr;
@@ -226,7 +228,7 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
                                        bytes);
       if (active) {
         perm[lane - g0] = fin;
-        bytes += lcp_g ? 28 : 24;  // cache 8 + index 4 + offset 8 read; perm 4 (+ lcp 4) written
+        bytes += lcp_g ? 24 : 20;  // record 16 read; perm 4 (+ lcp 4) written
       }
     });
   }
@@ -394,11 +396,12 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
     const SetDesc sd = c.sets[task_set(t)];
     const uint32_t par = task_par(t);
     const uint32_t n = t.len;
+    const uint32_t wide = c.wide[task_set(t)];
     for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
-      const uint32_t id = c.idx[par][t.begin + j];
-      m.key[j] = c.key[par][t.begin + j];
-      m.idx[j] = id;
-      m.off[j] = sd.offsets[id];
+      const Rec r = load_rec(c.rec[par] + t.begin + j);
+      m.key[j] = r.key;
+      m.idx[j] = r.idx;
+      m.off[j] = rec_offset(sd, wide, r.idx, r.off);
       m.tag[j] = make_tag(0, j, 1);
     }
     uint32_t* lcp = sd.lcp ? sd.lcp + (t.begin - sd.base) : nullptr;
@@ -479,9 +482,8 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
           } else if (size <= 32) {
             open = 0;
             handed = kHanded;
-            c.key[par][t.begin + j] = m.key[j];
-            c.idx[par][t.begin + j] = m.idx[tag_pos(tg)];
-            bytes += 12;
+            store_rec(c.rec[par] + t.begin + j, m.key[j], m.idx[tag_pos(tg)], (uint32_t)m.off[tag_pos(tg)]);
+            bytes += 16;
             if (j == s0) list_push(c.small_warp, Task{t.begin + j, size, depth, t.meta}, c.status);
           } else {
             atomicMax(&s_max_open, size);
@@ -506,7 +508,7 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
     for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
       const uint32_t tg = m.tag[j];
       if (!(tg & kHanded)) sd.perm[t.begin - sd.base + j] = m.idx[tag_pos(tg)];
-      bytes += sd.lcp ? 28 : 24;  // cache 8 + index 4 + offset 8 read; perm 4 (+ lcp 4) written
+      bytes += sd.lcp ? 24 : 20;  // record 16 read; perm 4 (+ lcp 4) written
     }
     __syncthreads();
   }

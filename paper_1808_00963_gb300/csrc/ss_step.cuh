@@ -68,13 +68,13 @@ __device__ void block_bitonic_u64(uint64_t* a) {
 // end, which keeps t a search tree.  Finally h'_i = lcp(x_{i-1}, x_i) with
 // h'_0 = h'_v = 0 (line 5).  Ends with __syncthreads().
 template <int LOGV>
-__device__ void build_splitters(const uint64_t* __restrict__ keys, uint32_t len, uint64_t hseed,
+__device__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint64_t hseed,
                                 Splitters<LOGV>& sp, BuildScratch<LOGV>& bs) {
   using G = Geo<LOGV>;
   for (uint32_t i = threadIdx.x; i < G::S; i += blockDim.x) {
     uint64_t h = mix64(hseed + i);
     uint32_t pos = (uint32_t)(((h >> 32) * (uint64_t)len) >> 32);
-    bs.sample[i] = keys[pos];
+    bs.sample[i] = recs[pos].key;
   }
   if (threadIdx.x == 0) { bs.ra[1] = 0; bs.rb[1] = (uint16_t)G::S; }
   __syncthreads();
@@ -132,7 +132,7 @@ __device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, c
 // atomics).  Each thread loads 8 keys before descending the tree for them,
 // so that the loads of a batch overlap.  Returns this thread's records.
 template <int LOGV>
-__device__ __forceinline__ uint32_t classify_count(const uint64_t* __restrict__ keys, uint16_t* __restrict__ bo,
+__device__ __forceinline__ uint32_t classify_count(const Rec* __restrict__ recs, uint16_t* __restrict__ bo,
                                                    uint32_t n, const uint64_t* tree, const uint64_t* x,
                                                    uint32_t* hist) {
   constexpr int U = 8;
@@ -143,7 +143,7 @@ __device__ __forceinline__ uint32_t classify_count(const uint64_t* __restrict__ 
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t p = p0 + u * kBlock;
-      k[u] = p < n ? keys[p] : 0ull;
+      k[u] = p < n ? recs[p].key : 0ull;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -257,31 +257,36 @@ __device__ void tile_scatter(const uint16_t* tb, uint32_t tl, uint32_t R, uint32
 // the bucket's new depth (fused character gather).  All loads of the batch
 // are issued before any of them is used.  bucket_first(b) is the position of
 // the first record of bucket b.  Returns the algorithmic bytes: bucket index 2
-// + idx 4 read; finished: perm 4 (+ lcp 4) written; open: key 8 read, key 8 +
-// idx 4 written, plus offset 8 + 8 characters read when the cache is reloaded.
+// + record 16 read (the record carries the string's offset); finished: perm 4
+// (+ lcp 4) written; open: record 16 written, plus 8 characters read when the
+// cache is reloaded.
 template <typename First>
-__device__ __forceinline__ uint32_t move_batch(const SortCtx& c, const SetDesc& sd, uint32_t par, uint32_t src0,
-                                               uint32_t depth, const uint32_t* desc, First&& bucket_first,
-                                               const uint32_t (&pp)[kMoveBatch], const uint32_t (&bb)[kMoveBatch],
-                                               const uint32_t (&dd)[kMoveBatch]) {
-  uint32_t id[kMoveBatch], ds[kMoveBatch];
+__device__ __forceinline__ uint32_t move_batch(const SortCtx& c, const SetDesc& sd, uint32_t wide, uint32_t par,
+                                               uint32_t src0, uint32_t depth, const uint32_t* desc,
+                                               First&& bucket_first, const uint32_t (&pp)[kMoveBatch],
+                                               const uint32_t (&bb)[kMoveBatch], const uint32_t (&dd)[kMoveBatch]) {
+  uint32_t id[kMoveBatch], ds[kMoveBatch], o32[kMoveBatch];
   uint64_t key[kMoveBatch], off[kMoveBatch];
   uint32_t bytes = 0;
 #pragma unroll
   for (int u = 0; u < kMoveBatch; ++u) {
     id[u] = 0;
+    o32[u] = 0;
     ds[u] = kFin;
     key[u] = 0;
     if (pp[u] != kInvalid) {
       ds[u] = desc[bb[u]];
-      id[u] = c.idx[par][src0 + pp[u]];
-      if (!(ds[u] & kFin)) key[u] = c.key[par][src0 + pp[u]];
+      const Rec r = load_rec(c.rec[par] + src0 + pp[u]);
+      id[u] = r.idx;
+      key[u] = r.key;
+      o32[u] = r.off;
     }
   }
 #pragma unroll
   for (int u = 0; u < kMoveBatch; ++u) {
     off[u] = 0;
-    if (pp[u] != kInvalid && !(ds[u] & kFin) && (ds[u] & kLow30) != depth) off[u] = sd.offsets[id[u]];
+    if (pp[u] != kInvalid && !(ds[u] & kFin) && (ds[u] & kLow30) != depth)
+      off[u] = rec_offset(sd, wide, id[u], o32[u]);
   }
 #pragma unroll
   for (int u = 0; u < kMoveBatch; ++u) {
@@ -290,7 +295,7 @@ __device__ __forceinline__ uint32_t move_batch(const SortCtx& c, const SetDesc& 
     const uint32_t dest = dd[u];
     if (d & kFin) {
       sd.perm[dest - sd.base] = id[u];
-      bytes += 10;
+      bytes += 22;
       if (sd.lcp && (d & kNulEq) && dest != bucket_first(bb[u])) {
         sd.lcp[dest - sd.base] = d & kLow30;
         bytes += 4;
@@ -299,13 +304,12 @@ __device__ __forceinline__ uint32_t move_batch(const SortCtx& c, const SetDesc& 
     }
     const uint32_t nd = d & kLow30;
     uint64_t k = key[u];
-    bytes += 26;
+    bytes += 32;
     if (nd != depth) {
       k = load_cache(sd.chars, off[u], nd, sd.cap);
-      bytes += 16;
+      bytes += 8;
     }
-    c.key[par ^ 1][dest] = k;
-    c.idx[par ^ 1][dest] = id[u];
+    store_rec(c.rec[par ^ 1] + dest, k, id[u], o32[u]);
   }
   return bytes;
 }
