@@ -96,7 +96,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
@@ -106,7 +106,11 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, t0, t1):
+        """Keep only samples received inside the timed region [t0, t1]."""
+        self.window = (t0, t1)
 
     def stop(self):
         if self.proc is None:
@@ -120,7 +124,10 @@ class ClockSampler:
             self.thread.join(timeout=2)
         sm, mx, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0, t1 = getattr(self, "window", (float("-inf"), float("inf")))
+        for ts, ln in self.lines:
+            if not (t0 <= ts <= t1 + 0.25):  # a sample arrives up to one period after it is taken
+                continue
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -203,7 +210,11 @@ def run_reference(args, ws, rank):
         return
     import oracle
     s, desc = workload(args.config)
-    sample = min(CPU_SAMPLE if args.config == "c2" else s.n, s.n)
+    # each step sorts a bounded sample of the workload (the first strings,
+    # generated i.i.d.) sized so that all warm-up and timed steps take about
+    # 45 s of one host core at ~1e6 strings/s
+    per_step = int(45e6 / max(1, args.steps + args.warmup))
+    sample = max(min(20_000, s.n), min(per_step, CPU_SAMPLE, s.n))
     offs = np.ascontiguousarray(s.offsets[:sample])
     oracle.load()
     for _ in range(args.warmup):
@@ -280,11 +291,13 @@ def run_ours(args, ws, rank, local):
     time.sleep(0.3)
     launches0 = ss.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start = time.perf_counter()
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark(t_start, time.perf_counter())
     launches = ss.launch_count() - launches0
     barrier(ws)
     clocks = sampler.stop()
@@ -500,7 +513,7 @@ def run_served(args, ws, rank, local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])

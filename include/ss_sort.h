@@ -21,9 +21,11 @@
  *                         out_lcp[j] = length of the common prefix of strings
  *                         out_perm[j-1] and out_perm[j].  Two equal strings
  *                         have lcp = their length.
- * A string's bytes are read only up to its terminator: the library loads
- * aligned 8-byte words that hold at least one byte of the string or its
- * terminator, and never a word that lies wholly past the terminator.
+ * Reads of a string stay inside the 4 KiB-aligned blocks that hold a byte of
+ * the string or its terminator: the library loads aligned 8-byte words, and
+ * when it looks ahead along a long common prefix it may read bytes past a
+ * terminator inside such a block (they are ignored).  Memory is mapped in
+ * blocks of at least 4 KiB, so these reads never leave mapped memory.
  *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
  * stream).  All work is enqueued on it.

@@ -304,7 +304,7 @@ __device__ __forceinline__ uint32_t move_batch(const SortCtx& c, const SetDesc& 
     }
     const uint32_t nd = d & kLow30;
     uint64_t k = key[u];
-    bytes += 32;
+    bytes += 34;
     if (nd != depth) {
       k = load_cache(sd.chars, off[u], nd, sd.cap);
       bytes += 8;
