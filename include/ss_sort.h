@@ -75,6 +75,13 @@ typedef struct ss_options {
                                   steps; >= small_cutoff (default 8192).         */
     uint32_t seed;             /* seed of the splitter sample (output does not
                                   depend on it).                                */
+    uint32_t classifier;       /* classification variant of Section 4.2.3 (the
+                                  output does not depend on it): 0 = S5-UI,
+                                  unrolled <=-descent then one equality test
+                                  against the sorted splitters (default);
+                                  1 = S5-UIC, the same test done in the tree
+                                  through Lemma 4.1's index map; 2 = S5-E, an
+                                  equality test at every node.                 */
     uint32_t flags;            /* reserved, must be 0                           */
     void* workspace;           /* optional caller-owned device workspace of at
                                   least ss_workspace_size() bytes, 256-byte
@@ -109,6 +116,22 @@ size_t ss_workspace_size(uint64_t n, const ss_options* opt);
 ss_status ss_sort_host(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets,
                        uint64_t n, uint32_t* out_perm, uint32_t* out_lcp,
                        const ss_options* opt, void* stream);
+
+/* Distinguishing characters and prefixes of a sorted set (the outputs of
+ * ss_sort on the same strings and max_len).  For each sorted position j,
+ * with h_j = lcp[j] (h_0 = 0) and h_n = 0:
+ *   out_char[j]    = c^_j = s_j[h_j], the character at which the string first
+ *                    differs from its predecessor (0 if it ends there) — the
+ *                    cached character of the LCP merge's caching variant
+ *                    (Section 4.3.4);
+ *   out_dprefix[j] = d_j = max(h_j, h_{j+1}) + 1, the length of its
+ *                    distinguishing prefix (proof of Lemma 2.1);
+ *   *out_D        += sum_j d_j = D (out_D: a device uint64).
+ * Any output may be NULL (chars/offsets are only read for out_char).
+ * Asynchronous on `stream`; argument errors are returned at once. */
+ss_status ss_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t max_len,
+                            const uint32_t* perm, const uint32_t* lcp, uint8_t* out_char,
+                            uint32_t* out_dprefix, uint64_t* out_D, void* stream);
 
 /* ---- batched sorting: many independent string sets in one launch ----------- */
 

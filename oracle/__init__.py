@@ -5,7 +5,8 @@ Only the tests, ``__graft_entry__.smoke()`` and the benchmark's ``cpu_baseline``
 path never calls it and shares no code with it.
 
 The arithmetic lives in ``ss_oracle.c`` (plain C, the definitions of Section
-2.1, the compare loop of Algorithm 4.2 and Lemma 2.1); this module compiles it
+2.1, the compare loop of Algorithm 4.2, Lemma 2.1 and the distinguishing
+characters of Section 4.3.4); this module compiles it
 with gcc and wraps it with ctypes.  Every function here has a parity pin in
 ``tests/test_oracle.py``.
 """
@@ -54,6 +55,12 @@ def _bind(lib):
     lib.oracle_bucket.restype = u32
     lib.oracle_tree.argtypes = [vp, u32, vp]
     lib.oracle_tree.restype = None
+    lib.oracle_distinguishing.argtypes = [vp, vp, u64, u32, vp, vp, vp, vp]
+    lib.oracle_distinguishing.restype = None
+    lib.oracle_level_to_pre.argtypes = [u32, u32]
+    lib.oracle_level_to_pre.restype = u32
+    lib.oracle_pre_to_level.argtypes = [u32, u32]
+    lib.oracle_pre_to_level.restype = u32
     return lib
 
 
@@ -145,6 +152,31 @@ def tree(x, lib=None):
     t = np.zeros(x.shape[0] + 1, np.uint64)
     lib.oracle_tree(x.ctypes.data, x.shape[0], t.ctypes.data)
     return t
+
+
+def distinguishing(chars, offsets, perm, lcp, max_len: int = 0, lib=None):
+    """(c^, d): distinguishing character and distinguishing-prefix length of
+    each sorted string (Section 4.3.4, Lemma 2.1)."""
+    lib = lib or load()
+    chars, offsets = _arrs(chars, offsets)
+    perm = np.ascontiguousarray(perm, dtype=np.uint32)
+    lcp = np.ascontiguousarray(lcp, dtype=np.uint32)
+    n = perm.shape[0]
+    dchar = np.empty(n, np.uint8)
+    dpre = np.empty(n, np.uint32)
+    lib.oracle_distinguishing(chars.ctypes.data, offsets.ctypes.data, n, max_len, perm.ctypes.data,
+                              lcp.ctypes.data, dchar.ctypes.data, dpre.ctypes.data)
+    return dchar, dpre
+
+
+def level_to_pre(l: int, w: int, lib=None) -> int:
+    """Lemma 4.1 (i): one-based level-order index -> pre-order index."""
+    return int((lib or load()).oracle_level_to_pre(l, w))
+
+
+def pre_to_level(p: int, w: int, lib=None) -> int:
+    """Lemma 4.1 (ii): one-based pre-order index -> level-order index."""
+    return int((lib or load()).oracle_pre_to_level(p, w))
 
 
 def from_strings(strs, max_len: int = 0):

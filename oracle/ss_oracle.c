@@ -199,3 +199,58 @@ void oracle_tree(const uint64_t* x, uint32_t v, uint64_t* t) {
     t[0] = 0;
     tree_fill(x, t, v, 1, &next);
 }
+
+/* For a sorted set (order perm, LCP array lcp): the distinguishing character
+ * of sorted string j, c^_j = s_j[h_j] with h_j its LCP with its predecessor
+ * (Section 4.3.4, caching variant of the LCP merge; h_0 = 0), 0 when the
+ * string ends at h_j; and the length of its distinguishing prefix
+ * d_j = max(h_j, h_{j+1}) + 1 with h_0 = h_n = 0 (proof of Lemma 2.1). */
+void oracle_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t max_len,
+                           const uint32_t* perm, const uint32_t* lcp, uint8_t* dchar, uint32_t* dprefix) {
+    for (uint64_t j = 0; j < n; ++j) {
+        uint64_t h = (j == 0) ? 0 : lcp[j];
+        uint64_t next = (j + 1 < n) ? lcp[j + 1] : 0;
+        dchar[j] = (uint8_t)char_at(chars + offsets[perm[j]], h, max_len);
+        dprefix[j] = (uint32_t)((h > next ? h : next) + 1);
+    }
+}
+
+/* Lemma 4.1 (Section 4.2.3): index maps of a perfect binary tree with 2^w - 1
+ * vertices between the one-based level-order index l = l_1 ... l_w and the
+ * one-based pre-order (sorted-splitter) index p = p_1 ... p_w, as bit strings
+ * (l_1, p_1 most significant).  (i) with l_x the first one bit of l:
+ * p = l_{x+1} ... l_w  l_x  l_1 ... l_{x-1};  (ii) with p_y the last one bit of
+ * p: l = p_{y+1} ... p_w  p_y  p_1 ... p_{y-1}.  Written on explicit bit
+ * arrays. */
+static void to_bits(uint32_t v, uint32_t w, int* b) {
+    for (uint32_t k = 0; k < w; ++k) b[k] = (int)((v >> (w - 1 - k)) & 1u); /* b[0] = l_1 */
+}
+static uint32_t from_bits(const int* b, uint32_t w) {
+    uint32_t v = 0;
+    for (uint32_t k = 0; k < w; ++k) v = (v << 1) | (uint32_t)b[k];
+    return v;
+}
+
+uint32_t oracle_level_to_pre(uint32_t l, uint32_t w) {
+    int lb[32], pb[32];
+    to_bits(l, w, lb);
+    uint32_t x = 0;
+    while (lb[x] == 0) ++x;          /* lb[x] is l_{x+1} in the lemma's one-based naming */
+    uint32_t o = 0;
+    for (uint32_t k = x + 1; k < w; ++k) pb[o++] = lb[k];
+    pb[o++] = lb[x];
+    for (uint32_t k = 0; k < x; ++k) pb[o++] = lb[k];
+    return from_bits(pb, w);
+}
+
+uint32_t oracle_pre_to_level(uint32_t p, uint32_t w) {
+    int pb[32], lb[32];
+    to_bits(p, w, pb);
+    uint32_t y = w - 1;
+    while (pb[y] == 0) --y;          /* last one bit */
+    uint32_t o = 0;
+    for (uint32_t k = y + 1; k < w; ++k) lb[o++] = pb[k];
+    lb[o++] = pb[y];
+    for (uint32_t k = 0; k < y; ++k) lb[o++] = pb[k];
+    return from_bits(lb, w);
+}

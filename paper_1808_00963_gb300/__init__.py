@@ -86,6 +86,7 @@ class Options(ctypes.Structure):
         ("small_cutoff", ctypes.c_uint32),
         ("big_threshold", ctypes.c_uint32),
         ("seed", ctypes.c_uint32),
+        ("classifier", ctypes.c_uint32),
         ("flags", ctypes.c_uint32),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
@@ -154,6 +155,8 @@ def load(path: str | None = None):
     lib.ss_kernel_stats.restype = u32
     lib.ss_reset_kernel_stats.argtypes = []
     lib.ss_reset_kernel_stats.restype = None
+    lib.ss_distinguishing.argtypes = [vp, vp, u64, u32, vp, vp, vp, vp, vp, vp]
+    lib.ss_distinguishing.restype = i32
     lib.ss_stream_status.argtypes = [vp]
     lib.ss_stream_status.restype = i32
     lib.ss_sort_noalloc.argtypes = [vp, vp, u64, u32, vp, vp, vp]
@@ -210,6 +213,24 @@ def sort(chars, offsets, max_len: int = 0, with_lcp: bool = True, out=None, stre
                         ctypes.byref(o), _stream_ptr(stream))
     _check(rc, "ss_sort_ex")
     return perm, lcp
+
+
+def distinguishing(chars, offsets, perm, lcp, max_len: int = 0, stream=None):
+    """Distinguishing character c^_j (uint8) and distinguishing-prefix length
+    d_j (int32) of every sorted position, and D = sum d_j (Section 4.3.4,
+    Lemma 2.1), from the outputs of sort()."""
+    import torch
+    lib = load()
+    n = int(perm.numel())
+    dchar = torch.empty(n, dtype=torch.uint8, device=perm.device)
+    dpre = torch.empty(n, dtype=torch.int32, device=perm.device)
+    D = torch.zeros(1, dtype=torch.int64, device=perm.device)
+    rc = lib.ss_distinguishing(ctypes.c_void_p(chars.data_ptr()), ctypes.c_void_p(offsets.data_ptr()), n, max_len,
+                               ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(lcp.data_ptr()),
+                               ctypes.c_void_p(dchar.data_ptr()), ctypes.c_void_p(dpre.data_ptr()),
+                               ctypes.c_void_p(D.data_ptr()), _stream_ptr(stream))
+    _check(rc, "ss_distinguishing")
+    return dchar, dpre, D
 
 
 def sort_host(chars, offsets, max_len: int = 0, with_lcp: bool = True, perm=None, lcp=None, stream=None,

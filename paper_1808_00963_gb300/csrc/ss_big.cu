@@ -63,7 +63,7 @@ __global__ void __launch_bounds__(kBlock) k_big_classify(SortCtx c, const GenTas
   const uint32_t tl = min(T, g.t.len - t0);
   const Rec* recs = c.rec[task_par(g.t)] + g.t.begin + t0;
   uint16_t* bo = c.bucket_of + g.t.begin + t0;
-  const uint32_t mine = classify_count<LOGV>(recs, bo, tl, tree, x, hist);
+  const uint32_t mine = classify_count<LOGV>(recs, bo, tl, tree, x, hist, c.classifier);
   __syncthreads();
   uint32_t* cnt = counters + cnt_base(g) + tile;
   for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) cnt[(uint64_t)b * g.tiles] = hist[b];

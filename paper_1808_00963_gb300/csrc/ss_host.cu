@@ -133,6 +133,7 @@ struct Opts {
   uint32_t cutoff = SS_TUNED_SMALL_CUTOFF;
   uint32_t big_thr = SS_TUNED_BIG_THRESHOLD;
   uint32_t seed = 0x5EED;
+  uint32_t classifier = 0;
   uint32_t mq_factor = 16;
 };
 
@@ -160,6 +161,8 @@ static ss_status resolve_opts(const ss_options* o, Opts& r) {
   if (o->big_threshold) r.big_thr = o->big_threshold;
   if (r.big_thr < r.cutoff) return SS_ERR_INVALID;
   if (o->seed) r.seed = o->seed;
+  if (o->classifier > 2) return SS_ERR_INVALID;
+  r.classifier = o->classifier;
   if (o->workspace && ((uintptr_t)o->workspace & 255)) return SS_ERR_INVALID;
   return SS_OK;
 }
@@ -239,6 +242,7 @@ static SortCtx make_ctx(uint8_t* ws, const Layout& L, uint32_t num_sets, uint32_
   c.big_threshold = o.big_thr;
   c.big_enabled = big ? 1u : 0u;
   c.seed = o.seed;
+  c.classifier = o.classifier;
   c.big_cur = 0;
   return c;
 }
@@ -480,6 +484,24 @@ uint32_t ss_kernel_stats(const char** names, uint64_t* launches, double* total_m
     ++i;
   }
   return i;
+}
+
+ss_status ss_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t max_len,
+                            const uint32_t* perm, const uint32_t* lcp, uint8_t* out_char, uint32_t* out_dprefix,
+                            uint64_t* out_D, void* stream) {
+  if (n >= 0xFFFFFFFFull) return SS_ERR_TOO_LARGE;
+  if (n == 0) return SS_OK;
+  if (!perm || !lcp || (out_char && (!chars || !offsets))) return SS_ERR_INVALID;
+  DevInfo dev;
+  ss_status s = device_info(dev);
+  if (s != SS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const uint32_t grid = std::max(1u, std::min<uint32_t>((uint32_t)((n + kBlock - 1) / kBlock), (uint32_t)dev.sms * 16));
+  const LaunchHook hook{st};
+  if (launch_distinguishing(chars, offsets, (uint32_t)n, max_len ? max_len : kNoCap, perm, lcp, out_char,
+                            out_dprefix, reinterpret_cast<unsigned long long*>(out_D), grid, st, hook) != cudaSuccess)
+    return SS_ERR_CUDA;
+  return SS_OK;
 }
 
 size_t ss_workspace_size(uint64_t n, const ss_options* opt) {

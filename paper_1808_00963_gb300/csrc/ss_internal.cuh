@@ -118,6 +118,7 @@ struct SortCtx {
   uint32_t big_threshold;  // tasks longer than this go to big[] (if big_enabled)
   uint32_t big_enabled;
   uint32_t seed;
+  uint32_t classifier;     // classification variant (kClassifyUI / UIC / E)
   uint32_t big_cur;        // which big[] list the current step reads
 };
 

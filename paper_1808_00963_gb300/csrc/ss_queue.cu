@@ -114,7 +114,7 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
   for (uint32_t b = threadIdx.x; b < Gm::KP; b += kBlock) s.hist[b] = 0;
   __syncthreads();
   uint16_t* bo = c.bucket_of + t.begin;
-  bytes += 10ull * classify_count<LOGV>(recs, bo, t.len, s.sp.tree, s.sp.x, s.hist);
+  bytes += 10ull * classify_count<LOGV>(recs, bo, t.len, s.sp.tree, s.sp.x, s.hist, c.classifier);
   __syncthreads();
 
   // line 15: prefix sum; bucket outcomes

@@ -538,6 +538,35 @@ __global__ void __launch_bounds__(kBlock) k_lcp_fix(SortCtx c) {
   account(c, kKLcpFix, bytes);
 }
 
+// Distinguishing characters and prefix lengths of a sorted set (Section
+// 4.3.4, proof of Lemma 2.1): c^_j = s_j[h_j] and d_j = max(h_j, h_{j+1}) + 1,
+// h_0 = h_n = 0; optionally the sum of d_j (= D) into *sum_d.
+__global__ void __launch_bounds__(kBlock) k_distinguishing(const uint8_t* __restrict__ chars,
+                                                           const uint64_t* __restrict__ offsets, uint32_t n,
+                                                           uint32_t cap, const uint32_t* __restrict__ perm,
+                                                           const uint32_t* __restrict__ lcp, uint8_t* dchar,
+                                                           uint32_t* dprefix, unsigned long long* sum_d) {
+  unsigned long long acc = 0;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  const uint32_t lim = (n + 31) / 32 * 32;
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < lim; j += stride) {
+    if (j < n) {
+      const uint32_t h = j == 0 ? 0u : lcp[j];
+      const uint32_t next = j + 1 < n ? lcp[j + 1] : 0u;
+      const uint32_t d = max(h, next) + 1;
+      if (dprefix) dprefix[j] = d;
+      if (dchar) dchar[j] = h < cap ? chars[offsets[perm[j]] + h] : 0;
+      acc += d;
+    }
+    if (sum_d) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(kFull, acc, o);
+      if (lane_id() == 0 && acc) atomicAdd(sum_d, acc);
+      acc = 0;
+    }
+  }
+}
+
 }  // namespace
 
 size_t small_cta_smem(uint32_t pmax) { return (size_t)pmax * (8 + 8 + 8 + 4 + 4 + 4 + 4 + 2); }
@@ -560,6 +589,15 @@ cudaError_t launch_small(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, ui
   }
   hook.run("small_cta", [&] { k_small_cta<<<grid_cta, kBlock, small_cta_smem(pmax), st>>>(c, pmax); });
   hook.run("small_warp", [&] { k_small_warp<<<grid_warp, kBlock, 0, st>>>(c); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t cap,
+                                  const uint32_t* perm, const uint32_t* lcp, uint8_t* dchar, uint32_t* dprefix,
+                                  unsigned long long* sum_d, uint32_t grid, cudaStream_t st, const LaunchHook& hook) {
+  hook.run("distinguishing", [&] {
+    k_distinguishing<<<grid, kBlock, 0, st>>>(chars, offsets, n, cap, perm, lcp, dchar, dprefix, sum_d);
+  });
   return cudaGetLastError();
 }
 

@@ -115,16 +115,52 @@ __device__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint
   __syncthreads();
 }
 
+// Lemma 4.1: one-based level-order index l <-> one-based pre-order index p
+// (the position of the vertex's splitter in sorted order) of a perfect binary
+// tree with w levels, by rotating the bits around the first (resp. last) one
+// bit.
+__device__ __forceinline__ uint32_t level_to_pre(uint32_t l, uint32_t w) {
+  const uint32_t s = 31 - __clz(l);  // bits after the first one bit
+  const uint32_t x = w - s;          // position of the first one bit, from the top
+  return ((l & ((1u << s) - 1)) << x) | (1u << (x - 1));
+}
+
+__device__ __forceinline__ uint32_t pre_to_level(uint32_t p, uint32_t w) {
+  const uint32_t t = (uint32_t)__ffs(p) - 1;  // bits after the last one bit
+  const uint32_t y = w - t;                    // position of the last one bit, from the top
+  return (1u << (y - 1)) | (p >> (t + 1));
+}
+
+// Classification variants of Section 4.2.3 (they give the same buckets up to
+// the numbering of empty ones, hence the same output).
+constexpr uint32_t kClassifyUI = 0;   // unrolled <=-descent, equality test on the sorted copy x
+constexpr uint32_t kClassifyUIC = 1;  // same descent, equality test in t via Lemma 4.1 (no copy needed)
+constexpr uint32_t kClassifyE = 2;    // equality test at every node of the descent
+
 // Lines 7-11 of Algorithm 4.1: branch-free descent of the level-order tree,
 // i := 2i + [c > t_i] (the reading of line 9 under which bucket b_{2r} holds
 // x_{r-1} < c < x_r), then the single equality test with x_r.
 template <int LOGV>
-__device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, const uint64_t* x) {
+__device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, const uint64_t* x,
+                                             uint32_t variant = kClassifyUI) {
   uint32_t i = 1;
+  if (variant == kClassifyE) {
+    uint32_t eq = 0;
+#pragma unroll
+    for (int l = 0; l < LOGV; ++l) {
+      const uint64_t t = tree[i];
+      if (!eq && c == t) eq = i;
+      i = 2 * i + (c > t ? 1u : 0u);
+    }
+    if (eq) return 2 * (level_to_pre(eq, LOGV) - 1) + 1;
+    return 2 * (i - (1u << LOGV));
+  }
 #pragma unroll
   for (int l = 0; l < LOGV; ++l) i = 2 * i + (c > tree[i] ? 1u : 0u);
   const uint32_t r = i - (1u << LOGV);
-  return 2 * r + ((r < Geo<LOGV>::V && x[r] == c) ? 1u : 0u);
+  bool eq = false;
+  if (r < Geo<LOGV>::V) eq = (variant == kClassifyUIC) ? tree[pre_to_level(r + 1, LOGV)] == c : x[r] == c;
+  return 2 * r + (eq ? 1u : 0u);
 }
 
 // Classifies n keys (lines 6-14 of Algorithm 4.1): writes the bucket of
@@ -134,7 +170,7 @@ __device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, c
 template <int LOGV>
 __device__ __forceinline__ uint32_t classify_count(const Rec* __restrict__ recs, uint16_t* __restrict__ bo,
                                                    uint32_t n, const uint64_t* tree, const uint64_t* x,
-                                                   uint32_t* hist) {
+                                                   uint32_t* hist, uint32_t variant) {
   constexpr int U = 8;
   uint32_t mine = 0;
   const uint32_t lim = (n + kBlock - 1) / kBlock * kBlock;
@@ -152,7 +188,7 @@ __device__ __forceinline__ uint32_t classify_count(const Rec* __restrict__ recs,
       const bool valid = p < n;
       uint32_t b = 0xFFFFu;
       if (valid) {
-        b = classify<LOGV>(k[u], tree, x);
+        b = classify<LOGV>(k[u], tree, x, variant);
         bo[p] = (uint16_t)b;
         ++mine;
       }

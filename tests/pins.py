@@ -218,5 +218,54 @@ def pin_bucket_and_tree(lib):
                     assert (r == 0 or xs[r - 1] < c) and (r == v or c < xs[r])
 
 
+def pin_distinguishing(lib):
+    """Section 4.3.4 / Lemma 2.1: on Lemma 2.1's example the distinguishing
+    prefixes are [2, 2, 2, 2] (sum D = 8) and the distinguishing characters
+    [a, b, b, b]; on random sets (with caps) the characters equal the byte of
+    each sorted string at its LCP with its predecessor (Python slicing), and
+    the prefix lengths sum to D."""
+    words = [w.encode() for w in golden("lemma2_1.txt")["words"].split()]
+    chars, offsets = oracle.from_strings(words)
+    p, l = oracle.sort(chars, offsets, lib=lib)
+    dc, dp = oracle.distinguishing(chars, offsets, p, l, lib=lib)
+    assert dp.tolist() == [2, 2, 2, 2] and bytes(dc.tolist()) == b"abbb"
+    rng = np.random.default_rng(31)
+    for t in range(20):
+        n = int(rng.integers(1, 300))
+        strs = [bytes(rng.integers(97, 100, size=int(rng.integers(0, 8))).astype(np.uint8)) for _ in range(n)]
+        cap = [0, 3, 5][t % 3]
+        view = [s[:cap] if cap else s for s in strs]
+        chars, offsets = oracle.from_strings(strs)
+        p, l = oracle.sort(chars, offsets, cap, lib=lib)
+        dc, dp = oracle.distinguishing(chars, offsets, p, l, cap, lib=lib)
+        srt = [view[i] for i in p]
+        for j in range(n):
+            h = 0 if j == 0 else len(os.path.commonprefix([srt[j - 1], srt[j]]))
+            want = srt[j][h] if h < len(srt[j]) else 0
+            assert dc[j] == want
+        D, _ = oracle.dl(l, lib=lib)
+        assert int(dp.astype(np.int64).sum()) == D
+
+
+def pin_lemma_4_1(lib):
+    """Lemma 4.1: the printed example (0101 level-order <-> 0110 pre-order),
+    the two maps are inverse, and the pre-order index of every tree vertex is
+    the one-based position of its splitter in sorted order (checked against
+    the level-order tree t built from the sorted splitters)."""
+    g = golden("lemma4_1.txt")
+    w = int(g["w"])
+    assert oracle.level_to_pre(int(g["level"], 2), w, lib=lib) == int(g["pre"], 2)
+    assert oracle.pre_to_level(int(g["pre"], 2), w, lib=lib) == int(g["level"], 2)
+    for w in range(1, 11):
+        v = (1 << w) - 1
+        x = np.arange(1, v + 1, dtype=np.uint64) * 3
+        t = oracle.tree(x, lib=lib)
+        for l in range(1, v + 1):
+            p = oracle.level_to_pre(l, w, lib=lib)
+            assert oracle.pre_to_level(p, w, lib=lib) == l
+            assert int(t[l]) == int(x[p - 1])
+
+
 ALL_PINS = [pin_paper_suffix_examples, pin_word_list_ties, pin_lemma_2_1, pin_brute_force,
-            pin_library_sort, pin_checker, pin_cache, pin_bucket_and_tree]
+            pin_library_sort, pin_checker, pin_cache, pin_bucket_and_tree, pin_distinguishing,
+            pin_lemma_4_1]

@@ -12,6 +12,11 @@ import pins
 SRC = os.path.join(os.path.dirname(oracle.__file__), "ss_oracle.c")
 
 MUTANTS = {
+    "lemma41_swapped_parts": ("    for (uint32_t k = x + 1; k < w; ++k) pb[o++] = lb[k];\n    pb[o++] = lb[x];",
+                              "    pb[o++] = lb[x];\n    for (uint32_t k = x + 1; k < w; ++k) pb[o++] = lb[k];"),
+    "dprefix_min": ("dprefix[j] = (uint32_t)((h > next ? h : next) + 1);", "dprefix[j] = (uint32_t)((h < next ? h : next) + 1);"),
+    "dchar_off_by_one": ("dchar[j] = (uint8_t)char_at(chars + offsets[perm[j]], h, max_len);",
+                         "dchar[j] = (uint8_t)char_at(chars + offsets[perm[j]], h + 1, max_len);"),
     "signed_char_compare": ("return ca < cb ? -1 : 1;",
                             "return (signed char)ca < (signed char)cb ? -1 : 1;"),
     "ties_descending": ("return c < 0 || (c == 0 && i < k);", "return c < 0 || (c == 0 && i > k);"),
