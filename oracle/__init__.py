@@ -5,8 +5,10 @@ Only the tests, ``__graft_entry__.smoke()`` and the benchmark's ``cpu_baseline``
 path never calls it and shares no code with it.
 
 The arithmetic lives in ``ss_oracle.c`` (plain C, the definitions of Section
-2.1, the compare loop of Algorithm 4.2, Lemma 2.1 and the distinguishing
-characters of Section 4.3.4); this module compiles it
+2.1, the compare loop of Algorithm 4.2, Lemma 2.1, the distinguishing
+characters of Section 4.3.4, and the K-way merge of Section 4.3.2 both as its
+definition and as Algorithm 4.5's LCP-aware tournament tree); this module
+compiles it
 with gcc and wraps it with ctypes.  Every function here has a parity pin in
 ``tests/test_oracle.py``.
 """
@@ -61,6 +63,10 @@ def _bind(lib):
     lib.oracle_level_to_pre.restype = u32
     lib.oracle_pre_to_level.argtypes = [u32, u32]
     lib.oracle_pre_to_level.restype = u32
+    lib.oracle_merge.argtypes = [vp, vp, u32, vp, u64, vp, vp]
+    lib.oracle_merge.restype = ctypes.c_int
+    lib.oracle_lcp_merge.argtypes = [vp, vp, u32, u32, vp, vp, vp, vp, vp, ctypes.POINTER(u64)]
+    lib.oracle_lcp_merge.restype = ctypes.c_int
     return lib
 
 
@@ -177,6 +183,51 @@ def level_to_pre(l: int, w: int, lib=None) -> int:
 def pre_to_level(p: int, w: int, lib=None) -> int:
     """Lemma 4.1 (ii): one-based pre-order index -> level-order index."""
     return int((lib or load()).oracle_pre_to_level(p, w))
+
+
+def merge(chars, offsets, runs, max_len: int = 0, lib=None):
+    """Merged order and LCP array of K sorted runs (sequences of string
+    indices): by definition the union of the runs in string order, ties by
+    index (Section 4.3.2)."""
+    lib = lib or load()
+    chars, offsets = _arrs(chars, offsets)
+    idx = np.ascontiguousarray(np.concatenate([np.asarray(r, np.uint32) for r in runs])
+                               if len(runs) else np.zeros(0, np.uint32), dtype=np.uint32)
+    n = idx.shape[0]
+    perm = np.empty(n, np.uint32)
+    lcp = np.empty(n, np.uint32)
+    if lib.oracle_merge(chars.ctypes.data, offsets.ctypes.data, max_len, idx.ctypes.data, n,
+                        perm.ctypes.data, lcp.ctypes.data) != 0:
+        raise ValueError("oracle_merge failed")
+    return perm, lcp
+
+
+def lcp_merge(chars, offsets, runs, max_len: int = 0, lib=None):
+    """The same merge by the LCP-aware tournament tree of Algorithm 4.5 with
+    one character per comparison.  ``runs`` is a list of (perm, lcp) pairs
+    (each run sorted, lcp its LCP array).  Returns (perm, lcp, character
+    comparisons)."""
+    lib = lib or load()
+    chars, offsets = _arrs(chars, offsets)
+    K = len(runs)
+    sizes = [len(r[0]) for r in runs]
+    if any(len(r[1]) != len(r[0]) for r in runs):
+        raise ValueError("each run needs one LCP entry per string")
+    start = np.zeros(K + 1, np.uint64)
+    start[1:] = np.cumsum(sizes) if K else []
+    cat = lambda xs: np.ascontiguousarray(np.concatenate([np.asarray(x, np.uint32) for x in xs])  # noqa: E731
+                                          if sum(sizes) else np.zeros(1, np.uint32), dtype=np.uint32)
+    idx = cat([r[0] for r in runs])
+    rl = cat([r[1] for r in runs])
+    n = int(sum(sizes))
+    perm = np.empty(max(n, 1), np.uint32)
+    lcp = np.empty(max(n, 1), np.uint32)
+    cmps = ctypes.c_uint64(0)
+    if lib.oracle_lcp_merge(chars.ctypes.data, offsets.ctypes.data, max_len, K, start.ctypes.data,
+                            idx.ctypes.data, rl.ctypes.data, perm.ctypes.data, lcp.ctypes.data,
+                            ctypes.byref(cmps)) != 0:
+        raise ValueError("oracle_lcp_merge failed")
+    return perm[:n], lcp[:n], int(cmps.value)
 
 
 def from_strings(strs, max_len: int = 0):

@@ -23,6 +23,9 @@
  *   - Lemma 2.1 (proof): the distinguishing prefix of the sorted string i is
  *     d_i = max(h_i, h_{i+1}) + 1 with h_0 = h_n = 0, D = sum d_i, and
  *     L = sum_{i>=1} h_i.
+ *   - Section 4.3.2: the merge of sorted runs, as its definition (the sorted
+ *     union) and as the LCP-aware tournament tree of Algorithm 4.5 (one
+ *     character per comparison, counted for Theorem 4.7).
  *
  * Parity pins (see tests/): brute force over all n! orders on tiny inputs,
  * the suffix arrays printed in Figure 5.1, Examples 8.4 and 8.11 and
@@ -253,4 +256,148 @@ uint32_t oracle_pre_to_level(uint32_t p, uint32_t w) {
     lb[o++] = pb[y];
     for (uint32_t k = 0; k < y; ++k) lb[o++] = pb[k];
     return from_bits(lb, w);
+}
+
+/* ---- K-way merge of sorted runs (Section 4.3.2) --------------------------
+ *
+ * The merge of K runs (each a sorted sequence of string indices of the same
+ * string set) has a plain definition: the union of the runs' indices in
+ * string order, ties by index, with its LCP array.  oracle_merge writes
+ * exactly that: the concatenated indices, merge-sorted with the comparison
+ * above, and the naive LCP scan.  idx[total] holds the runs back to back (the
+ * run boundaries do not matter to the definition). */
+int oracle_merge(const uint8_t* chars, const uint64_t* offsets, uint32_t max_len, const uint32_t* idx,
+                 uint64_t total, uint32_t* perm, uint32_t* lcp) {
+    if (total > 0xFFFFFFFFull) return -1;
+    if (total == 0) return 0;
+    uint32_t* tmp = (uint32_t*)malloc(total * sizeof(uint32_t));
+    if (!tmp) return -1;
+    memcpy(perm, idx, total * sizeof(uint32_t));
+    merge_sort(chars, offsets, max_len, perm, tmp, 0, total);
+    free(tmp);
+    oracle_lcp_array(chars, offsets, total, max_len, perm, lcp);
+    return 0;
+}
+
+/* The same merge by the method of Section 4.3.2: a tournament (loser) tree
+ * over the runs' front strings whose games are LCP-Compare (Algorithm 4.2),
+ * kept LCP-aware as in Algorithm 4.5, comparing ONE character per step so
+ * that the character comparisons can be counted against Theorem 4.7
+ * (at most dL + n log2 K + K, K a power of two, dL = L(H_0) - sum_k L(H_k)).
+ *
+ * A player is (run, string index, h) where h is the LCP of its string with a
+ * string p that precedes it; the two players of a game always share the same
+ * p.  The tree has K leaves (runs padded with empty ones to a power of two);
+ * internal node v (1..K-1, children 2v and 2v+1, leaf k at K + k) keeps the
+ * loser of its last game with h = LCP(loser, that game's winner).  Runs that
+ * are used up play a sentinel that loses every game. */
+typedef struct {
+    uint32_t run;                   /* K_pad: sentinel (used-up run) */
+    uint32_t idx;
+    uint64_t h;
+} lm_player;
+
+typedef struct {
+    const uint8_t* chars;
+    const uint64_t* offsets;
+    uint32_t max_len;
+    uint32_t sentinel;
+    uint64_t cmps;                  /* character comparisons */
+} lm_ctx;
+
+/* LCP-Compare: plays *x against *y; afterwards *x is the winner (its h
+ * unchanged: still its LCP with p) and *y the loser with h = LCP(loser,
+ * winner).  Equal LCPs (case 1): compare characters from there on.  Unequal
+ * LCPs (cases 2 and 3): the player with the larger LCP to p goes first, and
+ * the LCP of the two is the smaller value, so no character is read. */
+static void lcp_compare(lm_ctx* c, lm_player* x, lm_player* y) {
+    lm_player t;
+    if (y->run == c->sentinel) return;
+    if (x->run == c->sentinel) { t = *x; *x = *y; *y = t; return; }
+    if (x->h == y->h) {
+        const uint8_t* sa = c->chars + c->offsets[x->idx];
+        const uint8_t* sb = c->chars + c->offsets[y->idx];
+        uint64_t h = x->h;
+        unsigned ca, cb;
+        for (;;) {
+            ca = char_at(sa, h, c->max_len);
+            cb = char_at(sb, h, c->max_len);
+            c->cmps++;
+            if (ca != cb || ca == 0) break;
+            ++h;
+        }
+        int x_first = ca < cb || (ca == cb && x->idx <= y->idx);
+        if (!x_first) { t = *x; *x = *y; *y = t; }
+        y->h = h;
+        return;
+    }
+    if (x->h < y->h) { t = *x; *x = *y; *y = t; }
+}
+
+/* run_idx / run_lcp hold the K runs back to back, run k at
+ * [run_start[k], run_start[k+1]); run_lcp[j] = LCP with the previous string
+ * of the same run (its first entry is not read).  Writes the merged order and
+ * LCP array (total entries) and the number of character comparisons.
+ * Returns 0, or -1 on bad arguments / no memory. */
+int oracle_lcp_merge(const uint8_t* chars, const uint64_t* offsets, uint32_t max_len, uint32_t K,
+                     const uint64_t* run_start, const uint32_t* run_idx, const uint32_t* run_lcp,
+                     uint32_t* perm, uint32_t* lcp, uint64_t* char_cmps) {
+    if (K == 0 || K > (1u << 20)) return -1;
+    uint32_t kp = 1;
+    while (kp < K) kp <<= 1;
+    lm_ctx c = {chars, offsets, max_len, kp, 0};
+    lm_player* node = (lm_player*)calloc(2 * (size_t)kp, sizeof(lm_player));
+    uint64_t* pos = (uint64_t*)calloc(kp, sizeof(uint64_t));
+    if (!node || !pos) { free(node); free(pos); return -1; }
+    /* leaves: the first string of each run, h = 0 (p = the empty string) */
+    for (uint32_t k = 0; k < kp; ++k) {
+        lm_player* leaf = &node[kp + k];
+        if (k < K && run_start[k] < run_start[k + 1]) {
+            pos[k] = run_start[k];
+            leaf->run = k;
+            leaf->idx = run_idx[pos[k]];
+            leaf->h = 0;
+        } else {
+            leaf->run = kp;
+        }
+    }
+    /* first round: every game once, bottom-up; winners go up in w[] */
+    lm_player* w = (lm_player*)calloc(2 * (size_t)kp, sizeof(lm_player));
+    if (!w) { free(node); free(pos); return -1; }
+    for (uint32_t k = 0; k < kp; ++k) w[kp + k] = node[kp + k];
+    for (uint32_t v = kp - 1; v >= 1; --v) {
+        lm_player x = w[2 * v], y = w[2 * v + 1];
+        lcp_compare(&c, &x, &y);
+        w[v] = x;
+        node[v] = y;
+    }
+    lm_player win = kp > 1 ? w[1] : w[kp];
+    free(w);
+    uint64_t out = 0;
+    while (win.run != kp) {
+        perm[out] = win.idx;
+        lcp[out] = out == 0 ? 0 : (uint32_t)win.h;
+        ++out;
+        /* the winner's run moves on; the new front string has h = its LCP
+         * with the string just written, which is the common p of every loser
+         * on the path to the root */
+        uint32_t r = win.run;
+        lm_player x;
+        ++pos[r];
+        if (pos[r] < run_start[r + 1]) {
+            x.run = r;
+            x.idx = run_idx[pos[r]];
+            x.h = run_lcp[pos[r]];
+        } else {
+            x.run = kp;
+            x.idx = 0;
+            x.h = 0;
+        }
+        for (uint32_t v = (kp + r) / 2; v >= 1; v /= 2) lcp_compare(&c, &x, &node[v]);
+        win = x;
+    }
+    free(node);
+    free(pos);
+    *char_cmps = c.cmps;
+    return 0;
 }

@@ -266,6 +266,56 @@ def pin_lemma_4_1(lib):
             assert int(t[l]) == int(x[p - 1])
 
 
+def _py_runs(view, assign, K):
+    """Runs sorted by Python's bytes order (ties by index) and their LCP arrays."""
+    runs = []
+    for k in range(K):
+        r = sorted((i for i in range(len(view)) if assign[i] == k), key=lambda i: (view[i], i))
+        lc = [0] * min(1, len(r)) + [len(os.path.commonprefix([view[r[j - 1]], view[r[j]]]))
+                                     for j in range(1, len(r))]
+        runs.append((np.array(r, np.uint32), np.array(lc, np.uint32)))
+    return runs
+
+
+def pin_merge(lib):
+    """Section 4.3.2: merging K sorted runs gives Python's sorted() of their
+    union (ties by index) with its LCP array, both as the definition and by
+    Algorithm 4.5's LCP-aware tournament tree; the tree does at most
+    dL + n log2 K + K character comparisons (Theorem 4.7) and needs none for
+    a single run.  Runs of every count 1..17 (padded to powers of two), empty
+    runs, equal strings in different runs, an index present in two runs, caps."""
+    rng = np.random.default_rng(47)
+    for t in range(60):
+        n = int(rng.integers(0, 400))
+        K = int(rng.integers(1, 18))
+        lo, hi = [(97, 99), (1, 255), (120, 121)][t % 3]
+        strs = [bytes(rng.integers(lo, hi + 1, size=int(rng.integers(0, 9))).astype(np.uint8)) for _ in range(n)]
+        for k in range(0, n, 11):
+            strs[k] = strs[(k * 5) % n]
+        max_len = [0, 0, 3, 1][t % 4]
+        view = [s[:max_len] if max_len else s for s in strs]
+        assign = rng.integers(0, K, n) if t % 5 else np.minimum(rng.integers(0, 2 * K, n), K - 1)
+        runs = _py_runs(view, assign, K)
+        if t % 7 == 3 and n > 0:               # one index present in two runs
+            extra = _py_runs(view, np.where(np.arange(n) == n // 2, 0, 1), 2)[0]
+            runs.append(extra)
+        members = sorted((int(i) for r in runs for i in r[0]), key=lambda i: (view[i], i))
+        want_l = [0] + [len(os.path.commonprefix([view[members[j - 1]], view[members[j]]]))
+                        for j in range(1, len(members))]
+        chars, offsets = oracle.from_strings(strs)
+        pm, lm = oracle.merge(chars, offsets, [r[0] for r in runs], max_len, lib=lib)
+        assert pm.tolist() == members and lm.tolist() == want_l, (t, "definition")
+        pk, lk, cmps = oracle.lcp_merge(chars, offsets, runs, max_len, lib=lib)
+        assert pk.tolist() == members and lk.tolist() == want_l, (t, "Algorithm 4.5")
+        kp = 1
+        while kp < len(runs):
+            kp *= 2
+        dL = sum(want_l[1:]) - sum(int(r[1][1:].sum()) for r in runs)
+        assert cmps <= dL + len(members) * (kp.bit_length() - 1) + kp, (t, cmps)
+        if len(runs) == 1:
+            assert cmps == 0
+
+
 ALL_PINS = [pin_paper_suffix_examples, pin_word_list_ties, pin_lemma_2_1, pin_brute_force,
             pin_library_sort, pin_checker, pin_cache, pin_bucket_and_tree, pin_distinguishing,
-            pin_lemma_4_1]
+            pin_lemma_4_1, pin_merge]

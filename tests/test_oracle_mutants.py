@@ -31,6 +31,13 @@ MUTANTS = {
     "bucket_le": ("if (x[j] < c) ++r;", "if (x[j] <= c) ++r;"),
     "tree_mirrored": ("tree_fill(x, t, v, 2 * node, next);\n    t[node] = x[(*next)++];\n    tree_fill(x, t, v, 2 * node + 1, next);",
                       "tree_fill(x, t, v, 2 * node + 1, next);\n    t[node] = x[(*next)++];\n    tree_fill(x, t, v, 2 * node, next);"),
+    "lcp_compare_cases_swapped": ("    if (x->h < y->h) { t = *x; *x = *y; *y = t; }\n}",
+                                  "    if (x->h > y->h) { t = *x; *x = *y; *y = t; }\n}"),
+    "lcp_compare_ties_by_larger_index": ("(ca == cb && x->idx <= y->idx)", "(ca == cb && x->idx >= y->idx)"),
+    "lcp_compare_keeps_loser_h": ("        y->h = h;\n        return;", "        return;"),
+    "kway_new_front_h_zero": ("            x.h = run_lcp[pos[r]];", "            x.h = 0;"),
+    "kway_replay_skips_parent": ("for (uint32_t v = (kp + r) / 2; v >= 1; v /= 2)",
+                                 "for (uint32_t v = (kp + r) / 4; v >= 1; v /= 2)"),
     "merge_takes_right_on_tie": ("if (goes_before(chars, offsets, max_len, perm[b], perm[a])) tmp[o++] = perm[b++];",
                                  "if (str_compare(chars + offsets[perm[b]], chars + offsets[perm[a]], max_len) <= 0) tmp[o++] = perm[b++];"),
 }
