@@ -133,6 +133,57 @@ ss_status ss_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint6
                             const uint32_t* perm, const uint32_t* lcp, uint8_t* out_char,
                             uint32_t* out_dprefix, uint64_t* out_D, void* stream);
 
+/* ---- K-way LCP merge of sorted runs ----------------------------------------- */
+
+/* Up to this many runs per ss_merge call. */
+#define SS_MERGE_MAX_RUNS 64
+
+/* One sorted run of strings of the set (chars, offsets) given to ss_merge
+ * (device pointers, owned by the caller). */
+typedef struct ss_run {
+    const uint32_t* perm;      /* n string indices, in string order with equal
+                                  strings in ascending index order (as ss_sort
+                                  writes them, mapped to the set's indices).  */
+    const uint32_t* lcp;       /* lcp[j] = lcp(perm[j-1], perm[j]) for j >= 1
+                                  (lcp[0] is not read), as ss_sort writes it.  */
+    uint32_t n;
+    uint32_t reserved;         /* must be 0 */
+} ss_run;
+
+/* Merge K sorted runs into one sorted sequence with its LCP array: the
+ * multiway LCP-merge of Section 4.3.2 (LCP-Compare, Algorithm 4.2; the
+ * LCP-aware tournament tree of Algorithm 4.5), split into independent pieces
+ * as in Section 4.3.3.
+ *   runs       HOST array of num_runs (1..SS_MERGE_MAX_RUNS) run descriptors;
+ *              read during the call only.  Every index must be < the number
+ *              of strings behind offsets (not checked).  An index may appear
+ *              in several runs: it is then output once per appearance.
+ *   out_perm   uint32[total] (total = sum of the runs' n): the union of the
+ *              runs in string order, equal strings by ascending index — the
+ *              result of sorting the union with ss_sort.
+ *   out_lcp    uint32[total] or NULL: out_lcp[0] = 0, out_lcp[j] = lcp of
+ *              out_perm[j-1] and out_perm[j].
+ *   max_len    as ss_options.max_len; it must be the value the runs were
+ *              sorted with.  Strings are compared up to 2^30 characters.
+ *   sample_step  every sample_step-th string of a run bounds a piece
+ *              (16..65536; 0 = chosen from the total).
+ *   workspace  device memory of ss_merge_workspace_size() bytes, 256-byte
+ *              aligned, or NULL (a stream-ordered allocation is made and
+ *              freed on `stream`).
+ * Asynchronous on `stream` (no host synchronisation; no device status word:
+ * the result is defined when the inputs meet the conditions above).  Output
+ * buffers must not overlap the runs.  Returns SS_ERR_INVALID for bad
+ * arguments, SS_ERR_TOO_LARGE if total >= 2^32 - 1, SS_ERR_OOM if the
+ * workspace cannot be allocated. */
+ss_status ss_merge(const uint8_t* chars, const uint64_t* offsets, uint32_t max_len,
+                   const ss_run* runs, uint32_t num_runs, uint32_t sample_step,
+                   uint32_t* out_perm, uint32_t* out_lcp,
+                   void* workspace, size_t workspace_bytes, void* stream);
+
+/* Workspace bytes ss_merge needs for these runs (at least 256; 0 for invalid
+ * arguments). */
+size_t ss_merge_workspace_size(const ss_run* runs, uint32_t num_runs, uint32_t sample_step);
+
 /* ---- batched sorting: many independent string sets in one launch ----------- */
 
 /* One string set of a batch (device pointers, as for ss_sort). */
@@ -217,7 +268,9 @@ uint64_t ss_launch_count(void);
 
 /* Per-kernel device timing.  When enabled, the library records CUDA events
  * around each of its kernel launches on the launching stream and accumulates
- * the elapsed time per kernel class once the call has waited for its work,
+ * the elapsed time per kernel class once the call has waited for its work
+ * (launches of the asynchronous calls ss_merge and ss_distinguishing are
+ * waited for and added by the next ss_kernel_stats call of the same thread),
  * together with the algorithmic bytes the kernels of that class moved (the
  * bytes their task requires, counted on the device: each record read and
  * written once, 8 bytes per character-window gather).  ss_kernel_stats fills

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_BUILD, "libss_sort.so")
 ROOT = os.path.dirname(_HERE)
 HEADER = os.path.join(ROOT, "include", "ss_sort.h")
 
-SOURCES = ["ss_host.cu", "ss_big.cu", "ss_queue.cu", "ss_small.cu"]
+SOURCES = ["ss_host.cu", "ss_big.cu", "ss_queue.cu", "ss_small.cu", "ss_merge.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-Xcompiler", "-Wall"]
@@ -105,6 +105,18 @@ class SetDesc(ctypes.Structure):
     ]
 
 
+class RunDesc(ctypes.Structure):
+    """Mirror of ss_run."""
+    _fields_ = [
+        ("perm", ctypes.c_void_p),
+        ("lcp", ctypes.c_void_p),
+        ("n", ctypes.c_uint32),
+        ("reserved", ctypes.c_uint32),
+    ]
+
+
+MERGE_MAX_RUNS = 64
+
 _lib = None
 
 
@@ -161,6 +173,10 @@ def load(path: str | None = None):
     lib.ss_stream_status.restype = i32
     lib.ss_sort_noalloc.argtypes = [vp, vp, u64, u32, vp, vp, vp]
     lib.ss_sort_noalloc.restype = i32
+    lib.ss_merge.argtypes = [vp, vp, u32, ctypes.POINTER(RunDesc), u32, u32, vp, vp, vp, ctypes.c_size_t, vp]
+    lib.ss_merge.restype = i32
+    lib.ss_merge_workspace_size.argtypes = [ctypes.POINTER(RunDesc), u32, u32]
+    lib.ss_merge_workspace_size.restype = ctypes.c_size_t
     if path is None:
         _lib = lib
     return lib
@@ -231,6 +247,47 @@ def distinguishing(chars, offsets, perm, lcp, max_len: int = 0, stream=None):
                                ctypes.c_void_p(D.data_ptr()), _stream_ptr(stream))
     _check(rc, "ss_distinguishing")
     return dchar, dpre, D
+
+
+def _run_descs(runs):
+    arr = (RunDesc * max(1, len(runs)))()
+    for k, (perm, lcp) in enumerate(runs):
+        n = int(perm.numel())
+        if int(lcp.numel()) != n:
+            raise ValueError("each run needs one LCP entry per string")
+        arr[k].perm = perm.data_ptr() if n else None
+        arr[k].lcp = lcp.data_ptr() if n else None
+        arr[k].n = n
+        arr[k].reserved = 0
+    return arr
+
+
+def merge_workspace_size(runs, sample_step: int = 0) -> int:
+    """Device workspace bytes merge() needs for these runs."""
+    return int(load().ss_merge_workspace_size(_run_descs(runs), len(runs), sample_step))
+
+
+def merge(chars, offsets, runs, max_len: int = 0, with_lcp: bool = True, out=None, sample_step: int = 0,
+          workspace=None, workspace_bytes: int = 0, stream=None):
+    """Merge sorted runs (a list of (perm, lcp) int32 device tensors holding
+    indices into the string set (chars, offsets), each sorted as sort() sorts)
+    into one sorted order and its LCP array (Section 4.3.2, Algorithm 4.5).
+    Asynchronous on ``stream``."""
+    import torch
+    lib = load()
+    total = sum(int(r[0].numel()) for r in runs)
+    dev = runs[0][0].device if runs else chars.device
+    if out is None:
+        perm = torch.empty(total, dtype=torch.int32, device=dev)
+        lcp = torch.empty(total, dtype=torch.int32, device=dev) if with_lcp else None
+    else:
+        perm, lcp = out
+    rc = lib.ss_merge(ctypes.c_void_p(chars.data_ptr()), ctypes.c_void_p(offsets.data_ptr()), max_len,
+                      _run_descs(runs), len(runs), sample_step, ctypes.c_void_p(perm.data_ptr()),
+                      ctypes.c_void_p(lcp.data_ptr()) if lcp is not None else None,
+                      ctypes.c_void_p(workspace) if workspace else None, workspace_bytes, _stream_ptr(stream))
+    _check(rc, "ss_merge")
+    return perm, lcp
 
 
 def sort_host(chars, offsets, max_len: int = 0, with_lcp: bool = True, perm=None, lcp=None, stream=None,

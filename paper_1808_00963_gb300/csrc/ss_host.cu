@@ -469,6 +469,7 @@ void ss_reset_kernel_stats(void) {
 
 uint32_t ss_kernel_stats(const char** names, uint64_t* launches, double* total_ms, uint64_t* alg_bytes,
                          uint32_t cap) {
+  collect_profile();  // launches of asynchronous calls (merge, distinguishing) made by this thread
   std::lock_guard<std::mutex> lk(g_stats_mu);
   uint32_t i = 0;
   for (auto& kv : g_stats) {
@@ -502,6 +503,97 @@ ss_status ss_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint6
                             out_dprefix, reinterpret_cast<unsigned long long*>(out_D), grid, st, hook) != cudaSuccess)
     return SS_ERR_CUDA;
   return SS_OK;
+}
+
+// ---- K-way LCP merge ------------------------------------------------------------------
+
+static uint32_t merge_step(uint64_t total, uint32_t sample_step) {
+  if (sample_step) return sample_step;
+  uint32_t s = 64;  // about 2^16 pieces for large inputs, pieces of 64..2048 strings
+  while (s < 2048 && (uint64_t)s * 2 * 65536 <= total) s *= 2;
+  return s;
+}
+
+static ss_status merge_geometry(const ss_run* runs, uint32_t num_runs, uint32_t sample_step, uint64_t* total,
+                                uint32_t* S, uint64_t* C) {
+  if (num_runs == 0 || num_runs > SS_MERGE_MAX_RUNS || !runs) return SS_ERR_INVALID;
+  if (sample_step != 0 && (sample_step < 16 || sample_step > 65536)) return SS_ERR_INVALID;
+  uint64_t t = 0;
+  for (uint32_t k = 0; k < num_runs; ++k) {
+    if (runs[k].reserved != 0) return SS_ERR_INVALID;
+    if (runs[k].n > 0 && (!runs[k].perm || !runs[k].lcp)) return SS_ERR_INVALID;
+    t += runs[k].n;
+  }
+  if (t >= 0xFFFFFFFFull) return SS_ERR_TOO_LARGE;
+  *total = t;
+  *S = merge_step(t, sample_step);
+  uint64_t c = 0;
+  for (uint32_t k = 0; k < num_runs; ++k) c += runs[k].n / *S;
+  *C = c;
+  return SS_OK;
+}
+
+// cut vectors, sample ranks, piece counter
+static size_t merge_ws_bytes(uint64_t C, uint32_t kp) { return align256(C * kp * 4) + align256(C * 4) + 256; }
+
+static uint32_t pow2_at_least(uint32_t k, uint32_t* logk) {
+  uint32_t kp = 1, l = 0;
+  while (kp < k) { kp <<= 1; ++l; }
+  *logk = l;
+  return kp;
+}
+
+size_t ss_merge_workspace_size(const ss_run* runs, uint32_t num_runs, uint32_t sample_step) {
+  uint64_t total, C;
+  uint32_t S, logk;
+  if (merge_geometry(runs, num_runs, sample_step, &total, &S, &C) != SS_OK) return 0;
+  return merge_ws_bytes(C, pow2_at_least(num_runs, &logk));
+}
+
+ss_status ss_merge(const uint8_t* chars, const uint64_t* offsets, uint32_t max_len, const ss_run* runs,
+                   uint32_t num_runs, uint32_t sample_step, uint32_t* out_perm, uint32_t* out_lcp,
+                   void* workspace, size_t workspace_bytes, void* stream) {
+  uint64_t total, C;
+  uint32_t S, logk;
+  ss_status s = merge_geometry(runs, num_runs, sample_step, &total, &S, &C);
+  if (s != SS_OK) return s;
+  if (total == 0) return SS_OK;
+  if (!chars || !offsets || !out_perm) return SS_ERR_INVALID;
+  if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return SS_ERR_INVALID;
+  const uint32_t kp = pow2_at_least(num_runs, &logk);
+  const size_t need = merge_ws_bytes(C, kp);
+  if (workspace && workspace_bytes < need) return SS_ERR_INVALID;
+  DevInfo dev;
+  s = device_info(dev);
+  if (s != SS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* ws = static_cast<uint8_t*>(workspace);
+  const bool own = !ws;
+  if (own && cudaMallocAsync(reinterpret_cast<void**>(&ws), need, st) != cudaSuccess) return SS_ERR_OOM;
+  MergeParams m{};
+  m.chars = chars;
+  m.offsets = offsets;
+  m.cut = reinterpret_cast<uint32_t*>(ws);
+  m.rank = reinterpret_cast<uint32_t*>(ws + align256(C * kp * 4));
+  m.next_piece = reinterpret_cast<uint32_t*>(ws + align256(C * kp * 4) + align256(C * 4));
+  m.out_perm = out_perm;
+  m.out_lcp = out_lcp;
+  m.cap = max_len ? std::min<uint32_t>(max_len, 1u << 30) : (1u << 30);
+  m.K = kp;
+  m.S = S;
+  m.C = (uint32_t)C;
+  uint32_t base = 0;
+  for (uint32_t k = 0; k < kp; ++k) {
+    const bool real = k < num_runs;
+    m.run[k] = MergeRun{real ? runs[k].perm : nullptr, real ? runs[k].lcp : nullptr, real ? runs[k].n : 0u, base};
+    if (real) base += runs[k].n / S;
+  }
+  const LaunchHook hook{st};
+  if (cudaMemsetAsync(m.next_piece, 0, sizeof(uint32_t), st) != cudaSuccess ||
+      launch_merge(m, logk, (uint32_t)dev.sms, st, hook) != cudaSuccess)
+    s = SS_ERR_CUDA;
+  if (own && cudaFreeAsync(ws, st) != cudaSuccess && s == SS_OK) s = SS_ERR_CUDA;
+  return s;
 }
 
 size_t ss_workspace_size(uint64_t n, const ss_options* opt) {

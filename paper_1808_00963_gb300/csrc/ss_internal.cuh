@@ -168,6 +168,40 @@ __device__ __forceinline__ uint64_t load_cache(const uint8_t* chars, uint64_t of
   return bswap64(v);
 }
 
+// load_cache with both words issued at once: when the window is unaligned and
+// the second aligned word lies in the same 4 KiB block as byte h, it is loaded
+// together with the first (one memory round trip instead of two; bytes past
+// the terminator are discarded); across a block boundary it is loaded only if
+// the first word holds no terminator, as in load_cache.  Same result and
+// precondition as load_cache.
+__device__ __forceinline__ uint64_t load_cache_2w(const uint8_t* chars, uint64_t off, uint32_t h,
+                                                  uint32_t cap) {
+  if (h >= cap) return 0;
+  const uintptr_t a = (uintptr_t)(chars + off + h);
+  const uint64_t* p = (const uint64_t*)(a & ~(uintptr_t)7);
+  const uint32_t sh = (uint32_t)(a & 7);
+  const bool same_block = (((uintptr_t)(p + 1)) & 4095u) != 0;
+  const uint64_t w0 = __ldg(p);
+  uint64_t w1 = (sh && same_block) ? __ldg(p + 1) : 0ull;
+  uint64_t v = w0 >> (8 * sh);
+  const uint32_t room = cap - h;
+  uint32_t z;
+  if (sh == 0) {
+    z = first_zero_byte(v);
+  } else {
+    const uint32_t nb0 = 8 - sh;
+    z = first_zero_byte(v | (~0ull << (8 * nb0)));
+    if (z >= nb0 && room > nb0) {
+      if (!same_block) w1 = __ldg(p + 1);
+      v |= w1 << (8 * nb0);
+      z = first_zero_byte(v);
+    }
+  }
+  uint32_t keep = z < room ? z : room;
+  if (keep < 8) v &= (keep == 0) ? 0ull : (~0ull >> (64 - 8 * keep));
+  return bswap64(v);
+}
+
 constexpr int kLookWindows = 8;  // look-ahead: 8 windows = 64 characters per round
 
 // Look-ahead read for the refinement of long common prefixes: the KW windows

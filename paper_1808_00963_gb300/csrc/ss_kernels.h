@@ -54,4 +54,32 @@ cudaError_t launch_distinguishing(const uint8_t* chars, const uint64_t* offsets,
                                   const uint32_t* perm, const uint32_t* lcp, uint8_t* dchar, uint32_t* dprefix,
                                   unsigned long long* sum_d, uint32_t grid, cudaStream_t st, const LaunchHook& hook);
 
+// K-way LCP merge of sorted runs (ss_merge.cu).
+constexpr uint32_t kMergeMaxRuns = 64;
+
+struct MergeRun {
+  const uint32_t* perm;
+  const uint32_t* lcp;
+  uint32_t n;
+  uint32_t sample_base;   // index of the run's first sample
+};
+
+struct MergeParams {
+  const uint8_t* chars;
+  const uint64_t* offsets;
+  uint32_t* cut;          // C x K cut vectors
+  uint32_t* rank;         // C sample ranks
+  uint32_t* out_perm;
+  uint32_t* out_lcp;      // may be null
+  uint32_t* next_piece;   // piece counter (zero at launch)
+  uint32_t cap;           // strings end after cap characters
+  uint32_t K;             // runs, a power of two (unused runs are empty)
+  uint32_t S;             // every S-th string of a run is a sample
+  uint32_t C;             // samples
+  MergeRun run[kMergeMaxRuns];
+};
+
+cudaError_t launch_merge(const MergeParams& m, uint32_t logk, uint32_t sms, cudaStream_t st,
+                         const LaunchHook& hook);
+
 }  // namespace ss

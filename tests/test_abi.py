@@ -81,3 +81,50 @@ def test_workspace_size(lib):
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(RuntimeError):
         ss.load(str(tmp_path / "nope.so"))
+
+
+def test_merge_argument_checks(lib):
+    dummy = ctypes.c_void_p(4096)
+    runs = (ss.RunDesc * 65)()
+    for r in runs:
+        r.perm = r.lcp = 4096
+        r.n = 100
+    call = lambda k, step=0, chars=dummy, out=dummy: lib.ss_merge(  # noqa: E731
+        chars, dummy, 0, runs, k, step, out, None, None, 0, None)
+    assert call(0) == 1                      # no runs
+    assert call(65) == 1                     # more than SS_MERGE_MAX_RUNS
+    assert call(3, step=8) == 1              # sample step out of range
+    assert call(3, step=1 << 17) == 1
+    assert call(3, chars=None) == 1          # NULL chars with strings to merge
+    assert call(3, out=None) == 1            # NULL output
+    runs[1].reserved = 1
+    assert call(3) == 1
+    runs[1].reserved = 0
+    runs[2].perm = None
+    assert call(3) == 1                      # NULL run with n > 0
+    runs[2].perm = 4096
+    empty = (ss.RunDesc * 2)()
+    assert lib.ss_merge(None, None, 0, empty, 2, 0, None, None, None, 0, None) == 0  # nothing to merge
+    big = (ss.RunDesc * 2)()
+    for r in big:
+        r.perm = r.lcp = 4096
+        r.n = 0x80000000
+    assert lib.ss_merge(dummy, dummy, 0, big, 2, 0, dummy, None, None, 0, None) == 4
+    # misaligned or short caller workspace
+    assert lib.ss_merge(dummy, dummy, 0, runs, 3, 16, dummy, None, ctypes.c_void_p(4096 + 8), 1 << 20, None) == 1
+    assert lib.ss_merge(dummy, dummy, 0, runs, 3, 16, dummy, None, ctypes.c_void_p(4096), 1, None) == 1
+    if not _has_gpu():
+        assert call(3) == 7
+
+
+def test_merge_workspace_size(lib):
+    runs = (ss.RunDesc * 3)()
+    for r, n in zip(runs, (1000, 50, 3000)):
+        r.perm = r.lcp = 4096
+        r.n = n
+    # samples: 1000 // 64 + 50 // 64 + 3000 // 64 = 15 + 0 + 46; 4 padded runs
+    c = 15 + 46
+    # cut vectors, sample ranks, the piece counter
+    assert lib.ss_merge_workspace_size(runs, 3, 64) == ((c * 4 * 4 + 255) // 256 + (c * 4 + 255) // 256 + 1) * 256
+    assert lib.ss_merge_workspace_size(runs, 3, 4096) == 256   # one piece: the counter only
+    assert lib.ss_merge_workspace_size(runs, 0, 0) == 0
