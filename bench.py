@@ -7,7 +7,11 @@ step = one complete sort through the C-ABI (ss_sort_ex), producing the
 permutation and the LCP array.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--config c1|c2|c3|c4]
+                  [--config c1|c2|c3|c4|c5|m2]
+
+--config m2 times the K-way LCP merge instead: 16 sorted runs (a seeded
+partition of the 20 M URL-like strings, each run sorted on the GPU before the
+timed region) merged into one sorted order with its LCP array per step.
 
 --impl reference times the CPU oracle (single thread) on a bounded sample of
 the same workload.  Under torchrun (N > 1) every rank sorts its own copy of
@@ -203,12 +207,48 @@ def ncu_traffic(kernel: str, config: str):
     return e.get("dram_bytes_per_launch")
 
 
+MERGE_RUNS = 16
+MERGE_SAMPLE = 2_000_000
+
+
+def merge_assign(n: int, K: int = MERGE_RUNS):
+    """The seeded partition of the strings into K runs."""
+    return np.random.default_rng(5).integers(0, K, n)
+
+
+def cpu_merge_runs(s, sample: int, K: int = MERGE_RUNS):
+    """Sorted runs (with LCP arrays) of the first `sample` strings, made by the
+    oracle: the inputs of the oracle's merge."""
+    import oracle
+    a = merge_assign(s.n, K)[:sample]
+    offs = np.ascontiguousarray(s.offsets[:sample])
+    runs = []
+    for k in range(K):
+        sub = np.nonzero(a == k)[0].astype(np.uint32)
+        p, l = oracle.sort(s.chars, offs[sub], s.max_len)
+        runs.append((sub[p], l))
+    return offs, runs
+
+
+def time_oracle_merge(s, sample: int, reps: int):
+    import oracle
+    offs, runs = cpu_merge_runs(s, sample)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.lcp_merge(s.chars, offs, runs, s.max_len)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
 # ---- reference arm: the CPU oracle ----------------------------------------------------------
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return
     import oracle
+    if args.config == "m2":
+        return run_reference_merge(args)
     s, desc = workload(args.config)
     # each step sorts a bounded sample of the workload (the first strings,
     # generated i.i.d.) sized so that all warm-up and timed steps take about
@@ -232,6 +272,28 @@ def run_reference(args, ws, rank):
         "config": {"workload": desc, "n": s.n, "sample_strings": sample, "parallelism": "cpu, 1 thread"},
         "cpu_baseline": {"value": v, "unit": "strings/s", "cores": cores, "kind": "oracle",
                          "sample": f"first {sample} of the {s.n} strings (generated i.i.d.), same buffer"},
+        "e2e": {"value": v, "unit": "strings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_merge(args):
+    """The oracle's K-way LCP merge (Algorithm 4.5, one character per
+    comparison) on the runs of a bounded sample of the merge workload."""
+    s = gen.config2()
+    per_step = int(30e6 / max(1, args.steps + args.warmup))
+    sample = max(20_000, min(per_step, MERGE_SAMPLE, s.n))
+    times = time_oracle_merge(s, sample, args.warmup + args.steps)[args.warmup:]
+    dt = sum(times)
+    v = sample * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "merged strings/s (K-way LCP merge)", "value": v, "unit": "strings/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": f"K-way LCP merge of {MERGE_RUNS} sorted runs of URL-like strings",
+                   "sample_strings": sample, "parallelism": "cpu, 1 thread"},
+        "cpu_baseline": {"value": v, "unit": "strings/s", "cores": 1, "kind": "oracle",
+                         "sample": f"the {MERGE_RUNS} runs restricted to the first {sample} of the {s.n} strings"},
         "e2e": {"value": v, "unit": "strings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -362,6 +424,135 @@ def run_ours(args, ws, rank, local):
             "gpu_launches": launches,
             "clocks": clocks,
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 4), "alg_bytes": v[2]} for k, v in stats.items()},
+        }
+        print(json.dumps(line), flush=True)
+
+
+# ---- K-way LCP merge of sorted runs ------------------------------------------------------------
+
+# algorithmic bytes per merged string: its index and LCP entry read from its
+# run (8), its offset (8), one 8-character window (8), index and LCP written (8)
+MERGE_BYTES_PER_STRING = 32
+
+
+def run_merge(args, ws, rank, local):
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    ss.load()
+    s = gen.config2(args.n) if args.n else gen.config2()
+    K = MERGE_RUNS
+    desc = (f"K-way LCP merge of {K} sorted runs: a seeded partition of {s.n} URL-like strings "
+            "(~59 B mean, Zipf(1.1) over 2000 hosts), each run sorted on the GPU before timing")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    chars = torch.from_numpy(s.chars).to(dev)
+    offsets = torch.from_numpy(s.offsets.view(np.int64)).to(dev)
+    assign = torch.from_numpy(merge_assign(s.n, K)).to(dev)
+    runs = []
+    for k in range(K):
+        sub = torch.nonzero(assign == k).flatten()
+        p, l = ss.sort(chars, offsets[sub].contiguous(), max_len=s.max_len)
+        runs.append((sub[p.long()].int().contiguous(), l))
+    del assign
+    n = s.n
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    wsb = ss.merge_workspace_size(runs)
+    work = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ss.merge(chars, offsets, runs, max_len=s.max_len, out=(perm, lcp), workspace=work.data_ptr(),
+                 workspace_bytes=wsb)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ss.reset_kernel_stats()
+    ss.set_profiling(True)
+    sampler = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = ss.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(t_start, time.perf_counter())
+    launches = ss.launch_count() - launches0
+    stats = ss.kernel_stats()
+    barrier(ws)
+    clocks = sampler.stop()
+    ss.set_profiling(False)
+    ms, value = weak_scaling_value(e0.elapsed_time(e1), ws, n, args.steps)
+
+    peak, peak_kind = measured_peaks()
+    roof = None
+    if "merge_pieces" in stats:
+        nl, kms, _ = stats["merge_pieces"]
+        kbytes = MERGE_BYTES_PER_STRING * n
+        achieved = kbytes / (kms / nl / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": "merge_pieces", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": ncu_traffic("merge_pieces", "m2"), "alg_bytes_per_launch": kbytes,
+                "alg_bytes_per_string": MERGE_BYTES_PER_STRING, "launches": nl, "ms_per_launch": kms / nl,
+                "kernel_share": {k: round(v[1] / sum(x[1] for x in stats.values()), 4) for k, v in stats.items()}}
+
+    # end to end: runs, characters and offsets copied from pinned host memory,
+    # the merged order and LCP array copied back, every step
+    e2e = None
+    if not args.no_e2e:
+        h_chars = torch.from_numpy(s.chars).pin_memory()
+        h_offs = torch.from_numpy(s.offsets.view(np.int64)).pin_memory()
+        h_runs = [(p.cpu().pin_memory(), l.cpu().pin_memory()) for p, l in runs]
+        h_perm = torch.empty(n, dtype=torch.int32).pin_memory()
+        h_lcp = torch.empty(n, dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            d_chars = h_chars.to(dev, non_blocking=True)
+            d_offs = h_offs.to(dev, non_blocking=True)
+            d_runs = [(p.to(dev, non_blocking=True), l.to(dev, non_blocking=True)) for p, l in h_runs]
+            ss.merge(d_chars, d_offs, d_runs, max_len=s.max_len, out=(perm, lcp), workspace=work.data_ptr(),
+                     workspace_bytes=wsb)
+            h_perm.copy_(perm, non_blocking=True)
+            h_lcp.copy_(lcp, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        e2e_step()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        et = max_over_ranks(time.perf_counter() - t0, ws)
+        e2e = {"value": ws * n * args.steps / et, "unit": "strings/s",
+               "h2d_bytes_per_step": int(s.N + 8 * n + 8 * n), "d2h_bytes_per_step": int(8 * n),
+               "ms_per_step": et / args.steps * 1e3}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sample = min(MERGE_SAMPLE, n)
+        t = statistics.median(time_oracle_merge(s, sample, 3))
+        cpu = {"value": sample / t, "unit": "strings/s", "cores": 1, "kind": "oracle",
+               "sample": (f"Algorithm 4.5 as written in the oracle (one character per comparison) on the "
+                          f"{K} runs restricted to the first {sample} strings, median of 3, single thread")}
+    if rank == 0:
+        line = {
+            "metric": "merged strings/s (K-way LCP merge)", "value": value, "unit": "strings/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": desc, "n": n, "runs": K, "N": s.N,
+                       "l2": f"inputs larger than L2 (characters {s.N / 1e9:.2f} GB)",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "per_step": "one merge: permutation + LCP array",
+                       "sample_step": "default"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in stats.items()},
         }
         print(json.dumps(line), flush=True)
 
@@ -516,12 +707,12 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "m2"])
     ap.add_argument("--requests", type=int, default=150, help="number of requests (c5)")
     ap.add_argument("--sets", type=int, default=4096, help="number of sets (c4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--n", type=int, default=None, help="reduced string count (c2 only; profiler captures)")
+    ap.add_argument("--n", type=int, default=None, help="reduced string count (c2 and m2; profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
@@ -532,6 +723,8 @@ def main():
         run_batch(args, ws, rank, local)
     elif args.config == "c5":
         run_served(args, ws, rank, local)
+    elif args.config == "m2":
+        run_merge(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -509,8 +509,8 @@ ss_status ss_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint6
 
 static uint32_t merge_step(uint64_t total, uint32_t sample_step) {
   if (sample_step) return sample_step;
-  uint32_t s = 64;  // about 2^16 pieces for large inputs, pieces of 64..2048 strings
-  while (s < 2048 && (uint64_t)s * 2 * 65536 <= total) s *= 2;
+  uint32_t s = 64;  // about 2^17 pieces for large inputs, pieces of 64..2048 strings
+  while (s < 2048 && (uint64_t)s * 2 * 131072 <= total) s *= 2;
   return s;
 }
 

@@ -186,6 +186,14 @@ __device__ __forceinline__ uint64_t finish_window(uint64_t v, uint32_t room) {
   return bswap64(v);
 }
 
+// The window at depth h of a Raw16.
+__device__ __forceinline__ uint64_t finish8(const MergeParams& m, const Raw16& r) {
+  if (r.h >= m.cap) return 0;
+  if (!r.ok) return cache_at(m, r.off, r.h);
+  const uint32_t sh = (uint32_t)((uintptr_t)(m.chars + r.off + r.h) & 7) * 8;
+  return finish_window(sh ? (r.x0 >> sh) | (r.x1 << (64 - sh)) : r.x0, m.cap - r.h);
+}
+
 // The windows at depths h and h + 8 of a Raw16.
 __device__ __forceinline__ void finish16(const MergeParams& m, const Raw16& r, uint64_t& w0, uint64_t& w1) {
   if (r.h >= m.cap) {
@@ -278,7 +286,11 @@ __device__ __forceinline__ void slot_advance(const MergeParams& m, const MergeRu
   s.fh = s.nr.h;
   s.fr = s.nr;
   s.fpend = false;
-  if (s.pos < s.end) finish16(m, s.nr, s.fw0, s.fw1);
+  if (s.pos < s.end) {
+    s.fw0 = finish8(m, s.nr);
+    s.fpend = !has_nul(s.fw0);  // w1 is read out of the same words when first needed
+    if (!s.fpend) s.fw1 = 0;
+  }
   s.nidx = s.n2idx;
   if (s.pos + 1 < s.end) raw16_issue(m, s.n2off, s.n2h, s.nr);
   slot_fetch(m, r, s.pos + 2, s.end, s.n2idx, s.n2h, s.n2off);
@@ -381,15 +393,35 @@ __global__ void __launch_bounds__(kMergeBlock) k_merge_pieces(MergeParams m) {
       if (H1 == 0) break;
       const uint32_t H = H1 - 1;
       bool cand[NS];
-      uint64_t cm = ~0ull;
+      uint32_t ncand = 0, cslot = 0;
 #pragma unroll
       for (int t = 0; t < NS; ++t) {
         cand[t] = sl[t].pos < sl[t].end && sl[t].fh == H;
-        if (cand[t] && sl[t].fw0 < cm) cm = sl[t].fw0;
+        const uint32_t b = __ballot_sync(gm, cand[t]);
+        if (b) cslot = t * G + (__ffs(b) - 1) % G;
+        ncand += __popc(b);
       }
-      const uint64_t cmin = group_min_u64(gm, cm);
       bool in[NS];
       uint32_t lw[NS];
+      uint32_t wid, imin;
+      if (ncand == 1) {
+        // one front has the largest LCP with the last output: it goes first
+        // (cases 2/3 of LCP-Compare), and no other front's LCP changes
+        wid = cslot;
+        uint32_t wi = 0;
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+          in[t] = cand[t];
+          lw[t] = sl[t].fh;
+          if (cand[t]) wi = sl[t].fidx;
+        }
+        imin = __shfl_sync(gm, wi, gr.g * G + wid % G);
+      } else {
+      uint64_t cm = ~0ull;
+#pragma unroll
+      for (int t = 0; t < NS; ++t)
+        if (cand[t] && sl[t].fw0 < cm) cm = sl[t].fw0;
+      const uint64_t cmin = group_min_u64(gm, cm);
       uint32_t nin = 0;
 #pragma unroll
       for (int t = 0; t < NS; ++t) {
@@ -429,12 +461,13 @@ __global__ void __launch_bounds__(kMergeBlock) k_merge_pieces(MergeParams m) {
 #pragma unroll
       for (int t = 0; t < NS; ++t)
         if (in[t] && sl[t].fidx < im) im = sl[t].fidx;
-      const uint32_t imin = __reduce_min_sync(gm, im);
+      imin = __reduce_min_sync(gm, im);
       uint32_t id = 0xFFFFFFFFu;
 #pragma unroll
       for (int t = 0; t < NS; ++t)
         if (in[t] && sl[t].fidx == imin && t * G + gr.glane < id) id = t * G + gr.glane;
-      const uint32_t wid = __reduce_min_sync(gm, id);
+      wid = __reduce_min_sync(gm, id);
+      }
       const uint32_t wlane = gr.g * G + wid % G;
       uint32_t olcp = H;
       if (first) {

@@ -110,14 +110,14 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
   build_splitters<LOGV>(recs, t.len, mix64(c.seed ^ ((uint64_t)t.begin << 20) ^ t.depth), s.sp, s.u.bs);
   unsigned long long bytes = threadIdx.x == 0 ? Gm::S * 8ull : 0ull;
 
-  // lines 6-14: classify into the array o and count
+  // classification (Algorithm 4.1): classify into the array o and count
   for (uint32_t b = threadIdx.x; b < Gm::KP; b += kBlock) s.hist[b] = 0;
   __syncthreads();
   uint16_t* bo = c.bucket_of + t.begin;
   bytes += 10ull * classify_count<LOGV>(recs, bo, t.len, s.sp.tree, s.sp.x, s.hist, c.classifier);
   __syncthreads();
 
-  // line 15: prefix sum; bucket outcomes
+  // prefix sum over the bucket sizes; bucket outcomes
   block_excl_scan_smem(s.hist, s.bstart, Gm::KP);  // bstart[K] = len (hist[K] is 0)
   for (uint32_t b = threadIdx.x; b < Gm::K; b += kBlock) {
     const uint32_t size = s.hist[b];
@@ -126,7 +126,7 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
   }
   __syncthreads();
 
-  // line 16: stable out-of-place redistribution, tile by tile
+  // redistribution: stable and out of place, tile by tile
   const uint32_t T = kBlock * R;
   for (uint32_t t0 = 0; t0 < t.len; t0 += T) {
     const uint32_t tl = min(T, t.len - t0);

@@ -57,7 +57,7 @@ __device__ void block_bitonic_u64(uint64_t* a) {
   }
 }
 
-// Lines 1-5 of Algorithm 4.1 for the len keys at `keys`: draw a sample of
+// The sampling steps of Algorithm 4.1 for the len keys at `keys`: draw a sample of
 // alpha * (v + 1) keys at pseudo-random positions, sort it, select the
 // splitters with the recursive duplicate-skipping rule of Section 4.2.3
 // ("Sampling"): the middle sample of a range becomes the splitter, the ranges
@@ -66,7 +66,7 @@ __device__ void block_bitonic_u64(uint64_t* a) {
 // A node whose range is empty takes the sample just above its range (the
 // nearest splitter on the right among its ancestors), or all-ones past the
 // end, which keeps t a search tree.  Finally h'_i = lcp(x_{i-1}, x_i) with
-// h'_0 = h'_v = 0 (line 5).  Ends with __syncthreads().
+// h'_0 = h'_v = 0, the splitter LCPs of Algorithm 4.1.  Ends with __syncthreads().
 template <int LOGV>
 __device__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint64_t hseed,
                                 Splitters<LOGV>& sp, BuildScratch<LOGV>& bs) {
@@ -137,8 +137,8 @@ constexpr uint32_t kClassifyUI = 0;   // unrolled <=-descent, equality test on t
 constexpr uint32_t kClassifyUIC = 1;  // same descent, equality test in t via Lemma 4.1 (no copy needed)
 constexpr uint32_t kClassifyE = 2;    // equality test at every node of the descent
 
-// Lines 7-11 of Algorithm 4.1: branch-free descent of the level-order tree,
-// i := 2i + [c > t_i] (the reading of line 9 under which bucket b_{2r} holds
+// The classification of one key in Algorithm 4.1: branch-free descent of the level-order tree,
+// i := 2i + [c > t_i] (the reading of its descent step under which bucket b_{2r} holds
 // x_{r-1} < c < x_r), then the single equality test with x_r.
 template <int LOGV>
 __device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, const uint64_t* x,
@@ -163,7 +163,7 @@ __device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, c
   return 2 * r + (eq ? 1u : 0u);
 }
 
-// Classifies n keys (lines 6-14 of Algorithm 4.1): writes the bucket of
+// Classifies n keys (the classification loop of Algorithm 4.1): writes the bucket of
 // keys[p] to bo[p] and counts it in hist (shared memory, warp-aggregated
 // atomics).  Each thread loads 8 keys before descending the tree for them,
 // so that the loads of a batch overlap.  Returns this thread's records.
@@ -224,7 +224,7 @@ __device__ __forceinline__ uint32_t bucket_desc(uint32_t b, uint32_t size, uint3
 constexpr int kMoveBatch = 8;
 constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 
-// Stable distribution of one tile of records (Algorithm 4.1 line 16 with the
+// Stable distribution of one tile of records (the redistribution of Algorithm 4.1 with the
 // per-processor bucket arrays of Theorem 4.4, one per warp).
 //   tb[0..tl)    bucket of each record of the tile (shared memory)
 //   base[b]      in: destination of the tile's first record of bucket b;
@@ -287,7 +287,7 @@ __device__ void tile_scatter(const uint16_t* tb, uint32_t tl, uint32_t R, uint32
   __syncthreads();
 }
 
-// Moves a batch of records to their buckets (the body of line 16): a finished
+// Moves a batch of records to their buckets (the body of the redistribution): a finished
 // record writes its final index (and, inside a bucket of equal strings, its
 // LCP); an open one is copied to the other buffer with its cache reloaded at
 // the bucket's new depth (fused character gather).  All loads of the batch
