@@ -7,8 +7,10 @@ step = one complete sort through the C-ABI (ss_sort_ex), producing the
 permutation and the LCP array.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--config c1|c2|c3|c4|c5|m2]
+                  [--config c1|c2|c3|c4|c5|m2|s3]
 
+--config s3 times suffix array construction (prefix doubling on top of the
+sort) of the 4 M-character DNA-like text of configuration 3, uncapped.
 --config m2 times the K-way LCP merge instead: 16 sorted runs (a seeded
 partition of the 20 M URL-like strings, each run sorted on the GPU before the
 timed region) merged into one sorted order with its LCP array per step.
@@ -249,6 +251,8 @@ def run_reference(args, ws, rank):
     import oracle
     if args.config == "m2":
         return run_reference_merge(args)
+    if args.config == "s3":
+        return run_reference_sa(args)
     s, desc = workload(args.config)
     # each step sorts a bounded sample of the workload (the first strings,
     # generated i.i.d.) sized so that all warm-up and timed steps take about
@@ -557,6 +561,143 @@ def run_merge(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+# ---- suffix array by prefix doubling ------------------------------------------------------------
+
+SA_SAMPLE = 2_000_000
+
+
+def sa_text():
+    s = gen.config3()
+    return bytes(s.chars[:s.n]), s
+
+
+def time_oracle_sa(text: bytes, reps: int):
+    import oracle
+    oracle.load()
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.suffix_array(text)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def run_reference_sa(args):
+    text, _ = sa_text()
+    per_step = int(15e6 / max(1, args.steps + args.warmup))
+    sample = max(100_000, min(per_step, SA_SAMPLE, len(text)))
+    times = time_oracle_sa(text[:sample], args.warmup + args.steps)[args.warmup:]
+    dt = sum(times)
+    v = sample * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "suffixes/s (suffix array + LCP array)", "value": v, "unit": "suffixes/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": "suffix array of a DNA-like text", "sample_chars": sample,
+                   "parallelism": "cpu, 1 thread"},
+        "cpu_baseline": {"value": v, "unit": "suffixes/s", "cores": 1, "kind": "oracle",
+                         "sample": f"suffix array of the first {sample} characters of the text"},
+        "e2e": {"value": v, "unit": "suffixes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_sa(args, ws, rank, local):
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    ss.load()
+    text, s = sa_text()
+    n = len(text)
+    desc = (f"suffix array + LCP array of all {n} suffixes of a DNA-like text (order-3 Markov, 5 % duplicated "
+            "1000-character blocks), uncapped, by prefix doubling on the string sort")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d_text = torch.from_numpy(np.frombuffer(text + b"\0", np.uint8).copy()).to(dev)
+    sa = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ss.suffix_array(d_text, n, out=(sa, lcp))
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    ss.reset_kernel_stats()
+    ss.set_profiling(True)
+    sampler = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    launches0 = ss.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start = time.perf_counter()
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(t_start, time.perf_counter())
+    launches = ss.launch_count() - launches0
+    stats = ss.kernel_stats()
+    barrier(ws)
+    clocks = sampler.stop()
+    ss.set_profiling(False)
+    ms, value = weak_scaling_value(e0.elapsed_time(e1), ws, n, args.steps)
+    peak, peak_kind = measured_peaks()
+    roof = None
+    counted = {k: v for k, v in stats.items() if v[2] > 0}
+    if counted:
+        name, (nl, kms, kbytes) = max(counted.items(), key=lambda kv: kv[1][1])
+        achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if kms > 0 else 0.0
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": None, "alg_bytes_per_launch": kbytes / nl, "launches": nl, "ms_per_launch": kms / nl,
+                "kernel_share": {k: round(v[1] / sum(x[1] for x in stats.values()), 4) for k, v in stats.items()}}
+    e2e = None
+    if not args.no_e2e:
+        h_text = torch.from_numpy(np.frombuffer(text + b"\0", np.uint8).copy()).pin_memory()
+        h_sa = torch.empty(n, dtype=torch.int32).pin_memory()
+        h_lcp = torch.empty(n, dtype=torch.int32).pin_memory()
+
+        def e2e_step():
+            t = h_text.to(dev, non_blocking=True)
+            ss.suffix_array(t, n, out=(sa, lcp))
+            h_sa.copy_(sa, non_blocking=True)
+            h_lcp.copy_(lcp, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        e2e_step()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        et = max_over_ranks(time.perf_counter() - t0, ws)
+        e2e = {"value": ws * n * args.steps / et, "unit": "suffixes/s", "h2d_bytes_per_step": n + 1,
+               "d2h_bytes_per_step": 8 * n, "ms_per_step": et / args.steps * 1e3}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        sample = min(SA_SAMPLE, n)
+        t = statistics.median(time_oracle_sa(text[:sample], 3))
+        cpu = {"value": sample / t, "unit": "suffixes/s", "cores": 1, "kind": "oracle",
+               "sample": f"the oracle's sort of all suffixes of the first {sample} characters, median of 3, "
+                         "single thread"}
+    if rank == 0:
+        line = {
+            "metric": "suffixes/s (suffix array + LCP array)", "value": value, "unit": "suffixes/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic",
+            "config": {"workload": desc, "n": n, "l2": "text 4 MB; suffix array, names and LCPs 16 MB each",
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "per_step": "one suffix array + LCP array", "initial_depth": "default (64)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in stats.items()},
+        }
+        print(json.dumps(line), flush=True)
+
+
 # ---- batched workload (configuration 4) ---------------------------------------------------------
 
 def run_batch(args, ws, rank, local):
@@ -707,7 +848,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "m2"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "m2", "s3"])
     ap.add_argument("--requests", type=int, default=150, help="number of requests (c5)")
     ap.add_argument("--sets", type=int, default=4096, help="number of sets (c4)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -725,6 +866,8 @@ def main():
         run_served(args, ws, rank, local)
     elif args.config == "m2":
         run_merge(args, ws, rank, local)
+    elif args.config == "s3":
+        run_sa(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

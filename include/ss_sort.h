@@ -184,6 +184,28 @@ ss_status ss_merge(const uint8_t* chars, const uint64_t* offsets, uint32_t max_l
  * arguments). */
 size_t ss_merge_workspace_size(const ss_run* runs, uint32_t num_runs, uint32_t sample_step);
 
+/* ---- suffix array by prefix doubling ---------------------------------------- */
+
+/* Suffix array (and LCP array) of a text, by prefix doubling on top of the
+ * string sort (Section 8.2: Observation 8.1, Algorithms 8.1 and 8.3).  Round
+ * 0 sorts all suffixes by their first `initial_depth` characters (the string
+ * sort with that cap; 0 = 64, at most 2^20); every later round sorts only the
+ * suffixes of groups that are still tied, by the name pair of Observation
+ * 8.1, doubling the sorted depth, until every group is a single suffix.
+ *   text     DEVICE pointer to n bytes in 1..255 followed by a zero byte
+ *            (text[n] = 0).
+ *   out_sa   uint32[n] (device): out_sa[j] = start of the j-th smallest
+ *            non-empty suffix (the empty suffix at n is not listed).
+ *   out_lcp  uint32[n] (device) or NULL: out_lcp[0] = 0, out_lcp[j] = lcp of
+ *            the suffixes out_sa[j-1] and out_sa[j].
+ * Synchronous: waits for the result (the host reads the number of unsorted
+ * suffixes after each round).  Device memory of about 63 bytes per text
+ * character is taken from the stream-ordered pool for the call.  Returns
+ * SS_ERR_TOO_LARGE for n >= 2^32 - 2, SS_ERR_INVALID for NULL pointers or
+ * initial_depth > 2^20. */
+ss_status ss_suffix_array(const uint8_t* text, uint64_t n, uint32_t* out_sa, uint32_t* out_lcp,
+                          uint32_t initial_depth, void* stream);
+
 /* ---- batched sorting: many independent string sets in one launch ----------- */
 
 /* One string set of a batch (device pointers, as for ss_sort). */

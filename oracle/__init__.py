@@ -230,6 +230,43 @@ def lcp_merge(chars, offsets, runs, max_len: int = 0, lib=None):
     return perm[:n], lcp[:n], int(cmps.value)
 
 
+def h_names(chars, offsets, h: int, lib=None):
+    """Section 8.2.1: the h-name of every string (the smallest rank of its
+    group under the order limited to the first h characters), i.e. the
+    inverse h-suffix array ISA^h when the strings are the suffixes of a text.
+    By definition: the position, in the sort capped at h, of the first string
+    whose capped prefix equals its own."""
+    perm, lcp = sort(chars, offsets, h, lib=lib)
+    n = perm.shape[0]
+    names = np.empty(n, np.uint32)
+    start = 0
+    for j in range(n):
+        if j == 0 or not _capped_equal(chars, offsets, perm[j - 1], perm[j], h):
+            start = j
+        names[perm[j]] = start
+    return names
+
+
+def _capped_equal(chars, offsets, a, b, h):
+    """The first h characters of strings a and b agree, terminators included."""
+    oa, ob = int(offsets[a]), int(offsets[b])
+    for k in range(h):
+        ca, cb = int(chars[oa + k]), int(chars[ob + k])
+        if ca != cb:
+            return False
+        if ca == 0:
+            return True
+    return True
+
+
+def suffix_array(text: bytes, lib=None):
+    """Suffix array and LCP array of a text (its n non-empty suffixes), by
+    definition: the sort of all suffixes."""
+    chars = np.frombuffer(bytes(text) + b"\0", np.uint8).copy()
+    offsets = np.arange(len(text), dtype=np.uint64)
+    return sort(chars, offsets, 0, lib=lib)
+
+
 def from_strings(strs, max_len: int = 0):
     """Helper for small fixtures: list of bytes -> (chars, offsets)."""
     buf = bytearray()

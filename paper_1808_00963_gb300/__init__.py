@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_BUILD, "libss_sort.so")
 ROOT = os.path.dirname(_HERE)
 HEADER = os.path.join(ROOT, "include", "ss_sort.h")
 
-SOURCES = ["ss_host.cu", "ss_big.cu", "ss_queue.cu", "ss_small.cu", "ss_merge.cu"]
+SOURCES = ["ss_host.cu", "ss_big.cu", "ss_queue.cu", "ss_small.cu", "ss_merge.cu", "ss_sa.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
                      "-Xcompiler", "-Wall"]
@@ -177,6 +177,8 @@ def load(path: str | None = None):
     lib.ss_merge.restype = i32
     lib.ss_merge_workspace_size.argtypes = [ctypes.POINTER(RunDesc), u32, u32]
     lib.ss_merge_workspace_size.restype = ctypes.c_size_t
+    lib.ss_suffix_array.argtypes = [vp, u64, vp, vp, u32, vp]
+    lib.ss_suffix_array.restype = i32
     if path is None:
         _lib = lib
     return lib
@@ -288,6 +290,27 @@ def merge(chars, offsets, runs, max_len: int = 0, with_lcp: bool = True, out=Non
                       ctypes.c_void_p(workspace) if workspace else None, workspace_bytes, _stream_ptr(stream))
     _check(rc, "ss_merge")
     return perm, lcp
+
+
+def suffix_array(text, n: int | None = None, with_lcp: bool = True, initial_depth: int = 0, out=None,
+                 stream=None):
+    """Suffix array (int32) and LCP array of a text held on the device as n
+    bytes in 1..255 followed by a zero byte (Section 8.2, prefix doubling on
+    top of the string sort)."""
+    import torch
+    lib = load()
+    if n is None:
+        n = int(text.numel()) - 1
+    if out is None:
+        sa = torch.empty(n, dtype=torch.int32, device=text.device)
+        lcp = torch.empty(n, dtype=torch.int32, device=text.device) if with_lcp else None
+    else:
+        sa, lcp = out
+    rc = lib.ss_suffix_array(ctypes.c_void_p(text.data_ptr()), n, ctypes.c_void_p(sa.data_ptr()),
+                             ctypes.c_void_p(lcp.data_ptr()) if lcp is not None else None, initial_depth,
+                             _stream_ptr(stream))
+    _check(rc, "ss_suffix_array")
+    return sa, lcp
 
 
 def sort_host(chars, offsets, max_len: int = 0, with_lcp: bool = True, perm=None, lcp=None, stream=None,

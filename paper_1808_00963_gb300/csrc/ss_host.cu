@@ -596,6 +596,138 @@ ss_status ss_merge(const uint8_t* chars, const uint64_t* offsets, uint32_t max_l
   return s;
 }
 
+// ---- suffix array by prefix doubling --------------------------------------------------
+
+ss_status ss_suffix_array(const uint8_t* text, uint64_t n, uint32_t* out_sa, uint32_t* out_lcp,
+                          uint32_t initial_depth, void* stream) {
+  if (n >= 0xFFFFFFFEull) return SS_ERR_TOO_LARGE;
+  if (n == 0) return SS_OK;
+  if (!text || !out_sa) return SS_ERR_INVALID;
+  if (initial_depth > (1u << 20)) return SS_ERR_INVALID;
+  const uint32_t h0 = initial_depth ? initial_depth : 64;
+  DevInfo dev;
+  ss_status s = device_info(dev);
+  if (s != SS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // workspace: offsets, capped LCPs (unless out_lcp holds them), names, group
+  // starts, flags, two compacted position lists, scan totals, and per round
+  // the members, their encoded name pairs, offsets and sorted order / LCPs
+  const size_t a4 = align256(n * 4), a8 = align256(n * 8);
+  const size_t tot_b = align256(sa_scan_totals(n) * 4);
+  const size_t need = a8 + (out_lcp ? 0 : a4) + 7 * a4 + tot_b + align256(n * 11 + 16) + a8;
+  uint8_t* ws = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), need, st) != cudaSuccess) return SS_ERR_OOM;
+  uint8_t* p = ws;
+  auto take = [&](size_t b) { uint8_t* q = p; p += b; return q; };
+  uint64_t* off = reinterpret_cast<uint64_t*>(take(a8));
+  uint32_t* lcp0 = out_lcp ? out_lcp : reinterpret_cast<uint32_t*>(take(a4));
+  uint32_t* isa = reinterpret_cast<uint32_t*>(take(a4));
+  uint32_t* gs = reinterpret_cast<uint32_t*>(take(a4));
+  uint32_t* flag = reinterpret_cast<uint32_t*>(take(a4));
+  uint32_t* cpos[2] = {reinterpret_cast<uint32_t*>(take(a4)), reinterpret_cast<uint32_t*>(take(a4))};
+  uint32_t* member = reinterpret_cast<uint32_t*>(take(a4));
+  uint32_t* perm2 = reinterpret_cast<uint32_t*>(take(a4));
+  uint32_t* tot = reinterpret_cast<uint32_t*>(take(tot_b));
+  uint8_t* enc = take(align256(n * 11 + 16));
+  uint64_t* eoff = reinterpret_cast<uint64_t*>(take(a8));
+  uint32_t* lcp2 = reinterpret_cast<uint32_t*>(off);  // the offsets of round 0 are dead by then
+  const LaunchHook hook{st};
+  auto grid_for = [&](uint64_t m) {
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((m + 255) / 256, (uint64_t)dev.sms * 32));
+  };
+  auto read_u32 = [&](const uint32_t* d, uint32_t* h) {
+    return cudaMemcpyAsync(h, d, 4, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+           cudaStreamSynchronize(st) == cudaSuccess;
+  };
+  SaArgs x;
+  x.text = text;
+  x.n = n;
+  x.off = off;
+  x.sa = out_sa;
+  x.lcp = lcp0;
+  x.isa = isa;
+  x.gs = gs;
+  x.flag = flag;
+  x.h = h0;
+  bool ok = sa_launch(SaKernel::kIota, x, grid_for(n), st, hook) == cudaSuccess;
+  // round 0: the string sort by the first h0 characters
+  if (ok) {
+    ss_options o{};
+    o.max_len = h0;
+    s = sort_device(text, off, n, out_sa, lcp0, &o, st);
+    ok = s == SS_OK;
+  }
+  uint32_t M = 0;
+  if (ok) {
+    ok = sa_launch(SaKernel::kHeads0, x, grid_for(n), st, hook) == cudaSuccess &&
+         sa_scan_max(gs, n, tot, st, hook) == cudaSuccess &&
+         sa_launch(SaKernel::kName0, x, grid_for(n), st, hook) == cudaSuccess &&
+         sa_scan_sum(flag, n, tot, st, hook) == cudaSuccess && read_u32(flag + n - 1, &M);
+    SaArgs c = x;
+    c.vals = nullptr;
+    c.out = cpos[0];
+    if (ok && M) ok = sa_launch(SaKernel::kCompact, c, grid_for(n), st, hook) == cudaSuccess;
+  }
+  // doubling rounds over the unfinished groups (Observation 8.1)
+  uint64_t h = h0;
+  int cur = 0;
+  while (ok && s == SS_OK && M > 0) {
+    SaArgs r = x;
+    r.M = M;
+    r.h = (uint32_t)std::min<uint64_t>(h, 0xFFFFFFFFull);
+    r.cpos = cpos[cur];
+    r.member = member;
+    r.enc = enc;
+    r.eoff = eoff;
+    r.perm2 = perm2;
+    r.lcp2 = lcp2;
+    ok = sa_launch(SaKernel::kEncode, r, grid_for(M), st, hook) == cudaSuccess;
+    if (ok) {
+      s = sort_device(enc, eoff, M, perm2, lcp2, nullptr, st);
+      ok = s == SS_OK;
+    }
+    uint32_t M2 = 0;
+    if (ok)
+      ok = sa_launch(SaKernel::kApply, r, grid_for(M), st, hook) == cudaSuccess &&
+           sa_scan_max(gs, M, tot, st, hook) == cudaSuccess &&
+           sa_launch(SaKernel::kRename, r, grid_for(M), st, hook) == cudaSuccess &&
+           sa_scan_sum(flag, M, tot, st, hook) == cudaSuccess && read_u32(flag + M - 1, &M2);
+    if (ok && M2) {
+      SaArgs c = r;
+      c.n = M;
+      c.vals = cpos[cur];
+      c.out = cpos[cur ^ 1];
+      ok = sa_launch(SaKernel::kCompact, c, grid_for(M), st, hook) == cudaSuccess;
+    }
+    if (ok && M2 && h >= n) ok = false;  // cannot happen: every group is a singleton by depth n
+    M = M2;
+    cur ^= 1;
+    h *= 2;
+  }
+  if (ok && s == SS_OK && out_lcp) {
+    // LCPs of at least h0: list those positions, then one warp each
+    SaArgs l = x;
+    l.lcp_out = out_lcp;
+    uint32_t L = 0;
+    ok = sa_launch(SaKernel::kLongFlags, l, grid_for(n), st, hook) == cudaSuccess &&
+         sa_scan_sum(flag, n, tot, st, hook) == cudaSuccess && read_u32(flag + n - 1, &L);
+    if (ok && L) {
+      SaArgs c = x;
+      c.vals = nullptr;
+      c.out = cpos[0];
+      l.cpos = cpos[0];
+      l.M = L;
+      ok = sa_launch(SaKernel::kCompact, c, grid_for(n), st, hook) == cudaSuccess &&
+           sa_launch(SaKernel::kLcp, l, grid_for(32ull * L), st, hook) == cudaSuccess;
+    }
+  }
+  cudaFreeAsync(ws, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && ok) ok = false;
+  collect_profile();
+  if (s != SS_OK) return s;
+  return ok ? SS_OK : SS_ERR_CUDA;
+}
+
 size_t ss_workspace_size(uint64_t n, const ss_options* opt) {
   Opts o;
   if (resolve_opts(opt, o) != SS_OK || n >= 0xFFFFFFFFull) return 0;

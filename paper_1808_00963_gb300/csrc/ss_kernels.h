@@ -82,4 +82,34 @@ struct MergeParams {
 cudaError_t launch_merge(const MergeParams& m, uint32_t logk, uint32_t sms, cudaStream_t st,
                          const LaunchHook& hook);
 
+// Suffix array by prefix doubling (ss_sa.cu).
+enum class SaKernel { kIota, kHeads0, kName0, kCompact, kEncode, kApply, kRename, kLongFlags, kLcp };
+
+struct SaArgs {
+  const uint8_t* text = nullptr;
+  uint64_t n = 0;             // strings the kernel runs over (suffixes, or members M)
+  uint32_t h = 0;             // current depth (h0 for kHeads0 / kName0 / kLcp)
+  uint32_t M = 0;
+  uint64_t* off = nullptr;
+  uint32_t* sa = nullptr;
+  const uint32_t* lcp = nullptr;  // capped LCPs of the first sort
+  uint32_t* lcp_out = nullptr;    // final LCP array (holds the capped LCPs on entry)
+  uint32_t* isa = nullptr;
+  uint32_t* gs = nullptr;
+  uint32_t* flag = nullptr;       // flags, then their inclusive sum
+  const uint32_t* vals = nullptr;
+  uint32_t* out = nullptr;
+  const uint32_t* cpos = nullptr;
+  uint32_t* member = nullptr;
+  uint8_t* enc = nullptr;
+  uint64_t* eoff = nullptr;
+  const uint32_t* perm2 = nullptr;
+  const uint32_t* lcp2 = nullptr;
+};
+
+size_t sa_scan_totals(uint64_t n);  // entries of the scan's tile-total buffer
+cudaError_t sa_scan_max(uint32_t* a, uint64_t n, uint32_t* tot, cudaStream_t st, const LaunchHook& hook);
+cudaError_t sa_scan_sum(uint32_t* a, uint64_t n, uint32_t* tot, cudaStream_t st, const LaunchHook& hook);
+cudaError_t sa_launch(SaKernel k, const SaArgs& x, uint32_t grid, cudaStream_t st, const LaunchHook& hook);
+
 }  // namespace ss

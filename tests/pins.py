@@ -316,6 +316,23 @@ def pin_merge(lib):
             assert cmps == 0
 
 
+def pin_prefix_doubling_names(lib):
+    """Figure 8.1: the printed inverse h-suffix arrays ISA^1, ISA^2, ISA^4 of
+    tobeornottobe$ (smallest h-names), and the printed SA^8 as the suffix
+    array."""
+    g = golden("fig8_1.txt")
+    text = g["text"].encode()
+    chars = np.frombuffer(text + b"\0", np.uint8).copy()
+    offsets = np.array([int(x) for x in g["offsets"].split()], np.uint64)
+    for h in (1, 2, 4):
+        want = [int(x) for x in g[f"isa{h}"].split()]
+        assert oracle.h_names(chars, offsets, h, lib=lib).tolist() == want, h
+    sa, _ = oracle.sort(chars, offsets, 0, lib=lib)
+    assert sa.tolist() == [int(x) for x in g["perm"].split()]
+    sa2, _ = oracle.suffix_array(text, lib=lib)
+    assert sa2.tolist() == [int(x) for x in g["perm"].split()][1:]   # without the empty suffix
+
+
 ALL_PINS = [pin_paper_suffix_examples, pin_word_list_ties, pin_lemma_2_1, pin_brute_force,
             pin_library_sort, pin_checker, pin_cache, pin_bucket_and_tree, pin_distinguishing,
-            pin_lemma_4_1, pin_merge]
+            pin_lemma_4_1, pin_merge, pin_prefix_doubling_names]

@@ -128,3 +128,14 @@ def test_merge_workspace_size(lib):
     assert lib.ss_merge_workspace_size(runs, 3, 64) == ((c * 4 * 4 + 255) // 256 + (c * 4 + 255) // 256 + 1) * 256
     assert lib.ss_merge_workspace_size(runs, 3, 4096) == 256   # one piece: the counter only
     assert lib.ss_merge_workspace_size(runs, 0, 0) == 0
+
+
+def test_suffix_array_argument_checks(lib):
+    dummy = ctypes.c_void_p(4096)
+    assert lib.ss_suffix_array(None, 0, None, None, 0, None) == 0          # empty text
+    assert lib.ss_suffix_array(None, 10, dummy, None, 0, None) == 1        # NULL text
+    assert lib.ss_suffix_array(dummy, 10, None, None, 0, None) == 1        # NULL output
+    assert lib.ss_suffix_array(dummy, 1 << 32, dummy, None, 0, None) == 4  # too long
+    assert lib.ss_suffix_array(dummy, 10, dummy, None, (1 << 20) + 1, None) == 1
+    if not _has_gpu():
+        assert lib.ss_suffix_array(dummy, 10, dummy, None, 0, None) == 7
