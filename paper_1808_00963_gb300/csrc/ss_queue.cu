@@ -126,7 +126,10 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
   }
   __syncthreads();
 
-  // redistribution: stable and out of place, tile by tile
+  // redistribution: stable and out of place, tile by tile; a subset that fits
+  // one tile is spread over all warps (each warp owns 32 * R consecutive
+  // records of a tile)
+  R = min(R, (t.len + kBlock - 1) / kBlock);
   const uint32_t T = kBlock * R;
   for (uint32_t t0 = 0; t0 < t.len; t0 += T) {
     const uint32_t tl = min(T, t.len - t0);

@@ -36,23 +36,45 @@ struct Splitters {
 template <int LOGV>
 struct BuildScratch {
   uint64_t sample[Geo<LOGV>::S];
-  uint16_t ra[Geo<LOGV>::V + 1];
-  uint16_t rb[Geo<LOGV>::V + 1];
+  uint16_t lo[Geo<LOGV>::S];   // first sample position with a key >= sample[i]
+  uint16_t hi[Geo<LOGV>::S];   // first sample position with a key >  sample[i]
 };
 
-// Block-wide bitonic sort of N (power of two) uint64 in shared memory, ascending.
-template <uint32_t N>
-__device__ void block_bitonic_u64(uint64_t* a) {
+// Ascending bitonic sort of the 32 * E keys a warp holds, E per lane in
+// index order lane * E + e: partners closer than E sit in the same lane,
+// farther ones are exchanged with shuffles.
+template <int E>
+__device__ __forceinline__ void warp_bitonic_u64(uint64_t (&v)[E]) {
+  constexpr uint32_t N = 32 * E;
+  const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
   for (uint32_t k = 2; k <= N; k <<= 1) {
+#pragma unroll
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = threadIdx.x; i < N / 2; i += blockDim.x) {
-        uint32_t lo = 2 * i - (i & (j - 1));
-        uint32_t hi = lo + j;
-        bool up = (lo & k) == 0;
-        uint64_t A = a[lo], B = a[hi];
-        if ((A > B) == up) { a[lo] = B; a[hi] = A; }
+      if (j >= E) {
+        const uint32_t lj = j / E;
+        const bool lower = (lane & lj) == 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, v[e], lj);
+          const bool up = ((lane * E + e) & k) == 0;
+          const bool take_min = lower == up;
+          v[e] = take_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          if ((e & j) == 0) {
+            const int f = e | (int)j;
+            const bool up = ((lane * E + e) & k) == 0;
+            if ((v[e] > v[f]) == up) {
+              const uint64_t t = v[e];
+              v[e] = v[f];
+              v[f] = t;
+            }
+          }
+        }
       }
-      __syncthreads();
     }
   }
 }
@@ -62,53 +84,93 @@ __device__ void block_bitonic_u64(uint64_t* a) {
 // splitters with the recursive duplicate-skipping rule of Section 4.2.3
 // ("Sampling"): the middle sample of a range becomes the splitter, the ranges
 // left and right of the run of samples equal to it are split recursively.
-// Done level by level, the recursion directly yields the level-order tree t.
 // A node whose range is empty takes the sample just above its range (the
 // nearest splitter on the right among its ancestors), or all-ones past the
 // end, which keeps t a search tree.  Finally h'_i = lcp(x_{i-1}, x_i) with
-// h'_0 = h'_v = 0, the splitter LCPs of Algorithm 4.1.  Ends with __syncthreads().
+// h'_0 = h'_v = 0, the splitter LCPs of Algorithm 4.1.
+// The sample is sorted warp by warp in registers and merged by computing each
+// key's rank (its position in its chunk plus, in every other chunk, the keys
+// before it: <= for earlier chunks, < for later ones).  With the run of equal
+// keys around every sample position known, each tree node finds its range by
+// walking from the root along its level-order index, so the recursion needs
+// no step-by-step synchronisation.  Ends with __syncthreads().
 template <int LOGV>
 __device__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint64_t hseed,
                                 Splitters<LOGV>& sp, BuildScratch<LOGV>& bs) {
   using G = Geo<LOGV>;
-  for (uint32_t i = threadIdx.x; i < G::S; i += blockDim.x) {
-    uint64_t h = mix64(hseed + i);
-    uint32_t pos = (uint32_t)(((h >> 32) * (uint64_t)len) >> 32);
-    bs.sample[i] = recs[pos].key;
+  constexpr uint32_t C = G::S / kWarps;  // keys per warp
+  constexpr int E = (int)(C / 32);       // keys per lane
+  static_assert(E >= 1 && C % 32 == 0, "sample does not split into whole warps");
+  const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const uint32_t i = w * C + lane * E + e;
+    const uint64_t h = mix64(hseed + i);
+    const uint32_t pos = (uint32_t)(((h >> 32) * (uint64_t)len) >> 32);
+    v[e] = recs[pos].key;
   }
-  if (threadIdx.x == 0) { bs.ra[1] = 0; bs.rb[1] = (uint16_t)G::S; }
+  warp_bitonic_u64<E>(v);
+  uint64_t* s = bs.sample;
+#pragma unroll
+  for (int e = 0; e < E; ++e) s[w * C + lane * E + e] = v[e];
   __syncthreads();
-  block_bitonic_u64<G::S>(bs.sample);
-  const uint64_t* s = bs.sample;
-  for (int l = 0; l < LOGV; ++l) {
-    const uint32_t first = 1u << l;
-    for (uint32_t q = threadIdx.x; q < first; q += blockDim.x) {
-      const uint32_t i = first + q;
-      const uint32_t a = bs.ra[i], b = bs.rb[i];
-      uint64_t val;
-      uint32_t la, lb, ra2, rb2;
+  uint32_t rank[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    uint32_t r = lane * E + e;
+#pragma unroll
+    for (uint32_t ww = 0; ww < kWarps; ++ww) {
+      if (ww == w) continue;
+      const uint64_t* ch = s + ww * C;
+      uint32_t a = 0, b = C;
+      if (ww < w) {
+        while (a < b) { const uint32_t m = (a + b) >> 1; if (ch[m] <= v[e]) a = m + 1; else b = m; }
+      } else {
+        while (a < b) { const uint32_t m = (a + b) >> 1; if (ch[m] < v[e]) a = m + 1; else b = m; }
+      }
+      r += a;
+    }
+    rank[e] = r;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < E; ++e) s[rank[e]] = v[e];
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < G::S; i += blockDim.x) {
+    const uint64_t val = s[i];
+    uint32_t a = 0, b = i;
+    while (a < b) { const uint32_t m = (a + b) >> 1; if (s[m] < val) a = m + 1; else b = m; }
+    bs.lo[i] = (uint16_t)a;
+    a = i + 1;
+    b = G::S;
+    while (a < b) { const uint32_t m = (a + b) >> 1; if (s[m] <= val) a = m + 1; else b = m; }
+    bs.hi[i] = (uint16_t)a;
+  }
+  __syncthreads();
+  for (uint32_t q = threadIdx.x; q < G::V; q += blockDim.x) {
+    const uint32_t i = q + 1;               // level-order index
+    const int l = 31 - __clz(i);            // its level
+    uint32_t a = 0, b = G::S;               // its range of the sorted sample
+    for (int d = l - 1; d >= 0; --d) {
       if (a < b) {
         const uint32_t m = (a + b) >> 1;
-        val = s[m];
-        uint32_t lo = a, hi = m;       // first index in [a, m] with s >= val
-        while (lo < hi) { uint32_t md = (lo + hi) >> 1; if (s[md] < val) lo = md + 1; else hi = md; }
-        const uint32_t left_end = lo;
-        lo = m + 1; hi = b;            // first index in [m+1, b) with s > val, else b
-        while (lo < hi) { uint32_t md = (lo + hi) >> 1; if (s[md] <= val) lo = md + 1; else hi = md; }
-        la = a; lb = left_end; ra2 = lo; rb2 = b;
+        if (((i >> d) & 1u) == 0) {
+          const uint32_t le = bs.lo[m];
+          b = le > a ? le : a;              // left of the run of keys equal to s[m]
+        } else {
+          const uint32_t rs = bs.hi[m];
+          a = rs < b ? rs : b;              // right of that run
+        }
       } else {
-        val = (b < G::S) ? s[b] : ~0ull;
-        la = lb = ra2 = rb2 = b;
-      }
-      sp.tree[i] = val;
-      sp.x[(2 * q + 1) * (1u << (LOGV - 1 - l)) - 1] = val;
-      if (l + 1 < LOGV) {
-        bs.ra[2 * i] = (uint16_t)la; bs.rb[2 * i] = (uint16_t)lb;
-        bs.ra[2 * i + 1] = (uint16_t)ra2; bs.rb[2 * i + 1] = (uint16_t)rb2;
+        a = b;
       }
     }
-    __syncthreads();
+    const uint64_t val = a < b ? s[(a + b) >> 1] : (b < G::S ? s[b] : ~0ull);
+    sp.tree[i] = val;
+    sp.x[(2 * (i - (1u << l)) + 1) * (1u << (LOGV - 1 - l)) - 1] = val;
   }
+  __syncthreads();
   for (uint32_t r = threadIdx.x; r <= G::V; r += blockDim.x)
     sp.hp[r] = (r == 0 || r == G::V) ? 0 : (uint8_t)lcp8(sp.x[r - 1], sp.x[r]);
   if (threadIdx.x == 0) sp.tree[0] = 0;
