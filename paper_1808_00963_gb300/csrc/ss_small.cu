@@ -271,9 +271,10 @@ __device__ __forceinline__ bool elem_less(uint64_t ka, uint32_t ta, uint64_t kb,
 // outputs of one merged pair of runs: it finds where its outputs start with a
 // binary search along the merge path and merges sequentially.  Uses
 // (key2, tag2) as the second buffer; the result ends in (m.key, m.tag).
+template <uint32_t NT>
 __device__ void block_sort(CtaSmem& m, uint32_t n) {
   uint32_t ipt = 1;
-  while (ipt * kBlock < n) ipt <<= 1;
+  while (ipt * NT < n) ipt <<= 1;
   {
     const uint32_t a = threadIdx.x * ipt;
     const uint32_t e = min(n, a + ipt);
@@ -332,7 +333,7 @@ __device__ void block_sort(CtaSmem& m, uint32_t n) {
     uint32_t* tt = st; st = dt; dt = tt;
   }
   if (sk != m.key) {
-    for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+    for (uint32_t j = threadIdx.x; j < n; j += NT) {
       m.key[j] = sk[j];
       m.tag[j] = st[j];
     }
@@ -341,9 +342,11 @@ __device__ void block_sort(CtaSmem& m, uint32_t n) {
 }
 
 // Inclusive max-scan of a[0..n) in place.
+template <uint32_t NT>
 __device__ void block_max_scan(uint16_t* a, uint32_t n) {
-  __shared__ uint32_t wmax[kWarps];
-  const uint32_t per = (n + kBlock - 1) / kBlock;
+  constexpr uint32_t NW = NT / 32;
+  __shared__ uint32_t wmax[NW];
+  const uint32_t per = (n + NT - 1) / NT;
   const uint32_t b0 = threadIdx.x * per;
   uint32_t m = 0;
   for (uint32_t j = 0; j < per && b0 + j < n; ++j) m = max(m, (uint32_t)a[b0 + j]);
@@ -357,13 +360,13 @@ __device__ void block_max_scan(uint16_t* a, uint32_t n) {
   if (lane_id() == 31) wmax[w] = inc;
   __syncthreads();
   if (w == 0) {
-    uint32_t v = lane_id() < kWarps ? wmax[lane_id()] : 0;
+    uint32_t v = lane_id() < NW ? wmax[lane_id()] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t t = __shfl_up_sync(kFull, v, o);
       if (lane_id() >= (uint32_t)o) v = max(v, t);
     }
-    if (lane_id() < kWarps) wmax[lane_id()] = v;
+    if (lane_id() < NW) wmax[lane_id()] = v;
   }
   __syncthreads();
   uint32_t excl = __shfl_up_sync(kFull, inc, 1);
@@ -376,7 +379,12 @@ __device__ void block_max_scan(uint16_t* a, uint32_t n) {
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) {
+// Subsets with lo < len <= hi; while there are fewer than min_count subsets
+// in all, the narrow kernel (narrow = 1) leaves every subset to the wide one
+// (narrow = 0), which then takes all sizes.
+template <uint32_t NT>
+__global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint32_t lo, uint32_t hi,
+                                                  uint32_t min_count, uint32_t narrow) {
   extern __shared__ __align__(16) uint8_t smem[];
   CtaSmem m;
   m.key = reinterpret_cast<uint64_t*>(smem);
@@ -391,13 +399,18 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
   __shared__ uint64_t s_lead[kLookWindows];
   unsigned long long bytes = 0;
   const uint32_t count = min(*c.small_cta.count, c.small_cta.cap);
+  if (count < min_count) {
+    if (narrow) return;
+    lo = 0;
+  }
   for (uint32_t ti = blockIdx.x; ti < count; ti += gridDim.x) {
     const Task t = c.small_cta.items[ti];
+    if (t.len <= lo || t.len > hi) continue;  // another block size takes this subset
     const SetDesc sd = c.sets[task_set(t)];
     const uint32_t par = task_par(t);
     const uint32_t n = t.len;
     const uint32_t wide = c.wide[task_set(t)];
-    for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+    for (uint32_t j = threadIdx.x; j < n; j += NT) {
       const Rec r = load_rec(c.rec[par] + t.begin + j);
       m.key[j] = r.key;
       m.idx[j] = r.idx;
@@ -416,7 +429,7 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
       if (threadIdx.x == 0) s_neq = 0;
       __syncthreads();
       const uint64_t k0 = m.key[0];
-      for (uint32_t j = threadIdx.x; j < n; j += kBlock)
+      for (uint32_t j = threadIdx.x; j < n; j += NT)
         if (m.key[j] != k0) s_neq = 1;
       __syncthreads();
       if (s_neq || has_nul(k0) || depth + 8 * kLookWindows > kMaxDepth) break;
@@ -431,7 +444,7 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
         s_jstop = js;
       }
       __syncthreads();
-      for (uint32_t j = threadIdx.x + 1; j < n; j += kBlock) {
+      for (uint32_t j = threadIdx.x + 1; j < n; j += NT) {
         uint64_t w[kLookWindows];
         const uint32_t nwin = load_windows<kLookWindows>(sd.chars, m.off[j], depth + 8, sd.cap, w);
         uint32_t js = kLookWindows;
@@ -442,7 +455,7 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
       }
       __syncthreads();
       const uint32_t nd = depth + 8 * (s_jstop + 1);
-      for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+      for (uint32_t j = threadIdx.x; j < n; j += NT) {
         m.key[j] = load_cache(sd.chars, m.off[j], nd, sd.cap);
         bytes += 8ull * (s_jstop + 1);
       }
@@ -451,9 +464,9 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
     }
 
     while (true) {
-      block_sort(m, n);
+      block_sort<NT>(m, n);
       if (threadIdx.x == 0) s_max_open = 0;
-      for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+      for (uint32_t j = threadIdx.x; j < n; j += NT) {
         const uint32_t tg = m.tag[j];
         const bool st = j == 0 || tag_seg(tg) != tag_seg(m.tag[j - 1]) || m.key[j] != m.key[j - 1];
         if (lcp && (tg & 1u) && j > 0 && tag_seg(tg) == tag_seg(m.tag[j - 1]) && m.key[j] != m.key[j - 1])
@@ -462,13 +475,13 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
         m.aux[j] = 0;
       }
       __syncthreads();
-      block_max_scan(m.nseg, n);
-      for (uint32_t j = threadIdx.x; j < n; j += kBlock) atomicAdd(&m.aux[m.nseg[j]], 1u);
+      block_max_scan<NT>(m.nseg, n);
+      for (uint32_t j = threadIdx.x; j < n; j += NT) atomicAdd(&m.aux[m.nseg[j]], 1u);
       __syncthreads();
       // Runs of one string or of equal strings are finished; runs of at most
       // 32 strings go back to the record buffer as new warp tasks (a warp
       // finishes them without holding this block); larger runs continue here.
-      for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+      for (uint32_t j = threadIdx.x; j < n; j += NT) {
         const uint32_t s0 = m.nseg[j];
         uint32_t tg = m.tag[j];
         uint32_t open = tg & 1u, handed = tg & kHanded;
@@ -498,14 +511,14 @@ __global__ void __launch_bounds__(kBlock) k_small_cta(SortCtx c, uint32_t pmax) 
         break;
       }
       depth += 8;
-      for (uint32_t j = threadIdx.x; j < n; j += kBlock)
+      for (uint32_t j = threadIdx.x; j < n; j += NT)
         if (m.tag[j] & 1u) {
           m.key[j] = load_cache(sd.chars, m.off[tag_pos(m.tag[j])], depth, sd.cap);
           bytes += 8;
         }
       __syncthreads();
     }
-    for (uint32_t j = threadIdx.x; j < n; j += kBlock) {
+    for (uint32_t j = threadIdx.x; j < n; j += NT) {
       const uint32_t tg = m.tag[j];
       if (!(tg & kHanded)) sd.perm[t.begin - sd.base + j] = m.idx[tag_pos(tg)];
       bytes += sd.lcp ? 24 : 20;  // record 16 read; perm 4 (+ lcp 4) written
@@ -569,6 +582,8 @@ __global__ void __launch_bounds__(kBlock) k_distinguishing(const uint8_t* __rest
 
 }  // namespace
 
+constexpr uint32_t kSmallCtaNarrowMax = 256;
+
 size_t small_cta_smem(uint32_t pmax) { return (size_t)pmax * (8 + 8 + 8 + 4 + 4 + 4 + 4 + 2); }
 
 cudaError_t launch_init(const SortCtx& c, cudaStream_t st, const LaunchHook& hook) {
@@ -582,12 +597,30 @@ cudaError_t launch_small(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, ui
                          cudaStream_t st, const LaunchHook& hook) {
   static uint32_t attr_pmax = 0;
   if (pmax > attr_pmax) {
-    cudaError_t e = cudaFuncSetAttribute(k_small_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_small_cta<kBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)small_cta_smem(pmax));
     if (e != cudaSuccess) return e;
     attr_pmax = pmax;
   }
-  hook.run("small_cta", [&] { k_small_cta<<<grid_cta, kBlock, small_cta_smem(pmax), st>>>(c, pmax); });
+  // subsets of up to kSmallCtaNarrowMax strings: 64-thread blocks with small
+  // shared arrays, many per SM (a subset's sort is latency-bound, so more of
+  // them in flight beats more threads on each); larger ones: 256 threads
+  // (when there are enough subsets to fill the GPU with them)
+  const uint32_t min_count = 2 * grid_cta;
+  if (pmax <= kSmallCtaNarrowMax) {
+    hook.run("small_cta", [&] {
+      k_small_cta<64><<<grid_cta * 4, 64, small_cta_smem(pmax), st>>>(c, pmax, 0u, pmax, 0u, 1u);
+    });
+  } else {
+    hook.run("small_cta", [&] {
+      k_small_cta<64><<<grid_cta * 4, 64, small_cta_smem(kSmallCtaNarrowMax), st>>>(
+          c, kSmallCtaNarrowMax, 0u, kSmallCtaNarrowMax, min_count, 1u);
+    });
+    hook.run("small_cta", [&] {
+      k_small_cta<kBlock><<<grid_cta, kBlock, small_cta_smem(pmax), st>>>(c, pmax, kSmallCtaNarrowMax, 0xFFFFFFFFu,
+                                                                         min_count, 0u);
+    });
+  }
   hook.run("small_warp", [&] { k_small_warp<<<grid_warp, kBlock, 0, st>>>(c); });
   return cudaGetLastError();
 }
