@@ -105,7 +105,15 @@ __device__ uint32_t warp_refine(bool active, uint32_t g0, uint32_t nact, uint64_
   if (!active) { key = ~0ull; idx = 0xFFFFFFFFu; off = 0; depth = 0; }
   const uint32_t upto = (lane == 31) ? kFull : ((2u << lane) - 1);
   while (true) {
-    warp_sort(seg, key, idx, off, depth, open);
+    // sort only if some run is out of (cache, index) order: after a look-ahead
+    // jump over characters all members share, the runs often still are
+    {
+      const uint32_t ps0 = __shfl_up_sync(kFull, seg, 1);
+      const uint64_t pk0 = __shfl_up_sync(kFull, key, 1);
+      const uint32_t pi0 = __shfl_up_sync(kFull, idx, 1);
+      const bool disorder = active && lane > 0 && seg == ps0 && (key < pk0 || (key == pk0 && idx < pi0));
+      if (__any_sync(kFull, disorder)) warp_sort(seg, key, idx, off, depth, open);
+    }
     const uint32_t ps = __shfl_up_sync(kFull, seg, 1);
     const uint64_t pk = __shfl_up_sync(kFull, key, 1);
     const bool start = lane == 0 || seg != ps || key != pk;
