@@ -43,8 +43,24 @@ static const char* const kClassNames[kKClasses] = {"init",      "big_sample", "b
 struct PendingEvent {
   const char* name;
   cudaEvent_t a, b;
+  int dev;
 };
 static thread_local std::vector<PendingEvent> t_pending;
+// Events are reused (creating two per launch costs more host time than the
+// launch itself); an event belongs to the device it was created on.
+static thread_local std::map<int, std::vector<cudaEvent_t>> t_event_pool;
+
+static cudaEvent_t pooled_event(int dev) {
+  auto& pool = t_event_pool[dev];
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
 
 void LaunchHook::run(const char* name, const std::function<void()>& launch) const {
   g_launches.fetch_add(1, std::memory_order_relaxed);
@@ -54,9 +70,9 @@ void LaunchHook::run(const char* name, const std::function<void()>& launch) cons
     launch();
     return;
   }
-  PendingEvent p{name, nullptr, nullptr};
-  cudaEventCreate(&p.a);
-  cudaEventCreate(&p.b);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  PendingEvent p{name, pooled_event(dev), pooled_event(dev), dev};
   cudaEventRecord(p.a, stream);
   launch();
   cudaEventRecord(p.b, stream);
@@ -74,8 +90,8 @@ static void collect_profile() {
       e.first += 1;
       e.second += ms;
     }
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
+    t_event_pool[p.dev].push_back(p.a);
+    t_event_pool[p.dev].push_back(p.b);
   }
   t_pending.clear();
 }
