@@ -81,7 +81,10 @@ typedef struct ss_options {
                                   against the sorted splitters (default);
                                   1 = S5-UIC, the same test done in the tree
                                   through Lemma 4.1's index map; 2 = S5-E, an
-                                  equality test at every node.                 */
+                                  equality test at every node; 3 = S5-UI
+                                  entered through a jump table over the key's
+                                  top 12 bits (Section 4.4; multi-block steps,
+                                  the others as 0).                             */
     uint32_t flags;            /* reserved, must be 0                           */
     void* workspace;           /* optional caller-owned device workspace of at
                                   least ss_workspace_size() bytes, 256-byte

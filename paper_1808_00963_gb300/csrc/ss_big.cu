@@ -26,36 +26,57 @@ __device__ __forceinline__ uint64_t cnt_base(const GenTask& g) {
   return ((uint64_t)g.cnt_base_hi << 32) | g.cnt_base_lo;
 }
 
+// Splitters of one multi-block task, with the jump table of its tree (filled
+// for the jump-table classifier only).
+template <int LOGV>
+struct BigSplitters {
+  Splitters<LOGV> sp;
+  uint16_t jump[kJumpSize];
+};
+
 template <int LOGV>
 __global__ void __launch_bounds__(kBlock) k_big_sample(SortCtx c, const GenTask* __restrict__ gt,
-                                                       Splitters<LOGV>* __restrict__ out) {
+                                                       BigSplitters<LOGV>* __restrict__ out) {
   __shared__ __align__(16) Splitters<LOGV> sp;
   __shared__ __align__(16) BuildScratch<LOGV> bs;
   const GenTask g = gt[blockIdx.x];
   const Rec* recs = c.rec[task_par(g.t)] + g.t.begin;
   build_splitters<LOGV>(recs, g.t.len, mix64(c.seed ^ ((uint64_t)g.t.begin << 20) ^ g.t.depth), sp, bs);
   const uint64_t* src = reinterpret_cast<const uint64_t*>(&sp);
-  uint64_t* dst = reinterpret_cast<uint64_t*>(out + blockIdx.x);
+  uint64_t* dst = reinterpret_cast<uint64_t*>(&out[blockIdx.x].sp);
   for (uint32_t i = threadIdx.x; i < sizeof(Splitters<LOGV>) / 8; i += blockDim.x) dst[i] = src[i];
-  // sample reads + splitter writes
-  account(c, kKBigSample, threadIdx.x == 0 ? Geo<LOGV>::S * 8ull + sizeof(Splitters<LOGV>) : 0ull);
+  unsigned long long bytes = threadIdx.x == 0 ? Geo<LOGV>::S * 8ull + sizeof(Splitters<LOGV>) : 0ull;
+  if (c.classifier == kClassifyUIJ) {
+    for (uint32_t p = threadIdx.x; p < kJumpSize; p += blockDim.x)
+      out[blockIdx.x].jump[p] = (uint16_t)jump_entry<LOGV>(p, sp.tree);
+    if (threadIdx.x == 0) bytes += 2ull * kJumpSize;
+  }
+  // sample reads + splitter (and jump table) writes
+  account(c, kKBigSample, bytes);
 }
 
 template <int LOGV>
 __global__ void __launch_bounds__(kBlock) k_big_classify(SortCtx c, const GenTask* __restrict__ gt,
-                                                         uint32_t G, const Splitters<LOGV>* __restrict__ spl,
+                                                         uint32_t G, const BigSplitters<LOGV>* __restrict__ spl,
                                                          uint32_t* __restrict__ counters, uint32_t R) {
   using Gm = Geo<LOGV>;
   __shared__ __align__(16) uint64_t tree[Gm::V + 1];
   __shared__ __align__(16) uint64_t x[Gm::V + 1];
   __shared__ uint32_t hist[Gm::KP];
+  __shared__ __align__(16) uint16_t jump[kJumpSize];
   __shared__ uint32_t s_g;
   if (threadIdx.x == 0) s_g = find_gen_task(gt, G, blockIdx.x);
   for (uint32_t b = threadIdx.x; b < Gm::KP; b += blockDim.x) hist[b] = 0;
   __syncthreads();
   const GenTask g = gt[s_g];
-  const Splitters<LOGV>& sp = spl[s_g];
+  const Splitters<LOGV>& sp = spl[s_g].sp;
   for (uint32_t i = threadIdx.x; i <= Gm::V; i += blockDim.x) { tree[i] = sp.tree[i]; x[i] = sp.x[i]; }
+  const bool use_jump = c.classifier == kClassifyUIJ;
+  if (use_jump) {
+    const uint4* js = reinterpret_cast<const uint4*>(spl[s_g].jump);
+    uint4* jd = reinterpret_cast<uint4*>(jump);
+    for (uint32_t i = threadIdx.x; i < kJumpSize * 2 / 16; i += blockDim.x) jd[i] = js[i];
+  }
   __syncthreads();
   const uint32_t tile = blockIdx.x - g.tile_start;
   const uint32_t T = kBlock * R;
@@ -63,7 +84,7 @@ __global__ void __launch_bounds__(kBlock) k_big_classify(SortCtx c, const GenTas
   const uint32_t tl = min(T, g.t.len - t0);
   const Rec* recs = c.rec[task_par(g.t)] + g.t.begin + t0;
   uint16_t* bo = c.bucket_of + g.t.begin + t0;
-  const uint32_t mine = classify_count<LOGV>(recs, bo, tl, tree, x, hist, c.classifier);
+  const uint32_t mine = classify_count<LOGV>(recs, bo, tl, tree, x, hist, c.classifier, use_jump ? jump : nullptr);
   __syncthreads();
   uint32_t* cnt = counters + cnt_base(g) + tile;
   for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) cnt[(uint64_t)b * g.tiles] = hist[b];
@@ -75,13 +96,13 @@ __global__ void __launch_bounds__(kBlock) k_big_classify(SortCtx c, const GenTas
 
 template <int LOGV>
 __global__ void __launch_bounds__(kBlock) k_big_emit(SortCtx c, const GenTask* __restrict__ gt,
-                                                     const Splitters<LOGV>* __restrict__ spl,
+                                                     const BigSplitters<LOGV>* __restrict__ spl,
                                                      const uint32_t* __restrict__ scanned,
                                                      uint32_t* __restrict__ gstart, uint32_t* __restrict__ gdesc,
                                                      uint32_t next_big) {
   using Gm = Geo<LOGV>;
   const GenTask g = gt[blockIdx.x];
-  const Splitters<LOGV>& sp = spl[blockIdx.x];
+  const Splitters<LOGV>& sp = spl[blockIdx.x].sp;
   const SetDesc sd = c.sets[task_set(g.t)];
   const uint32_t* sc = scanned + cnt_base(g);
   unsigned long long bytes = 0;
@@ -232,9 +253,9 @@ __global__ void __launch_bounds__(kBlock) k_scan_down(uint32_t* __restrict__ a, 
 
 size_t big_splitters_bytes(int logv) {
   switch (logv) {
-    case 8: return sizeof(Splitters<8>);
-    case 9: return sizeof(Splitters<9>);
-    default: return sizeof(Splitters<10>);
+    case 8: return sizeof(BigSplitters<8>);
+    case 9: return sizeof(BigSplitters<9>);
+    default: return sizeof(BigSplitters<10>);
   }
 }
 
@@ -253,7 +274,7 @@ static cudaError_t launch_big_step_t(const BigStepArgs& a, cudaStream_t st, cons
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  auto* spl = reinterpret_cast<Splitters<LOGV>*>(a.splitters);
+  auto* spl = reinterpret_cast<BigSplitters<LOGV>*>(a.splitters);
   hook.run("big_sample", [&] { k_big_sample<LOGV><<<a.G, kBlock, 0, st>>>(a.c, a.gt, spl); });
   hook.run("big_classify", [&] {
     k_big_classify<LOGV><<<a.tiles, kBlock, 0, st>>>(a.c, a.gt, a.G, spl, a.counters, a.R);

@@ -177,7 +177,7 @@ static ss_status resolve_opts(const ss_options* o, Opts& r) {
   if (o->big_threshold) r.big_thr = o->big_threshold;
   if (r.big_thr < r.cutoff) return SS_ERR_INVALID;
   if (o->seed) r.seed = o->seed;
-  if (o->classifier > 2) return SS_ERR_INVALID;
+  if (o->classifier > 3) return SS_ERR_INVALID;
   r.classifier = o->classifier;
   if (o->workspace && ((uintptr_t)o->workspace & 255)) return SS_ERR_INVALID;
   return SS_OK;

@@ -198,6 +198,40 @@ __device__ __forceinline__ uint32_t pre_to_level(uint32_t p, uint32_t w) {
 constexpr uint32_t kClassifyUI = 0;   // unrolled <=-descent, equality test on the sorted copy x
 constexpr uint32_t kClassifyUIC = 1;  // same descent, equality test in t via Lemma 4.1 (no copy needed)
 constexpr uint32_t kClassifyE = 2;    // equality test at every node of the descent
+constexpr uint32_t kClassifyUIJ = 3;  // UI entered through a jump table over the key's top bits
+
+// Jump tables (Section 4.4, "Jump tables"): for every value p of a key's top
+// kJumpBits bits, the first node of the descent whose splitter does not
+// decide by those bits alone (its top bits equal p), or the leaf reached
+// (>= 2^LOGV) when every splitter on the way decides.  Keys with top bits p
+// take the same path down to that node, so the descent can start there.
+constexpr int kJumpBits = 12;
+constexpr uint32_t kJumpSize = 1u << kJumpBits;
+
+template <int LOGV>
+__device__ __forceinline__ uint32_t jump_entry(uint32_t p, const uint64_t* tree) {
+  uint32_t i = 1;
+  while (i < (1u << LOGV)) {
+    const uint32_t tp = (uint32_t)(tree[i] >> (64 - kJumpBits));
+    if (p == tp) break;
+    i = 2 * i + (p > tp ? 1u : 0u);
+  }
+  return i;
+}
+
+// The UI classification entered at the jump table's node: the remaining
+// levels are predicated off for keys already at a leaf.
+template <int LOGV>
+__device__ __forceinline__ uint32_t classify_jump(uint64_t c, const uint64_t* tree, const uint64_t* x,
+                                                  const uint16_t* jump) {
+  uint32_t i = jump[c >> (64 - kJumpBits)];
+#pragma unroll
+  for (int l = 0; l < LOGV; ++l)
+    if (i < (1u << LOGV)) i = 2 * i + (c > tree[i] ? 1u : 0u);
+  const uint32_t r = i - (1u << LOGV);
+  const bool eq = r < Geo<LOGV>::V && x[r] == c;
+  return 2 * r + (eq ? 1u : 0u);
+}
 
 // The classification of one key in Algorithm 4.1: branch-free descent of the level-order tree,
 // i := 2i + [c > t_i] (the reading of its descent step under which bucket b_{2r} holds
@@ -232,7 +266,8 @@ __device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, c
 template <int LOGV>
 __device__ __forceinline__ uint32_t classify_count(const Rec* __restrict__ recs, uint16_t* __restrict__ bo,
                                                    uint32_t n, const uint64_t* tree, const uint64_t* x,
-                                                   uint32_t* hist, uint32_t variant) {
+                                                   uint32_t* hist, uint32_t variant,
+                                                   const uint16_t* jump = nullptr) {
   constexpr int U = 8;
   uint32_t mine = 0;
   const uint32_t lim = (n + kBlock - 1) / kBlock * kBlock;
@@ -250,7 +285,8 @@ __device__ __forceinline__ uint32_t classify_count(const Rec* __restrict__ recs,
       const bool valid = p < n;
       uint32_t b = 0xFFFFu;
       if (valid) {
-        b = classify<LOGV>(k[u], tree, x, variant);
+        b = (variant == kClassifyUIJ && jump) ? classify_jump<LOGV>(k[u], tree, x, jump)
+                                              : classify<LOGV>(k[u], tree, x, variant);
         bo[p] = (uint16_t)b;
         ++mine;
       }

@@ -35,12 +35,13 @@ def test_distinguishing_matches_oracle(case):
     assert int(D.item()) == oracle.dl(l)[0]
 
 
-@pytest.mark.parametrize("classifier", [0, 1, 2])
+@pytest.mark.parametrize("classifier", [0, 1, 2, 3])
 @pytest.mark.parametrize("case", ["binary", "dna", "url", "equal_heavy"])
 def test_classifier_variants_same_output(classifier, case):
-    """S5-UI, S5-UIC (Lemma 4.1 index map) and S5-E (equality at every node)
-    give the oracle's output, on inputs whose samples hold many equal caches
-    (duplicate splitters), through both the multi-block and single-block steps."""
+    """S5-UI, S5-UIC (Lemma 4.1 index map), S5-E (equality at every node) and
+    S5-UI entered through a jump table give the oracle's output, on inputs
+    whose samples hold many equal caches (duplicate splitters), through both
+    the multi-block and single-block steps."""
     from gpu_util import assert_parity, gpu_sort
     s = {"binary": lambda: gen.random_set(80000, 61, 0, 24, ord("0"), ord("1")),
          "dna": lambda: gen.dna_suffix_set(120000, 62, nblocks=20, blocklen=500),
