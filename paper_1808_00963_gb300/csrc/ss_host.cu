@@ -523,15 +523,10 @@ ss_status ss_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint6
 
 // ---- K-way LCP merge ------------------------------------------------------------------
 
-static uint32_t merge_step(uint64_t total, uint32_t sample_step) {
-  if (sample_step) return sample_step;
-  uint32_t s = 64;  // about 2^17 pieces for large inputs, pieces of 64..2048 strings
-  while (s < 2048 && (uint64_t)s * 2 * 131072 <= total) s *= 2;
-  return s;
-}
+static uint32_t merge_step(uint32_t sample_step) { return sample_step ? sample_step : 128; }
 
 static ss_status merge_geometry(const ss_run* runs, uint32_t num_runs, uint32_t sample_step, uint64_t* total,
-                                uint32_t* S, uint64_t* C) {
+                                uint32_t* S) {
   if (num_runs == 0 || num_runs > SS_MERGE_MAX_RUNS || !runs) return SS_ERR_INVALID;
   if (sample_step != 0 && (sample_step < 16 || sample_step > 65536)) return SS_ERR_INVALID;
   uint64_t t = 0;
@@ -542,74 +537,102 @@ static ss_status merge_geometry(const ss_run* runs, uint32_t num_runs, uint32_t 
   }
   if (t >= 0xFFFFFFFFull) return SS_ERR_TOO_LARGE;
   *total = t;
-  *S = merge_step(t, sample_step);
-  uint64_t c = 0;
-  for (uint32_t k = 0; k < num_runs; ++k) c += runs[k].n / *S;
-  *C = c;
+  *S = merge_step(sample_step);
   return SS_OK;
 }
 
-// cut vectors, sample ranks, piece counter
-static size_t merge_ws_bytes(uint64_t C, uint32_t kp) { return align256(C * kp * 4) + align256(C * 4) + 256; }
-
-static uint32_t pow2_at_least(uint32_t k, uint32_t* logk) {
-  uint32_t kp = 1, l = 0;
-  while (kp < k) { kp <<= 1; ++l; }
-  *logk = l;
-  return kp;
+// two record buffers (32 bytes per string), the sample cuts of a round, the
+// piece counter
+static size_t merge_ws_bytes(uint64_t total, uint32_t num_runs, uint32_t S) {
+  if (num_runs <= 1) return 256;
+  return 2 * align256(total * sizeof(MergeRec)) + align256((total / S + num_runs + 1) * 4) + 256;
 }
 
 size_t ss_merge_workspace_size(const ss_run* runs, uint32_t num_runs, uint32_t sample_step) {
-  uint64_t total, C;
-  uint32_t S, logk;
-  if (merge_geometry(runs, num_runs, sample_step, &total, &S, &C) != SS_OK) return 0;
-  return merge_ws_bytes(C, pow2_at_least(num_runs, &logk));
+  uint64_t total;
+  uint32_t S;
+  if (merge_geometry(runs, num_runs, sample_step, &total, &S) != SS_OK) return 0;
+  return merge_ws_bytes(total, num_runs, S);
 }
 
 ss_status ss_merge(const uint8_t* chars, const uint64_t* offsets, uint32_t max_len, const ss_run* runs,
                    uint32_t num_runs, uint32_t sample_step, uint32_t* out_perm, uint32_t* out_lcp,
                    void* workspace, size_t workspace_bytes, void* stream) {
-  uint64_t total, C;
-  uint32_t S, logk;
-  ss_status s = merge_geometry(runs, num_runs, sample_step, &total, &S, &C);
+  uint64_t total;
+  uint32_t S;
+  ss_status s = merge_geometry(runs, num_runs, sample_step, &total, &S);
   if (s != SS_OK) return s;
   if (total == 0) return SS_OK;
   if (!chars || !offsets || !out_perm) return SS_ERR_INVALID;
   if (workspace && (reinterpret_cast<uintptr_t>(workspace) & 255)) return SS_ERR_INVALID;
-  const uint32_t kp = pow2_at_least(num_runs, &logk);
-  const size_t need = merge_ws_bytes(C, kp);
+  const size_t need = merge_ws_bytes(total, num_runs, S);
   if (workspace && workspace_bytes < need) return SS_ERR_INVALID;
   DevInfo dev;
   s = device_info(dev);
   if (s != SS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const LaunchHook hook{st};
+  const uint32_t sms = (uint32_t)dev.sms;
+  const uint32_t K = num_runs;
+  std::vector<uint32_t> start(K + 1, 0);
+  for (uint32_t k = 0; k < K; ++k) start[k + 1] = start[k] + runs[k].n;
+  if (K == 1) {
+    return launch_merge_copy(runs[0].perm, runs[0].lcp, (uint32_t)total, out_perm, out_lcp, sms, st, hook) ==
+                   cudaSuccess
+               ? SS_OK
+               : SS_ERR_CUDA;
+  }
   uint8_t* ws = static_cast<uint8_t*>(workspace);
   const bool own = !ws;
   if (own && cudaMallocAsync(reinterpret_cast<void**>(&ws), need, st) != cudaSuccess) return SS_ERR_OOM;
-  MergeParams m{};
-  m.chars = chars;
-  m.offsets = offsets;
-  m.cut = reinterpret_cast<uint32_t*>(ws);
-  m.rank = reinterpret_cast<uint32_t*>(ws + align256(C * kp * 4));
-  m.next_piece = reinterpret_cast<uint32_t*>(ws + align256(C * kp * 4) + align256(C * 4));
-  m.out_perm = out_perm;
-  m.out_lcp = out_lcp;
-  m.cap = max_len ? std::min<uint32_t>(max_len, 1u << 30) : (1u << 30);
-  m.K = kp;
-  m.S = S;
-  m.C = (uint32_t)C;
-  uint32_t base = 0;
-  for (uint32_t k = 0; k < kp; ++k) {
-    const bool real = k < num_runs;
-    m.run[k] = MergeRun{real ? runs[k].perm : nullptr, real ? runs[k].lcp : nullptr, real ? runs[k].n : 0u, base};
-    if (real) base += runs[k].n / S;
+  const size_t recb = align256(total * sizeof(MergeRec));
+  MergeRec* rec[2] = {reinterpret_cast<MergeRec*>(ws), reinterpret_cast<MergeRec*>(ws + recb)};
+  uint32_t* cut = reinterpret_cast<uint32_t*>(ws + 2 * recb);
+  uint32_t* counter = reinterpret_cast<uint32_t*>(ws + 2 * recb + align256((total / S + K + 1) * 4));
+  const uint32_t cap = max_len ? std::min<uint32_t>(max_len, 1u << 30) : (1u << 30);
+  MergePrepArgs pa{};
+  pa.chars = chars;
+  pa.offsets = offsets;
+  pa.cap = cap;
+  pa.K = K;
+  pa.total = (uint32_t)total;
+  pa.dst = rec[0];
+  for (uint32_t k = 0; k <= K; ++k) pa.start[k] = start[k];
+  for (uint32_t k = 0; k < K; ++k) {
+    pa.perm[k] = runs[k].perm;
+    pa.lcp[k] = runs[k].lcp;
   }
-  const LaunchHook hook{st};
-  if (cudaMemsetAsync(m.next_piece, 0, sizeof(uint32_t), st) != cudaSuccess ||
-      launch_merge(m, logk, (uint32_t)dev.sms, st, hook) != cudaSuccess)
-    s = SS_ERR_CUDA;
-  if (own && cudaFreeAsync(ws, st) != cudaSuccess && s == SS_OK) s = SS_ERR_CUDA;
-  return s;
+  bool ok = launch_merge_prep(pa, sms, st, hook) == cudaSuccess;
+  uint32_t rounds = 0;
+  while ((1u << rounds) < K) ++rounds;
+  int cur = 0;
+  for (uint32_t r = 0; ok && r < rounds; ++r) {
+    const uint32_t w = 1u << r;
+    MergeRoundArgs ra{};
+    ra.chars = chars;
+    ra.offsets = offsets;
+    ra.cap = cap;
+    ra.ncur = (K + w - 1) / w;
+    ra.S = S;
+    ra.src = rec[cur];
+    ra.dst = r + 1 == rounds ? nullptr : rec[cur ^ 1];
+    ra.cut = cut;
+    ra.out_perm = out_perm;
+    ra.out_lcp = out_lcp;
+    ra.counter = counter;
+    uint32_t ns = 0;
+    for (uint32_t c = 0; c <= ra.ncur; ++c) {
+      ra.start[c] = start[std::min(c * w, K)];
+      ra.sbase[c] = ns;
+      if (c < ra.ncur) ns += (start[std::min((c + 1) * w, K)] - start[c * w]) / S;
+    }
+    ra.nsamples = ns;
+    ok = cudaMemsetAsync(counter, 0, sizeof(uint32_t), st) == cudaSuccess &&
+         launch_merge_round(ra, sms, st, hook) == cudaSuccess;
+    cur ^= 1;
+  }
+  if (own && cudaFreeAsync(ws, st) != cudaSuccess) ok = false;
+  return ok ? SS_OK : SS_ERR_CUDA;
 }
 
 // ---- suffix array by prefix doubling --------------------------------------------------

@@ -54,33 +54,54 @@ cudaError_t launch_distinguishing(const uint8_t* chars, const uint64_t* offsets,
                                   const uint32_t* perm, const uint32_t* lcp, uint8_t* dchar, uint32_t* dprefix,
                                   unsigned long long* sum_d, uint32_t grid, cudaStream_t st, const LaunchHook& hook);
 
-// K-way LCP merge of sorted runs (ss_merge.cu).
+// K-way LCP merge of sorted runs (ss_merge.cu): ceil(log2 K) rounds of
+// pairwise LCP merges over 32-byte records.
 constexpr uint32_t kMergeMaxRuns = 64;
 
-struct MergeRun {
-  const uint32_t* perm;
-  const uint32_t* lcp;
-  uint32_t n;
-  uint32_t sample_base;   // index of the run's first sample
+struct MergeRec {
+  uint64_t w0, w1;   // the string's characters [h, h + 16), first one most significant
+  uint64_t off;      // string offset
+  uint32_t idx;      // string index
+  uint32_t h;        // LCP with the preceding string of its run
 };
 
-struct MergeParams {
+// Records of all runs, run k at [start[k], start[k + 1]).
+struct MergePrepArgs {
   const uint8_t* chars;
   const uint64_t* offsets;
-  uint32_t* cut;          // C x K cut vectors
-  uint32_t* rank;         // C sample ranks
-  uint32_t* out_perm;
-  uint32_t* out_lcp;      // may be null
-  uint32_t* next_piece;   // piece counter (zero at launch)
-  uint32_t cap;           // strings end after cap characters
-  uint32_t K;             // runs, a power of two (unused runs are empty)
-  uint32_t S;             // every S-th string of a run is a sample
-  uint32_t C;             // samples
-  MergeRun run[kMergeMaxRuns];
+  uint32_t cap;
+  uint32_t K;
+  uint32_t total;
+  MergeRec* dst;
+  uint32_t start[kMergeMaxRuns + 1];
+  const uint32_t* perm[kMergeMaxRuns];
+  const uint32_t* lcp[kMergeMaxRuns];
 };
 
-cudaError_t launch_merge(const MergeParams& m, uint32_t logk, uint32_t sms, cudaStream_t st,
-                         const LaunchHook& hook);
+// One round: current run c at [start[c], start[c + 1]); runs 2p and 2p + 1
+// are merged into the same range; every S-th record of a run is a sample,
+// the samples of run c being [sbase[c], sbase[c + 1]).
+struct MergeRoundArgs {
+  const uint8_t* chars;
+  const uint64_t* offsets;
+  uint32_t cap;
+  uint32_t ncur;
+  uint32_t S;
+  uint32_t nsamples;
+  const MergeRec* src;
+  MergeRec* dst;            // null in the last round
+  uint32_t* cut;            // per sample: records of the partner run before it
+  uint32_t* out_perm;       // last round
+  uint32_t* out_lcp;        // last round, may be null
+  uint32_t* counter;        // piece counter, zero at launch
+  uint32_t start[kMergeMaxRuns + 1];
+  uint32_t sbase[kMergeMaxRuns + 1];
+};
+
+cudaError_t launch_merge_prep(const MergePrepArgs& a, uint32_t sms, cudaStream_t st, const LaunchHook& hook);
+cudaError_t launch_merge_round(const MergeRoundArgs& a, uint32_t sms, cudaStream_t st, const LaunchHook& hook);
+cudaError_t launch_merge_copy(const uint32_t* perm, const uint32_t* lcp, uint32_t n, uint32_t* out_perm,
+                              uint32_t* out_lcp, uint32_t sms, cudaStream_t st, const LaunchHook& hook);
 
 // Suffix array by prefix doubling (ss_sa.cu).
 enum class SaKernel { kIota, kHeads0, kName0, kCompact, kEncode, kApply, kRename, kLongFlags, kLcp };

@@ -1,31 +1,30 @@
-// K-way LCP-aware merge of sorted runs (Section 4.3.2, Algorithm 4.5) and its
-// parallel splitting into independent pieces (Section 4.3.3).
+// K-way LCP-aware merge of sorted runs (Section 4.3.2) as ceil(log2 K) rounds
+// of binary LCP merges (Algorithms 4.3 and 4.4), each split into independent
+// pieces (Section 4.3.3).
 //
-// Splitting.  Every S-th string of every run is a sample.  k_merge_cut gives
-// each sample its cut vector: for every run j, the number of strings of run j
-// that are <= the sample in the order (string, index), found by a binary
-// search that skips the prefix every string between the two bounds shares
-// with the sample; the sum is the sample's rank (its end position in the
-// output).  The pieces are the stretches of the output between consecutive
-// samples in rank order.  A sample's predecessor in that order is the largest
-// -ranked of the runs' last samples below it, found by a binary search per
-// run over that run's sample ranks (increasing, as the run is sorted), so no
-// sample sort is needed.
+// Records.  Every string of every run travels as a 32-byte record: its index,
+// its offset, h = its LCP with the string before it in its run, and its
+// characters [h, h + 16) as two big-endian words (the distinguishing
+// characters of the caching variant of Section 4.3.4, 16 at a time).  A merge
+// writes its output in the same form: the winner of each comparison already
+// carries h = LCP with the string output before it and the characters from
+// there on, so the output records of one round are the input of the next.
 //
-// Merging.  One warp merges one piece; each lane holds the front strings of
-// its runs with h = the LCP of the front with the last output string p (the
-// common predecessor LCP-Compare, Algorithm 4.2, needs) and the 8 characters
-// from depth h on (the distinguishing characters of the caching variant of
-// Section 4.3.4, 8 at a time).  Each output is one tournament over all fronts,
-// played as warp reductions instead of a replay of one root path of a loser
-// tree: unequal LCPs decide without reading characters (the larger LCP goes
-// first), equal LCPs compare the cached windows and read further windows only
-// for fronts that are still tied.  As in Algorithm 4.5, the LCP of the winner
-// is its h, and the string that replaces it enters with h = its LCP entry in
-// its run; every other front's h becomes its LCP with the winner (unchanged
-// below the maximum, from the compared windows at the maximum).  The first
-// output of a piece gets its LCP by one direct comparison with the sample that
-// ends the previous piece (the string just before it).
+// Splitting.  Every S-th record of every run is a sample.  k_merge_cut counts,
+// for each sample, the records of the partner run that go before it, with a
+// binary search that skips the prefix every record between the two bounds
+// shares with the sample.  The pieces of a pair of runs are the stretches of
+// its output between consecutive samples; each thread takes pieces from a
+// counter.  With two runs a piece holds at most 2S records.
+//
+// Merging a piece.  Both front records carry h = LCP with the last string
+// output (a piece starts after a sample, whose LCP with the other run's front
+// is computed directly).  LCP-Compare (Algorithm 4.2): unequal h decide
+// without reading characters (the larger h goes first, the loser keeps its
+// h); equal h compare the cached words, and read the strings only when 16
+// characters agree; the loser's h becomes its LCP with the winner and its
+// words are reloaded at that depth.  Ties of equal strings go by index, and an
+// index present in both runs takes the first run's record first.
 #include "../../include/ss_sort.h"
 #include "ss_kernels.h"
 
@@ -33,39 +32,21 @@ namespace ss {
 
 namespace {
 
-constexpr uint32_t kNoRun = 0xFFFFFFFFu;
-constexpr uint32_t kMergeBlock = 128;  // 4 warps
+constexpr uint32_t kMergeBlock = 128;
+constexpr uint32_t kNoSample = 0xFFFFFFFFu;
 
-// Lanes of a warp are split into groups of G lanes (G = the padded run count,
-// at least 4, at most 32); each group works on its own sample or piece, and
-// each lane of a group holds run t * G + (lane % G) for t < NS.
-template <int G>
-struct Group {
-  uint32_t lane, g, glane, mask;
-  __device__ __forceinline__ Group() {
-    lane = threadIdx.x & 31;
-    g = lane / G;
-    glane = lane % G;
-    mask = G == 32 ? 0xFFFFFFFFu : (((1u << G) - 1) << (g * G));
-  }
-  // index of this group among all groups of the grid
-  __device__ __forceinline__ uint32_t id() const {
-    return (blockIdx.x * (kMergeBlock / 32) + (threadIdx.x >> 5)) * (32 / G) + g;
-  }
-};
-
-__device__ __forceinline__ uint64_t cache_at(const MergeParams& m, uint64_t off, uint32_t h) {
-  return load_cache_2w(m.chars, off, h, m.cap);
+__device__ __forceinline__ uint64_t cache_at(const uint8_t* chars, uint32_t cap, uint64_t off, uint32_t h) {
+  return load_cache_2w(chars, off, h, cap);
 }
 
 // Compares string a (index ia, at offset oa) with string b (ib, ob); both
 // share their first h characters (and neither ends before h).  Returns <0 / 0
 // / >0 in the order (string, index) and sets *l = lcp(a, b).
-__device__ __forceinline__ int cmp_from(const MergeParams& m, uint32_t ia, uint64_t oa, uint32_t ib, uint64_t ob,
-                                        uint32_t h, uint32_t* l) {
+__device__ __forceinline__ int cmp_from(const uint8_t* chars, uint32_t cap, uint32_t ia, uint64_t oa, uint32_t ib,
+                                        uint64_t ob, uint32_t h, uint32_t* l) {
   while (true) {
-    const uint64_t ca = cache_at(m, oa, h);
-    const uint64_t cb = cache_at(m, ob, h);
+    const uint64_t ca = cache_at(chars, cap, oa, h);
+    const uint64_t cb = cache_at(chars, cap, ob, h);
     if (ca != cb) {
       *l = h + lcp8(ca, cb);
       return ca < cb ? -1 : 1;
@@ -78,467 +59,273 @@ __device__ __forceinline__ int cmp_from(const MergeParams& m, uint32_t ia, uint6
   }
 }
 
-// The run that sample i belongs to (sample_base is non-decreasing in k).
-__device__ __forceinline__ uint32_t sample_run(const MergeParams& m, uint32_t i) {
-  uint32_t lo = 0, hi = m.K;  // last k with sample_base[k] <= i
+__device__ __forceinline__ MergeRec load_mrec(const MergeRec* p) {
+  const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+  const uint4 b = __ldg(reinterpret_cast<const uint4*>(p) + 1);
+  MergeRec r;
+  r.w0 = ((uint64_t)a.y << 32) | a.x;
+  r.w1 = ((uint64_t)a.w << 32) | a.z;
+  r.off = ((uint64_t)b.y << 32) | b.x;
+  r.idx = b.z;
+  r.h = b.w;
+  return r;
+}
+
+__device__ __forceinline__ void store_mrec(MergeRec* p, const MergeRec& r) {
+  uint4* q = reinterpret_cast<uint4*>(p);
+  q[0] = make_uint4((uint32_t)r.w0, (uint32_t)(r.w0 >> 32), (uint32_t)r.w1, (uint32_t)(r.w1 >> 32));
+  q[1] = make_uint4((uint32_t)r.off, (uint32_t)(r.off >> 32), r.idx, r.h);
+}
+
+// The 16 characters of a string from depth h (no terminator before h).
+__device__ __forceinline__ void load_words(const uint8_t* chars, uint32_t cap, uint64_t off, uint32_t h,
+                                           uint64_t& w0, uint64_t& w1) {
+  w0 = cache_at(chars, cap, off, h);
+  w1 = has_nul(w0) ? 0ull : cache_at(chars, cap, off, h + 8);
+}
+
+// Index of the last range whose start is <= i (starts non-decreasing).
+__device__ __forceinline__ uint32_t find_range(const uint32_t* start, uint32_t count, uint32_t i) {
+  uint32_t lo = 0, hi = count;  // start[lo] <= i < start[hi]
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (m.run[mid].sample_base <= i) lo = mid; else hi = mid;
+    if (start[mid] <= i) lo = mid; else hi = mid;
   }
   return lo;
 }
 
-__device__ __forceinline__ uint32_t sample_pos(const MergeParams& m, uint32_t k, uint32_t i) {
-  return (i - m.run[k].sample_base + 1) * m.S - 1;
-}
+// ---- round 0: records of the input runs --------------------------------------------------
 
-// Cut vectors and ranks; one lane group per sample, one lane per run.
-template <int G, int NS>
-__global__ void __launch_bounds__(kMergeBlock) k_merge_cut(MergeParams m) {
-  const Group<G> gr;
-  const uint32_t groups = gridDim.x * (kMergeBlock / 32) * (32 / G);
-  for (uint32_t i = gr.id(); i < m.C; i += groups) {
-    const uint32_t k = sample_run(m, i);
-    const uint32_t p = sample_pos(m, k, i);
-    const uint32_t sidx = m.run[k].perm[p];
-    const uint64_t soff = m.offsets[sidx];
-    uint32_t sum = 0;
-#pragma unroll
-    for (int t = 0; t < NS; ++t) {
-      const uint32_t j = t * G + gr.glane;
-      if (j >= m.K) continue;
-      uint32_t cut;
-      if (j == k) {
-        cut = p + 1;
-      } else {
-        const uint32_t* perm = m.run[j].perm;
-        uint32_t lo = 0, hi = m.run[j].n, llo = 0, lhi = 0;
-        while (lo < hi) {
-          const uint32_t mid = (lo + hi) >> 1;
-          const uint32_t e = perm[mid];
-          uint32_t l;
-          const int c = cmp_from(m, e, m.offsets[e], sidx, soff, llo < lhi ? llo : lhi, &l);
-          if (c <= 0) { lo = mid + 1; llo = l; } else { hi = mid; lhi = l; }
-        }
-        cut = lo;
-      }
-      m.cut[(size_t)i * m.K + j] = cut;
-      sum += cut;
-    }
-    sum = __reduce_add_sync(gr.mask, sum);
-    if (gr.glane == 0) m.rank[i] = sum;
+__global__ void __launch_bounds__(256) k_merge_prep(MergePrepArgs a) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += gridDim.x * blockDim.x) {
+    const uint32_t k = find_range(a.start, a.K, g);
+    const uint32_t j = g - a.start[k];
+    MergeRec r;
+    r.idx = a.perm[k][j];
+    r.h = j ? a.lcp[k][j] : 0u;
+    r.off = a.offsets[r.idx];
+    load_words(a.chars, a.cap, r.off, r.h, r.w0, r.w1);
+    store_mrec(a.dst + g, r);
   }
 }
 
-// Common prefix of two 8-character windows at the same depth, in characters:
-// up to the first difference, or up to the terminator when they are equal and
-// hold one (the strings end there), else all 8.
-__device__ __forceinline__ uint32_t window_lcp(uint64_t a, uint64_t b) {
-  return a != b ? lcp8(a, b) : (has_nul(a) ? nnz_prefix(a) : 8u);
-}
+// ---- splitting -------------------------------------------------------------------------
 
-// Group minimum of a 64-bit value (every lane of the group takes part; lanes
-// without a candidate pass ~0).
-__device__ __forceinline__ uint64_t group_min_u64(uint32_t mask, uint64_t v) {
-  const uint32_t hi = __reduce_min_sync(mask, (uint32_t)(v >> 32));
-  const uint32_t lo = __reduce_min_sync(mask, (uint32_t)(v >> 32) == hi ? (uint32_t)v : 0xFFFFFFFFu);
-  return ((uint64_t)hi << 32) | lo;
-}
-
-// ---- 16-character windows loaded ahead of use --------------------------------------------
-//
-// A load is split into issuing the aligned words (Raw16) and reading them out
-// (finish16) so that the memory round trip overlaps the tournaments that run
-// in between.  The three words covering characters [h, h + 16) are issued at
-// once only when they lie in the 4 KiB block that holds character h (the
-// string or its terminator is in that block, so the reads cannot fault);
-// otherwise the window is read later with the terminator-checked load.
-
-struct Raw16 {
-  uint64_t x0, x1, x2;
-  uint64_t off;
-  uint32_t h;
-  uint32_t ok;   // 1: the words were issued
-};
-
-__device__ __forceinline__ void raw16_issue(const MergeParams& m, uint64_t off, uint32_t h, Raw16& r) {
-  r.off = off;
-  r.h = h;
-  const uintptr_t a = (uintptr_t)(m.chars + off + h);
-  const uintptr_t p = a & ~(uintptr_t)7;
-  r.ok = (h < m.cap) && (p + 24 <= ((a | 4095u) + 1));
-  if (r.ok) {
-    const uint64_t* w = reinterpret_cast<const uint64_t*>(p);
-    r.x0 = __ldg(w);
-    r.x1 = __ldg(w + 1);
-    r.x2 = __ldg(w + 2);
-  } else {
-    r.x0 = r.x1 = r.x2 = 0;
-  }
-}
-
-// Raw little-endian bytes of a window, cut at the terminator or after `room`
-// characters, as a big-endian key.
-__device__ __forceinline__ uint64_t finish_window(uint64_t v, uint32_t room) {
-  const uint32_t z = first_zero_byte(v);
-  const uint32_t keep = z < room ? z : room;
-  if (keep < 8) v &= keep == 0 ? 0ull : (~0ull >> (64 - 8 * keep));
-  return bswap64(v);
-}
-
-// The window at depth h of a Raw16.
-__device__ __forceinline__ uint64_t finish8(const MergeParams& m, const Raw16& r) {
-  if (r.h >= m.cap) return 0;
-  if (!r.ok) return cache_at(m, r.off, r.h);
-  const uint32_t sh = (uint32_t)((uintptr_t)(m.chars + r.off + r.h) & 7) * 8;
-  return finish_window(sh ? (r.x0 >> sh) | (r.x1 << (64 - sh)) : r.x0, m.cap - r.h);
-}
-
-// The windows at depths h and h + 8 of a Raw16.
-__device__ __forceinline__ void finish16(const MergeParams& m, const Raw16& r, uint64_t& w0, uint64_t& w1) {
-  if (r.h >= m.cap) {
-    w0 = w1 = 0;
-    return;
-  }
-  const uint32_t room = m.cap - r.h;
-  if (r.ok) {
-    const uint32_t sh = (uint32_t)((uintptr_t)(m.chars + r.off + r.h) & 7) * 8;
-    const uint64_t v0 = sh ? (r.x0 >> sh) | (r.x1 << (64 - sh)) : r.x0;
-    const uint64_t v1 = sh ? (r.x1 >> sh) | (r.x2 << (64 - sh)) : r.x1;
-    w0 = finish_window(v0, room);
-    w1 = (has_nul(w0) || room <= 8) ? 0ull : finish_window(v1, room - 8);
-  } else {
-    w0 = cache_at(m, r.off, r.h);
-    w1 = (has_nul(w0) || room <= 8) ? 0ull : cache_at(m, r.off, r.h + 8);
-  }
-}
-
-// One run of a piece as seen by its lane.  The front string is compared: its
-// index, h = LCP with the last output, w0 = the 8 characters from depth h and
-// the next 8 (w1, read out of the pending words `fr` when first needed).  The
-// next string has its words in flight, the one after it its index, LCP entry
-// and offset.
-struct Slot {
-  uint32_t pos, end;             // front at pos; valid while pos < end
-  uint32_t fidx, fh;
-  uint64_t fw0, fw1;
-  Raw16 fr;                      // pending words for fw1 (fpend)
-  bool fpend;
-  uint32_t nidx;
-  Raw16 nr;                      // next string: words at depth nr.h (its LCP entry)
-  uint32_t n2idx, n2h;
-  uint64_t n2off;
-};
-
-__device__ __forceinline__ void slot_fetch(const MergeParams& m, const MergeRun& r, uint32_t p, uint32_t end,
-                                           uint32_t& idx, uint32_t& h, uint64_t& off) {
-  if (p < end) {
-    idx = r.perm[p];
-    h = r.lcp[p];
-    off = m.offsets[idx];
-  } else {
-    idx = 0;
-    h = 0;
-    off = 0;
-  }
-}
-
-__device__ __forceinline__ void slot_init(const MergeParams& m, const MergeRun& r, Slot& s, uint32_t pos,
-                                          uint32_t end) {
-  s.pos = pos;
-  s.end = end;
-  uint32_t h;
-  uint64_t off;
-  slot_fetch(m, r, pos, end, s.fidx, h, off);  // the first string of a run in the piece: h = 0
-  uint32_t nh;
-  uint64_t noff;
-  slot_fetch(m, r, pos + 1, end, s.nidx, nh, noff);
-  slot_fetch(m, r, pos + 2, end, s.n2idx, s.n2h, s.n2off);
-  s.fh = 0;
-  s.fpend = false;
-  s.fr.ok = 0;
-  if (pos < end) {
-    Raw16 r0;
-    raw16_issue(m, off, 0, r0);
-    finish16(m, r0, s.fw0, s.fw1);
-    s.fr = r0;
-  } else {
-    s.fw0 = s.fw1 = 0;
-    s.fr.off = 0;
-    s.fr.h = 0;
-  }
-  if (pos + 1 < end) raw16_issue(m, noff, nh, s.nr);
-  else s.nr.ok = 0, s.nr.off = 0, s.nr.h = 0;
-}
-
-__device__ __forceinline__ uint64_t slot_w1(const MergeParams& m, Slot& s) {
-  if (s.fpend) {
-    uint64_t w0;
-    finish16(m, s.fr, w0, s.fw1);
-    s.fpend = false;
-  }
-  return s.fw1;
-}
-
-__device__ __forceinline__ void slot_advance(const MergeParams& m, const MergeRun& r, Slot& s) {
-  ++s.pos;
-  s.fidx = s.nidx;
-  s.fh = s.nr.h;
-  s.fr = s.nr;
-  s.fpend = false;
-  if (s.pos < s.end) {
-    s.fw0 = finish8(m, s.nr);
-    s.fpend = !has_nul(s.fw0);  // w1 is read out of the same words when first needed
-    if (!s.fpend) s.fw1 = 0;
-  }
-  s.nidx = s.n2idx;
-  if (s.pos + 1 < s.end) raw16_issue(m, s.n2off, s.n2h, s.nr);
-  slot_fetch(m, r, s.pos + 2, s.end, s.n2idx, s.n2h, s.n2off);
-}
-
-// The front lost with LCP lw > fh to the winner: move its windows to depth lw.
-__device__ __forceinline__ void slot_deepen(const MergeParams& m, Slot& s, uint32_t lw) {
-  const uint32_t d = lw - s.fh;
-  const uint64_t off = s.fr.off;
-  if (d < 8) {
-    const uint64_t w1 = slot_w1(m, s);
-    s.fw0 = (s.fw0 << (8 * d)) | (w1 >> (64 - 8 * d));
-  } else if (d == 8) {
-    s.fw0 = slot_w1(m, s);
-  } else {
-    s.fw0 = cache_at(m, off, lw);
-  }
-  s.fh = lw;
-  if (has_nul(s.fw0)) {
-    s.fw1 = 0;
-    s.fpend = false;
-    s.fr.h = lw;
-  } else {
-    raw16_issue(m, off, lw, s.fr);
-    s.fpend = true;
-  }
-}
-
-// One lane group merges one piece at a time, taking pieces from a counter.
-// Every output is one LCP-aware tournament over the runs' front strings, all
-// of which carry h = LCP with the last output p: the largest h goes first
-// (cases 2 and 3 of LCP-Compare, no characters read); among the fronts with
-// that h the 8 cached characters decide, then further 8-character windows of
-// the fronts still tied, then the index (then the run, for an index present
-// in two runs).  Afterwards every front's h becomes its LCP with the string
-// just written: unchanged below the maximum, and from the compared windows for
-// the fronts that had it.  The winner's run moves on; its next string enters
-// with h = its LCP entry in the run.  Outputs are buffered one per lane and
-// written G at a time.
-template <int G, int NS>
-__global__ void __launch_bounds__(kMergeBlock) k_merge_pieces(MergeParams m) {
-  const Group<G> gr;
-  const uint32_t gm = gr.mask;
-  while (true) {
-    uint32_t q = 0;
-    if (gr.glane == 0) q = atomicAdd(m.next_piece, 1u);
-    q = __shfl_sync(gm, q, gr.g * G);
-    if (q > m.C) return;  // uniform within the group
-    // predecessor sample: the largest rank below this piece's end sample
-    const uint64_t rq = q < m.C ? (uint64_t)m.rank[q] : ~0ull;
-    uint32_t best = 0, best_id = 0;  // rank + 1 of this lane's best candidate
-#pragma unroll
-    for (int t = 0; t < NS; ++t) {
-      const uint32_t j = t * G + gr.glane;
-      if (j >= m.K) continue;
-      const uint32_t base = m.run[j].sample_base;
-      uint32_t lo = 0, hi = m.run[j].n / m.S;
+// For each sample: the records of the partner run that go before it (for a
+// sample of the first run of a pair, the partner's records that are smaller;
+// for one of the second run, those that are smaller or the same record).
+__global__ void __launch_bounds__(256) k_merge_cut(MergeRoundArgs a) {
+  for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < a.nsamples; s += gridDim.x * blockDim.x) {
+    const uint32_t c = find_range(a.sbase, a.ncur, s);
+    const uint32_t pos = (s - a.sbase[c] + 1) * a.S - 1;
+    const MergeRec x = load_mrec(a.src + a.start[c] + pos);
+    const uint32_t q = c ^ 1u;
+    uint32_t lo = 0, hi = 0;
+    if (q < a.ncur) {
+      const MergeRec* prt = a.src + a.start[q];
+      hi = a.start[q + 1] - a.start[q];
+      uint32_t llo = 0, lhi = 0;  // LCP of the sample with the records just below / at the bounds
+      const bool strict = (c & 1u) == 0;
       while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if ((uint64_t)m.rank[base + mid] < rq) lo = mid + 1; else hi = mid;
-      }
-      if (lo > 0 && m.rank[base + lo - 1] + 1 > best) {
-        best = m.rank[base + lo - 1] + 1;
-        best_id = base + lo - 1;
-      }
-    }
-    const uint32_t pbest = __reduce_max_sync(gm, best);
-    uint32_t pred = kNoRun;
-    if (pbest > 0) {
-      const uint32_t owner = __ffs(__ballot_sync(gm, best == pbest)) - 1;
-      pred = __shfl_sync(gm, best_id, owner);
-    }
-    Slot sl[NS];
-#pragma unroll
-    for (int t = 0; t < NS; ++t) {
-      const uint32_t j = t * G + gr.glane;
-      uint32_t p0 = 0, e0 = 0;
-      if (j < m.K) {
-        p0 = pred == kNoRun ? 0u : m.cut[(size_t)pred * m.K + j];
-        e0 = q < m.C ? m.cut[(size_t)q * m.K + j] : m.run[j].n;
-      }
-      slot_init(m, m.run[j < m.K ? j : 0], sl[t], p0, e0);
-    }
-    uint32_t out = pred == kNoRun ? 0u : pbest - 1;
-    uint32_t pred_idx = 0;
-    uint64_t pred_off = 0;
-    if (pred != kNoRun) {
-      const uint32_t k = sample_run(m, pred);
-      pred_idx = m.run[k].perm[sample_pos(m, k, pred)];
-      pred_off = m.offsets[pred_idx];
-    }
-    bool first = true;
-    uint32_t cnt = 0, ob_idx = 0, ob_lcp = 0;
-    while (true) {
-      uint32_t hk = 0;
-#pragma unroll
-      for (int t = 0; t < NS; ++t)
-        if (sl[t].pos < sl[t].end && sl[t].fh + 1 > hk) hk = sl[t].fh + 1;
-      const uint32_t H1 = __reduce_max_sync(gm, hk);
-      if (H1 == 0) break;
-      const uint32_t H = H1 - 1;
-      bool cand[NS];
-      uint32_t ncand = 0, cslot = 0;
-#pragma unroll
-      for (int t = 0; t < NS; ++t) {
-        cand[t] = sl[t].pos < sl[t].end && sl[t].fh == H;
-        const uint32_t b = __ballot_sync(gm, cand[t]);
-        if (b) cslot = t * G + (__ffs(b) - 1) % G;
-        ncand += __popc(b);
-      }
-      bool in[NS];
-      uint32_t lw[NS];
-      uint32_t wid, imin;
-      if (ncand == 1) {
-        // one front has the largest LCP with the last output: it goes first
-        // (cases 2/3 of LCP-Compare), and no other front's LCP changes
-        wid = cslot;
-        uint32_t wi = 0;
-#pragma unroll
-        for (int t = 0; t < NS; ++t) {
-          in[t] = cand[t];
-          lw[t] = sl[t].fh;
-          if (cand[t]) wi = sl[t].fidx;
+        const uint4 b = __ldg(reinterpret_cast<const uint4*>(prt + mid) + 1);
+        const uint64_t off = ((uint64_t)b.y << 32) | b.x;
+        uint32_t l;
+        const int cmp = cmp_from(a.chars, a.cap, b.z, off, x.idx, x.off, llo < lhi ? llo : lhi, &l);
+        if (strict ? cmp < 0 : cmp <= 0) {
+          lo = mid + 1;
+          llo = l;
+        } else {
+          hi = mid;
+          lhi = l;
         }
-        imin = __shfl_sync(gm, wi, gr.g * G + wid % G);
+      }
+    }
+    a.cut[s] = lo;
+  }
+}
+
+// End of a sample in its pair's output: records of the first and second run
+// up to and including it.
+__device__ __forceinline__ void sample_end(const MergeRoundArgs& a, uint32_t c, uint32_t t, uint32_t& ea,
+                                           uint32_t& eb) {
+  const uint32_t pos = (t + 1) * a.S;  // records of its own run up to and including it
+  const uint32_t cut = a.cut[a.sbase[c] + t];
+  if (c & 1u) {
+    ea = cut;
+    eb = pos;
+  } else {
+    ea = pos;
+    eb = cut;
+  }
+}
+
+// Last sample of run c whose end rank is below `rank` (its rank to r_out),
+// or kNoSample.
+__device__ __forceinline__ uint32_t last_sample_below(const MergeRoundArgs& a, uint32_t c, uint32_t rank,
+                                                      uint32_t& r_out) {
+  if (c >= a.ncur) return kNoSample;
+  uint32_t lo = 0, hi = a.sbase[c + 1] - a.sbase[c];
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    uint32_t ea, eb;
+    sample_end(a, c, mid, ea, eb);
+    if (ea + eb < rank) lo = mid + 1; else hi = mid;
+  }
+  if (lo == 0) return kNoSample;
+  uint32_t ea, eb;
+  sample_end(a, c, lo - 1, ea, eb);
+  r_out = ea + eb;
+  return lo - 1;
+}
+
+// ---- merging ------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kMergeBlock) k_merge_round(MergeRoundArgs a) {
+  const uint32_t npairs = (a.ncur + 1) / 2;
+  const uint32_t npieces = a.nsamples + npairs;
+  while (true) {
+    const uint32_t q = atomicAdd(a.counter, 1u);
+    if (q >= npieces) return;
+    // the pair and the end of this piece (records of each run up to it)
+    uint32_t p, ea, eb;
+    if (q < a.nsamples) {
+      const uint32_t c = find_range(a.sbase, a.ncur, q);
+      p = c >> 1;
+      sample_end(a, c, q - a.sbase[c], ea, eb);
+    } else {
+      p = q - a.nsamples;
+      ea = a.start[min(2 * p + 1, a.ncur)] - a.start[2 * p];
+      eb = a.start[min(2 * p + 2, a.ncur)] - a.start[min(2 * p + 1, a.ncur)];
+    }
+    const uint32_t cA = 2 * p, cB = 2 * p + 1;
+    const uint32_t base = a.start[cA];
+    const MergeRec* A = a.src + base;
+    const MergeRec* B = a.src + a.start[min(cB, a.ncur)];
+    // the piece starts after the latest sample of the pair that ends before it
+    uint32_t sa = 0, sb = 0, prev_run = 2;  // prev_run: 0 = A, 1 = B, 2 = none
+    {
+      uint32_t ra = 0, rb = 0;
+      const uint32_t ta = last_sample_below(a, cA, ea + eb, ra);
+      const uint32_t tb = last_sample_below(a, cB, ea + eb, rb);
+      if (ta != kNoSample && (tb == kNoSample || ra > rb)) {
+        sample_end(a, cA, ta, sa, sb);
+        prev_run = 0;
+      } else if (tb != kNoSample) {
+        sample_end(a, cB, tb, sa, sb);
+        prev_run = 1;
+      }
+    }
+    uint32_t out = sa + sb;
+    const uint32_t out_end = ea + eb;
+    if (out >= out_end) continue;
+    uint32_t ia = sa, jb = sb;
+    MergeRec fa{}, fb{};
+    if (ia < ea) fa = load_mrec(A + ia);
+    if (jb < eb) fb = load_mrec(B + jb);
+    // LCP of the other run's front with the sample just before the piece
+    if (prev_run == 0 && jb < eb) {
+      const MergeRec P = load_mrec(A + sa - 1);
+      cmp_from(a.chars, a.cap, P.idx, P.off, fb.idx, fb.off, 0, &fb.h);
+      load_words(a.chars, a.cap, fb.off, fb.h, fb.w0, fb.w1);
+    } else if (prev_run == 1 && ia < ea) {
+      const MergeRec P = load_mrec(B + sb - 1);
+      cmp_from(a.chars, a.cap, P.idx, P.off, fa.idx, fa.off, 0, &fa.h);
+      load_words(a.chars, a.cap, fa.off, fa.h, fa.w0, fa.w1);
+    }
+    const bool last = a.dst == nullptr;
+    while (out < out_end) {
+      bool take_a;
+      if (ia >= ea) {
+        take_a = false;
+      } else if (jb >= eb) {
+        take_a = true;
+      } else if (fa.h != fb.h) {
+        take_a = fa.h > fb.h;  // the larger LCP with the last output goes first; the loser keeps its h
       } else {
-      uint64_t cm = ~0ull;
-#pragma unroll
-      for (int t = 0; t < NS; ++t)
-        if (cand[t] && sl[t].fw0 < cm) cm = sl[t].fw0;
-      const uint64_t cmin = group_min_u64(gm, cm);
-      uint32_t nin = 0;
-#pragma unroll
-      for (int t = 0; t < NS; ++t) {
-        in[t] = cand[t] && sl[t].fw0 == cmin;
-        lw[t] = cand[t] ? H + window_lcp(sl[t].fw0, cmin) : sl[t].fh;
-        nin += in[t];
-      }
-      nin = __reduce_add_sync(gm, nin);
-      if (nin > 1) {
-        uint64_t key = cmin;
-        uint32_t depth = H;
-        while (!has_nul(key)) {  // tied fronts continue past this window: compare the next one
-          depth += 8;
-          uint64_t c2[NS];
-          uint64_t mm = ~0ull;
-#pragma unroll
-          for (int t = 0; t < NS; ++t) {
-            c2[t] = ~0ull;
-            if (in[t]) c2[t] = depth == H + 8 ? slot_w1(m, sl[t]) : cache_at(m, sl[t].fr.off, depth);
-            if (c2[t] < mm) mm = c2[t];
+        const uint32_t h = fa.h;
+        uint32_t lw;
+        if (fa.w0 != fb.w0) {
+          take_a = fa.w0 < fb.w0;
+          lw = h + lcp8(fa.w0, fb.w0);
+        } else if (has_nul(fa.w0)) {
+          take_a = fa.idx <= fb.idx;
+          lw = h + nnz_prefix(fa.w0);
+        } else if (fa.w1 != fb.w1) {
+          take_a = fa.w1 < fb.w1;
+          lw = h + 8 + lcp8(fa.w1, fb.w1);
+        } else if (has_nul(fa.w1)) {
+          take_a = fa.idx <= fb.idx;
+          lw = h + 8 + nnz_prefix(fa.w1);
+        } else {
+          take_a = cmp_from(a.chars, a.cap, fa.idx, fa.off, fb.idx, fb.off, h + 16, &lw) <= 0;
+        }
+        if (take_a) {
+          if (lw != fb.h) {
+            fb.h = lw;
+            load_words(a.chars, a.cap, fb.off, lw, fb.w0, fb.w1);
           }
-          key = group_min_u64(gm, mm);
-          uint32_t k2 = 0;
-#pragma unroll
-          for (int t = 0; t < NS; ++t) {
-            if (in[t]) {
-              lw[t] = depth + window_lcp(c2[t], key);
-              if (c2[t] != key) in[t] = false;
-            }
-            k2 += in[t];
-          }
-          if (__reduce_add_sync(gm, k2) <= 1) break;
+        } else if (lw != fa.h) {
+          fa.h = lw;
+          load_words(a.chars, a.cap, fa.off, lw, fa.w0, fa.w1);
         }
       }
-      // winner: smallest index among the fronts still tied, then the lowest slot
-      uint32_t im = 0xFFFFFFFFu;
-#pragma unroll
-      for (int t = 0; t < NS; ++t)
-        if (in[t] && sl[t].fidx < im) im = sl[t].fidx;
-      imin = __reduce_min_sync(gm, im);
-      uint32_t id = 0xFFFFFFFFu;
-#pragma unroll
-      for (int t = 0; t < NS; ++t)
-        if (in[t] && sl[t].fidx == imin && t * G + gr.glane < id) id = t * G + gr.glane;
-      wid = __reduce_min_sync(gm, id);
+      const MergeRec w = take_a ? fa : fb;
+      if (last) {
+        a.out_perm[base + out] = w.idx;
+        if (a.out_lcp) a.out_lcp[base + out] = out == 0 ? 0u : w.h;
+      } else {
+        MergeRec o = w;
+        if (out == 0) o.h = 0;
+        store_mrec(a.dst + base + out, o);
       }
-      const uint32_t wlane = gr.g * G + wid % G;
-      uint32_t olcp = H;
-      if (first) {
-        uint32_t l = 0;
-        if (pred != kNoRun && wlane == gr.lane) {
-          uint64_t woff = 0;
-#pragma unroll
-          for (int t = 0; t < NS; ++t)
-            if ((uint32_t)t == wid / G) woff = sl[t].fr.off;
-          cmp_from(m, pred_idx, pred_off, imin, woff, 0, &l);
-        }
-        olcp = __shfl_sync(gm, l, wlane);
-        first = false;
+      ++out;
+      if (take_a) {
+        if (++ia < ea) fa = load_mrec(A + ia);
+      } else {
+        if (++jb < eb) fb = load_mrec(B + jb);
       }
-      if (gr.glane == cnt) {
-        ob_idx = imin;
-        ob_lcp = olcp;
-      }
-      if (++cnt == G) {
-        m.out_perm[out + gr.glane] = ob_idx;
-        if (m.out_lcp) m.out_lcp[out + gr.glane] = ob_lcp;
-        out += G;
-        cnt = 0;
-      }
-#pragma unroll
-      for (int t = 0; t < NS; ++t) {
-        if ((uint32_t)t * G + gr.glane == wid) slot_advance(m, m.run[t * G + gr.glane], sl[t]);
-        else if (cand[t] && lw[t] != sl[t].fh) slot_deepen(m, sl[t], lw[t]);
-      }
-    }
-    if (gr.glane < cnt) {
-      m.out_perm[out + gr.glane] = ob_idx;
-      if (m.out_lcp) m.out_lcp[out + gr.glane] = ob_lcp;
     }
   }
 }
 
-template <int G, int NS>
-cudaError_t launch_merge_g(const MergeParams& m, uint32_t sms, cudaStream_t st, const LaunchHook& hook) {
-  constexpr uint32_t per_block = (kMergeBlock / 32) * (32 / G);
-  if (m.C > 0) {
-    const uint32_t cut_grid = std::max(1u, std::min(sms * 16, (m.C + per_block - 1) / per_block));
-    hook.run("merge_cut", [&] { k_merge_cut<G, NS><<<cut_grid, kMergeBlock, 0, st>>>(m); });
-    const cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+__global__ void k_merge_copy(const uint32_t* __restrict__ perm, const uint32_t* __restrict__ lcp, uint32_t n,
+                             uint32_t* __restrict__ out_perm, uint32_t* __restrict__ out_lcp) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    out_perm[j] = perm[j];
+    if (out_lcp) out_lcp[j] = j ? lcp[j] : 0u;
   }
-  static int resident = 0;  // blocks per SM (the same on every device this library runs on)
-  if (resident == 0) {
-    int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_merge_pieces<G, NS>, kMergeBlock, 0) != cudaSuccess ||
-        b < 1)
-      b = 1;
-    resident = b;
-  }
-  const uint32_t grid = std::max(1u, std::min(sms * (uint32_t)resident, (m.C + 1 + per_block - 1) / per_block));
-  hook.run("merge_pieces", [&] { k_merge_pieces<G, NS><<<grid, kMergeBlock, 0, st>>>(m); });
-  return cudaGetLastError();
+}
+
+uint32_t grid_for(uint64_t items, uint32_t block, uint32_t sms, uint32_t per_sm) {
+  const uint64_t g = (items + block - 1) / block;
+  return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(g, (uint64_t)sms * per_sm));
 }
 
 }  // namespace
 
-cudaError_t launch_merge(const MergeParams& m, uint32_t logk, uint32_t sms, cudaStream_t st,
-                         const LaunchHook& hook) {
-  switch (logk) {
-    case 0: case 1: case 2: return launch_merge_g<4, 1>(m, sms, st, hook);
-    case 3: return launch_merge_g<8, 1>(m, sms, st, hook);
-    case 4: return launch_merge_g<16, 1>(m, sms, st, hook);
-    case 5: return launch_merge_g<32, 1>(m, sms, st, hook);
-    case 6: return launch_merge_g<32, 2>(m, sms, st, hook);
-    default: return cudaErrorInvalidValue;
+cudaError_t launch_merge_prep(const MergePrepArgs& a, uint32_t sms, cudaStream_t st, const LaunchHook& hook) {
+  hook.run("merge_prep", [&] { k_merge_prep<<<grid_for(a.total, 256, sms, 16), 256, 0, st>>>(a); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_round(const MergeRoundArgs& a, uint32_t sms, cudaStream_t st, const LaunchHook& hook) {
+  if (a.nsamples) {
+    hook.run("merge_cut", [&] { k_merge_cut<<<grid_for(a.nsamples, 256, sms, 16), 256, 0, st>>>(a); });
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
+  const uint32_t pieces = a.nsamples + (a.ncur + 1) / 2;
+  hook.run("merge_round",
+           [&] { k_merge_round<<<grid_for(pieces, kMergeBlock, sms, 16), kMergeBlock, 0, st>>>(a); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_merge_copy(const uint32_t* perm, const uint32_t* lcp, uint32_t n, uint32_t* out_perm,
+                              uint32_t* out_lcp, uint32_t sms, cudaStream_t st, const LaunchHook& hook) {
+  hook.run("merge_round",
+           [&] { k_merge_copy<<<grid_for(n, 256, sms, 16), 256, 0, st>>>(perm, lcp, n, out_perm, out_lcp); });
+  return cudaGetLastError();
 }
 
 }  // namespace ss

@@ -122,11 +122,13 @@ def test_merge_workspace_size(lib):
     for r, n in zip(runs, (1000, 50, 3000)):
         r.perm = r.lcp = 4096
         r.n = n
-    # samples: 1000 // 64 + 50 // 64 + 3000 // 64 = 15 + 0 + 46; 4 padded runs
-    c = 15 + 46
-    # cut vectors, sample ranks, the piece counter
-    assert lib.ss_merge_workspace_size(runs, 3, 64) == ((c * 4 * 4 + 255) // 256 + (c * 4 + 255) // 256 + 1) * 256
-    assert lib.ss_merge_workspace_size(runs, 3, 4096) == 256   # one piece: the counter only
+    al = lambda x: (x + 255) // 256 * 256  # noqa: E731
+    total = 4050
+    # two 32-byte record buffers, the sample cuts of a round, the piece counter
+    for step in (64, 4096):
+        want = 2 * al(total * 32) + al((total // step + 3 + 1) * 4) + 256
+        assert lib.ss_merge_workspace_size(runs, 3, step) == want
+    assert lib.ss_merge_workspace_size(runs, 1, 0) == 256   # one run: a copy
     assert lib.ss_merge_workspace_size(runs, 0, 0) == 0
 
 
