@@ -456,9 +456,18 @@ def run_ours(args, ws, rank, local):
 
 # ---- K-way LCP merge of sorted runs ------------------------------------------------------------
 
-# algorithmic bytes per merged string: its index and LCP entry read from its
-# run (8), its offset (8), one 8-character window (8), index and LCP written (8)
-MERGE_BYTES_PER_STRING = 32
+# Algorithmic bytes of the merge's rounds (the dominant kernel): per string and
+# round, its 32-byte record read and written (index, offset, LCP, 16
+# characters), the last round writing the index and LCP (8) instead.  The
+# record gather before the rounds: index and LCP entry read (8), offset (8),
+# 16 characters (16), record written (32).
+MERGE_RECORD_BYTES = 32
+
+
+def merge_round_bytes(n: int, runs: int) -> float:
+    """Average algorithmic bytes per launch of the merge rounds."""
+    rounds = max(1, (runs - 1).bit_length())
+    return n * (2 * MERGE_RECORD_BYTES * (rounds - 1) + MERGE_RECORD_BYTES + 8) / rounds
 
 
 def run_merge(args, ws, rank, local):
@@ -516,14 +525,14 @@ def run_merge(args, ws, rank, local):
 
     peak, peak_kind = measured_peaks()
     roof = None
-    if "merge_pieces" in stats:
-        nl, kms, _ = stats["merge_pieces"]
-        kbytes = MERGE_BYTES_PER_STRING * n
+    if "merge_round" in stats:
+        nl, kms, _ = stats["merge_round"]
+        kbytes = merge_round_bytes(n, K)
         achieved = kbytes / (kms / nl / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": "merge_pieces", "achieved": achieved, "peak": peak, "unit": "GB/s",
+        roof = {"bound": "hbm", "kernel": "merge_round", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
-                "traffic": ncu_traffic("merge_pieces", "m2"), "alg_bytes_per_launch": kbytes,
-                "alg_bytes_per_string": MERGE_BYTES_PER_STRING, "launches": nl, "ms_per_launch": kms / nl,
+                "traffic": ncu_traffic("merge_round", "m2"), "alg_bytes_per_launch": kbytes,
+                "launches": nl, "ms_per_launch": kms / nl,
                 "kernel_share": {k: round(v[1] / sum(x[1] for x in stats.values()), 4) for k, v in stats.items()},
                 "timing": "CUDA events around each launch in a profiled pass of the same steps after the timed region",
                 "profiled_ms_per_step": prof_ms}

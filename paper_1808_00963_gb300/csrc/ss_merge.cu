@@ -280,10 +280,12 @@ __global__ void __launch_bounds__(kMergeBlock) k_merge_round(MergeRoundArgs a) {
         store_mrec(a.dst + base + out, o);
       }
       ++out;
-      if (take_a) {
-        if (++ia < ea) fa = load_mrec(A + ia);
-      } else {
-        if (++jb < eb) fb = load_mrec(B + jb);
+      // the winner's run moves on: one load for every lane, from the run it took
+      if (take_a) ++ia; else ++jb;
+      const bool more = take_a ? ia < ea : jb < eb;
+      if (more) {
+        const MergeRec nx = load_mrec(take_a ? A + ia : B + jb);
+        if (take_a) fa = nx; else fb = nx;
       }
     }
   }
