@@ -720,7 +720,7 @@ def run_sa(args, ws, rank, local):
             "data": "synthetic",
             "config": {"workload": desc, "n": n, "l2": "text 4 MB; suffix array, names and LCPs 16 MB each",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "per_step": "one suffix array + LCP array", "initial_depth": "default (64)"},
+                       "per_step": "one suffix array + LCP array", "initial_depth": "default (256)"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 4)} for k, v in stats.items()},
         }

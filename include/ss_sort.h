@@ -192,7 +192,7 @@ size_t ss_merge_workspace_size(const ss_run* runs, uint32_t num_runs, uint32_t s
 /* Suffix array (and LCP array) of a text, by prefix doubling on top of the
  * string sort (Section 8.2: Observation 8.1, Algorithms 8.1 and 8.3).  Round
  * 0 sorts all suffixes by their first `initial_depth` characters (the string
- * sort with that cap; 0 = 64, at most 2^20); every later round sorts only the
+ * sort with that cap; 0 = 256, at most 2^20); every later round sorts only the
  * suffixes of groups that are still tied, by the name pair of Observation
  * 8.1, doubling the sorted depth, until every group is a single suffix.
  *   text     DEVICE pointer to n bytes in 1..255 followed by a zero byte

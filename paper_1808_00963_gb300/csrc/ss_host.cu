@@ -643,7 +643,7 @@ ss_status ss_suffix_array(const uint8_t* text, uint64_t n, uint32_t* out_sa, uin
   if (n == 0) return SS_OK;
   if (!text || !out_sa) return SS_ERR_INVALID;
   if (initial_depth > (1u << 20)) return SS_ERR_INVALID;
-  const uint32_t h0 = initial_depth ? initial_depth : 64;
+  const uint32_t h0 = initial_depth ? initial_depth : 256;
   DevInfo dev;
   ss_status s = device_info(dev);
   if (s != SS_OK) return s;
