@@ -154,9 +154,9 @@ typedef struct ss_run {
 } ss_run;
 
 /* Merge K sorted runs into one sorted sequence with its LCP array: the
- * multiway LCP-merge of Section 4.3.2 (LCP-Compare, Algorithm 4.2; the
- * LCP-aware tournament tree of Algorithm 4.5), split into independent pieces
- * as in Section 4.3.3.
+ * multiway LCP-merge of Section 4.3.2, done as ceil(log2 K) rounds of binary
+ * LCP merges (LCP-Compare, Algorithm 4.2; Algorithms 4.3 and 4.4), each split
+ * into independent pieces as in Section 4.3.3.
  *   runs       HOST array of num_runs (1..SS_MERGE_MAX_RUNS) run descriptors;
  *              read during the call only.  Every index must be < the number
  *              of strings behind offsets (not checked).  An index may appear
@@ -169,7 +169,7 @@ typedef struct ss_run {
  *   max_len    as ss_options.max_len; it must be the value the runs were
  *              sorted with.  Strings are compared up to 2^30 characters.
  *   sample_step  every sample_step-th string of a run bounds a piece
- *              (16..65536; 0 = chosen from the total).
+ *              (16..65536; 0 = 128).
  *   workspace  device memory of ss_merge_workspace_size() bytes, 256-byte
  *              aligned, or NULL (a stream-ordered allocation is made and
  *              freed on `stream`).
@@ -183,7 +183,8 @@ ss_status ss_merge(const uint8_t* chars, const uint64_t* offsets, uint32_t max_l
                    uint32_t* out_perm, uint32_t* out_lcp,
                    void* workspace, size_t workspace_bytes, void* stream);
 
-/* Workspace bytes ss_merge needs for these runs (at least 256; 0 for invalid
+/* Workspace bytes ss_merge needs for these runs: two 32-byte records per
+ * string, plus the sample counts (256 for a single run; 0 for invalid
  * arguments). */
 size_t ss_merge_workspace_size(const ss_run* runs, uint32_t num_runs, uint32_t sample_step);
 
