@@ -7,8 +7,10 @@ step = one complete sort through the C-ABI (ss_sort_ex), producing the
 permutation and the LCP array.  Prints one JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--config c1|c2|c3|c4|c5|m2|s3]
+                  [--config c1|c2|c3|c4|c5|m2|s3|d3]
 
+--config d3 sorts configuration 3 with alphabet compression (3-bit character
+codes, 21 characters per key).
 --config s3 times suffix array construction (prefix doubling on top of the
 sort) of the 4 M-character DNA-like text of configuration 3, uncapped.
 --config m2 times the K-way LCP merge instead: 16 sorted runs (a seeded
@@ -40,7 +42,7 @@ import numpy as np  # noqa: E402
 import gen  # noqa: E402
 
 METRIC = "strings/s & D-bytes/s vs HBM roofline; batched/served vs plain p99 + throughput"
-KIND = {"c1": "random", "c2": "url", "c3": "dna"}
+KIND = {"c1": "random", "c2": "url", "c3": "dna", "d3": "dna"}
 CPU_SAMPLE = 2_000_000
 
 
@@ -162,6 +164,9 @@ def workload(name: str, n: int | None = None):
         return gen.config2(), "plain sort, 20M URL-like strings (~59 B mean, Zipf(1.1) over 2000 hosts)"
     if name == "c3":
         return gen.config3(), "plain sort, all 4M suffixes of a DNA-like text, capped at 500 B"
+    if name == "d3":
+        return gen.config3(), ("plain sort, all 4M suffixes of a DNA-like text, capped at 500 B, with alphabet "
+                               "compression (3-bit character codes, 21 characters per key)")
     raise ValueError(name)
 
 
@@ -363,8 +368,10 @@ def run_ours(args, ws, rank, local):
     opts = dict(workspace=work.data_ptr(), workspace_bytes=wsb, **tuned)
     stream = torch.cuda.current_stream()
 
+    dna = args.config == "d3"
+
     def step():
-        ss.sort(chars, offsets, max_len=s.max_len, out=(perm, lcp), **opts)
+        ss.sort(chars, offsets, max_len=s.max_len, out=(perm, lcp), dna=dna, **opts)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -417,12 +424,24 @@ def run_ours(args, ws, rank, local):
         hoffs = torch.from_numpy(s.offsets.view(np.int64)).pin_memory()
         hperm = torch.empty(n, dtype=torch.int32).pin_memory()
         hlcp = torch.empty(n, dtype=torch.int32).pin_memory()
-        ss.sort_host(hchars, hoffs, s.max_len, perm=hperm, lcp=hlcp, **tuned)
+
+        def e2e_step():
+            if not dna:  # through the host-buffer entry point
+                ss.sort_host(hchars, hoffs, s.max_len, perm=hperm, lcp=hlcp, **tuned)
+                return
+            dc = hchars.to(dev, non_blocking=True)
+            do = hoffs.to(dev, non_blocking=True)
+            ss.sort(dc, do, max_len=s.max_len, out=(perm, lcp), dna=True, **opts)
+            hperm.copy_(perm, non_blocking=True)
+            hlcp.copy_(lcp, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        e2e_step()
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            ss.sort_host(hchars, hoffs, s.max_len, perm=hperm, lcp=hlcp, **tuned)
+            e2e_step()
         torch.cuda.synchronize()
         et = max_over_ranks(time.perf_counter() - t0, ws)
         e2e = {"value": ws * n * args.steps / et, "unit": "strings/s",
@@ -877,7 +896,7 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "m2", "s3"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "m2", "s3", "d3"])
     ap.add_argument("--requests", type=int, default=150, help="number of requests (c5)")
     ap.add_argument("--sets", type=int, default=4096, help="number of sets (c4)")
     ap.add_argument("--no-e2e", action="store_true")

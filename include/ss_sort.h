@@ -120,6 +120,18 @@ ss_status ss_sort_host(const uint8_t* chars, uint64_t chars_len, const uint64_t*
                        uint64_t n, uint32_t* out_perm, uint32_t* out_lcp,
                        const ss_options* opt, void* stream);
 
+/* ss_sort_ex for strings over the DNA alphabet, with alphabet compression
+ * (Section 4.4, "Alphabet compression"): chars[0, chars_len) (DEVICE) holds
+ * only the bytes 'A', 'C', 'G', 'T' and the zero terminator; it is packed
+ * into 3-bit codes (terminator, A, C, G, T), so that each key of the sort
+ * holds 21 characters instead of 8.  Same output as ss_sort_ex on the same
+ * strings (A < C < G < T as bytes).  A device copy of 3 bits per byte of
+ * chars is allocated from the stream-ordered pool for the call.  Returns
+ * SS_ERR_INVALID (after the call has run; the outputs are then undefined) if
+ * another byte occurs in chars[0, chars_len); otherwise as ss_sort_ex. */
+ss_status ss_sort_dna(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets, uint64_t n,
+                      uint32_t* out_perm, uint32_t* out_lcp, const ss_options* opt, void* stream);
+
 /* Distinguishing characters and prefixes of a sorted set (the outputs of
  * ss_sort on the same strings and max_len).  For each sorted position j,
  * with h_j = lcp[j] (h_0 = 0) and h_n = 0:

@@ -177,6 +177,8 @@ def load(path: str | None = None):
     lib.ss_merge.restype = i32
     lib.ss_merge_workspace_size.argtypes = [ctypes.POINTER(RunDesc), u32, u32]
     lib.ss_merge_workspace_size.restype = ctypes.c_size_t
+    lib.ss_sort_dna.argtypes = [vp, u64, vp, u64, vp, vp, ctypes.POINTER(Options), vp]
+    lib.ss_sort_dna.restype = i32
     lib.ss_suffix_array.argtypes = [vp, u64, vp, vp, u32, vp]
     lib.ss_suffix_array.restype = i32
     if path is None:
@@ -204,11 +206,14 @@ def _check(code, what):
         raise SortError(code, what)
 
 
-def sort(chars, offsets, max_len: int = 0, with_lcp: bool = True, out=None, stream=None, **opts):
+def sort(chars, offsets, max_len: int = 0, with_lcp: bool = True, out=None, stream=None, dna: bool = False,
+         **opts):
     """Sort the strings of a device string set.
 
     chars   : torch.uint8 CUDA tensor (NUL-terminated strings)
     offsets : torch.int64 CUDA tensor (start of each string)
+    dna     : the bytes of chars are only A, C, G, T and terminators: sort
+              with 3-bit character codes, 21 characters per key
     Returns (perm, lcp) as torch.int32 CUDA tensors holding uint32 values
     (lcp is None when with_lcp is False).  Runs on the current stream (or
     ``stream``) and returns when the sort has finished.
@@ -225,11 +230,16 @@ def sort(chars, offsets, max_len: int = 0, with_lcp: bool = True, out=None, stre
     assert chars.dtype == torch.uint8 and chars.is_cuda and chars.is_contiguous()
     assert offsets.dtype == torch.int64 and offsets.is_cuda and offsets.is_contiguous()
     o = make_options(max_len, **opts)
-    rc = lib.ss_sort_ex(ctypes.c_void_p(chars.data_ptr()), ctypes.c_void_p(offsets.data_ptr()), n,
-                        ctypes.c_void_p(perm.data_ptr()),
-                        ctypes.c_void_p(lcp.data_ptr()) if lcp is not None else None,
-                        ctypes.byref(o), _stream_ptr(stream))
-    _check(rc, "ss_sort_ex")
+    lp = ctypes.c_void_p(lcp.data_ptr()) if lcp is not None else None
+    if dna:
+        rc = lib.ss_sort_dna(ctypes.c_void_p(chars.data_ptr()), int(chars.numel()),
+                             ctypes.c_void_p(offsets.data_ptr()), n, ctypes.c_void_p(perm.data_ptr()), lp,
+                             ctypes.byref(o), _stream_ptr(stream))
+        _check(rc, "ss_sort_dna")
+    else:
+        rc = lib.ss_sort_ex(ctypes.c_void_p(chars.data_ptr()), ctypes.c_void_p(offsets.data_ptr()), n,
+                            ctypes.c_void_p(perm.data_ptr()), lp, ctypes.byref(o), _stream_ptr(stream))
+        _check(rc, "ss_sort_ex")
     return perm, lcp
 
 

@@ -41,7 +41,8 @@ __global__ void __launch_bounds__(kBlock) k_big_sample(SortCtx c, const GenTask*
   __shared__ __align__(16) BuildScratch<LOGV> bs;
   const GenTask g = gt[blockIdx.x];
   const Rec* recs = c.rec[task_par(g.t)] + g.t.begin;
-  build_splitters<LOGV>(recs, g.t.len, mix64(c.seed ^ ((uint64_t)g.t.begin << 20) ^ g.t.depth), sp, bs);
+  build_splitters<LOGV>(recs, g.t.len, mix64(c.seed ^ ((uint64_t)g.t.begin << 20) ^ g.t.depth), sp, bs,
+                        c.sets[task_set(g.t)].dna);
   const uint64_t* src = reinterpret_cast<const uint64_t*>(&sp);
   uint64_t* dst = reinterpret_cast<uint64_t*>(&out[blockIdx.x].sp);
   for (uint32_t i = threadIdx.x; i < sizeof(Splitters<LOGV>) / 8; i += blockDim.x) dst[i] = src[i];
@@ -114,7 +115,7 @@ __global__ void __launch_bounds__(kBlock) k_big_emit(SortCtx c, const GenTask* _
     gstart[(uint64_t)blockIdx.x * Gm::KP + b] = s;
     uint32_t desc = kFin;
     if (size) {
-      desc = bucket_desc<LOGV>(b, size, g.t.depth, sp);
+      desc = bucket_desc<LOGV>(b, size, g.t.depth, sp, sd.dna);
       emit_bucket(c, sd, g.t, s, size, desc, next_big);
     }
     gdesc[(uint64_t)blockIdx.x * Gm::KP + b] = desc;

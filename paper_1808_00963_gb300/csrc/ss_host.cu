@@ -390,7 +390,7 @@ static ss_status read_status(uint8_t* ws, const Layout& L, cudaStream_t st) {
 }
 
 static ss_status sort_device(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t* perm,
-                             uint32_t* lcp, const ss_options* opt, cudaStream_t st) {
+                             uint32_t* lcp, const ss_options* opt, cudaStream_t st, uint32_t dna = 0) {
   Opts o;
   ss_status s = resolve_opts(opt, o);
   if (s != SS_OK) return s;
@@ -411,7 +411,7 @@ static ss_status sort_device(const uint8_t* chars, const uint64_t* offsets, uint
       if (cudaMallocAsync(reinterpret_cast<void**>(&ws), L.total, st) != cudaSuccess) return SS_ERR_OOM;
       owned = true;
     }
-    SetDesc sd{chars, offsets, perm, lcp, (uint32_t)n, o.cap, 0, 0};
+    SetDesc sd{chars, offsets, perm, lcp, (uint32_t)n, o.cap, 0, dna};
     ss_status r = SS_OK;
     if (t_up.reserve(sizeof(SetDesc)) != SS_OK) r = SS_ERR_OOM;
     if (r == SS_OK) {
@@ -421,7 +421,9 @@ static ss_status sort_device(const uint8_t* chars, const uint64_t* offsets, uint
           cudaStreamSynchronize(st) != cudaSuccess)
         r = SS_ERR_CUDA;
     }
-    if (r == SS_OK) r = run_sort(ws, L, make_ctx(ws, L, 1, (uint32_t)n, o, big), o, dev, big, st);
+    SortCtx ctx = make_ctx(ws, L, 1, (uint32_t)n, o, big);
+    ctx.dna = dna;
+    if (r == SS_OK) r = run_sort(ws, L, ctx, o, dev, big, st);
     ss_status r2 = read_status(ws, L, st);
     if (r == SS_OK) r = r2;
     if (owned) {
@@ -781,6 +783,42 @@ ss_status ss_sort_ex(const uint8_t* chars, const uint64_t* offsets, uint64_t n, 
 ss_status ss_sort(const uint8_t* chars, const uint64_t* offsets, uint64_t n, uint32_t* out_perm,
                   uint32_t* out_lcp, void* stream) {
   return ss_sort_ex(chars, offsets, n, out_perm, out_lcp, nullptr, stream);
+}
+
+ss_status ss_sort_dna(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets, uint64_t n,
+                      uint32_t* out_perm, uint32_t* out_lcp, const ss_options* opt, void* stream) {
+  if (n >= 0xFFFFFFFFull) return SS_ERR_TOO_LARGE;
+  if (n == 0) return SS_OK;
+  if (!chars || !offsets || !out_perm || chars_len == 0) return SS_ERR_INVALID;
+  if (chars_len >= (1ull << 60)) return SS_ERR_TOO_LARGE;
+  Opts o;
+  ss_status s = resolve_opts(opt, o);
+  if (s != SS_OK) return s;
+  DevInfo dev;
+  if ((s = device_info(dev)) != SS_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // packed codes, four zero words of padding (a key reads the word after its
+  // own), then the invalid-byte flag
+  const uint64_t words = (3 * chars_len + 63) / 64 + 4;
+  const size_t flag_at = align256(words * 8);
+  uint8_t* d = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&d), flag_at + 256, st) != cudaSuccess) return SS_ERR_OOM;
+  uint32_t* bad = reinterpret_cast<uint32_t*>(d + flag_at);
+  const LaunchHook hook{st};
+  const uint32_t grid = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>((words + kBlock - 1) / kBlock,
+                                                                           (uint64_t)dev.sms * 16));
+  ss_status r = SS_OK;
+  if (cudaMemsetAsync(bad, 0, 4, st) != cudaSuccess ||
+      launch_pack_dna(chars, chars_len, reinterpret_cast<uint64_t*>(d), words, bad, grid, st, hook) != cudaSuccess)
+    r = SS_ERR_CUDA;
+  if (r == SS_OK) r = sort_device(d, offsets, n, out_perm, out_lcp, opt, st, 1);
+  uint32_t hbad = 0;
+  if (cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    if (r == SS_OK) r = SS_ERR_CUDA;
+  cudaFreeAsync(d, st);
+  if (r == SS_OK && hbad) r = SS_ERR_INVALID;
+  return r;
 }
 
 ss_status ss_sort_host(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets, uint64_t n,

@@ -35,7 +35,7 @@ struct SetDesc {
   uint32_t n;
   uint32_t cap;      // kNoCap or max_len
   uint32_t base;     // first record position of this set
-  uint32_t pad;
+  uint32_t dna;      // 1: chars holds 3-bit character codes (see dna_key), not bytes
 };
 
 // One string being sorted (moved with one 16-byte load and store).
@@ -120,6 +120,7 @@ struct SortCtx {
   uint32_t seed;
   uint32_t classifier;     // classification variant (kClassifyUI / UIC / E)
   uint32_t big_cur;        // which big[] list the current step reads
+  uint32_t dna;            // every set holds 3-bit character codes (SetDesc::dna)
 };
 
 // ---------------------------------------------------------------------------
@@ -274,6 +275,84 @@ __device__ __forceinline__ bool has_nul(uint64_t c) { return (c & 0xFFu) == 0; }
 // Characters before the terminator inside a cache that holds one.
 __device__ __forceinline__ uint32_t nnz_prefix(uint64_t c) {
   return c ? 8u - ((uint32_t)(__ffsll((long long)c) - 1) >> 3) : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Alphabet compression for DNA (Section 4.4, "Alphabet compression"): each
+// character is a 3-bit code (0 = end of string, 1..4 = A, C, G, T), packed
+// most significant first into 64-bit words, so that a key holds 21
+// characters (bits 63..1) instead of 8, still compares as an integer in
+// string order, and still ends in a zero code when it holds the end.  Code 0
+// keeps the terminator: with 2 bits per character a string that ends inside
+// a word could not be told from one that continues with A.
+
+constexpr uint32_t kDnaWidth = 21;                       // characters per key
+constexpr uint64_t kDnaDigitLow = 0x2492492492492492ull;  // lowest bit of each code: bits 61, 58, ..., 1
+
+// The 21 characters of the string at character offset `off` from depth h of
+// a packed code buffer (padded with zero words past its end), with every code
+// at or after the end (or the cap) zero.  Precondition as load_cache: the
+// string does not end before h.
+__device__ __forceinline__ uint64_t dna_key(const uint8_t* packed, uint64_t off, uint32_t h, uint32_t cap) {
+  if (h >= cap) return 0;
+  const uint64_t* p = reinterpret_cast<const uint64_t*>(packed);
+  const uint64_t bit = 3 * (off + h);
+  const uint64_t wi = bit >> 6;
+  const uint32_t r = (uint32_t)(bit & 63);
+  uint64_t x = __ldg(p + wi) << r;
+  if (r) x |= __ldg(p + wi + 1) >> (64 - r);
+  x &= ~1ull;
+  const uint64_t y = x | (x >> 1) | (x >> 2);
+  const uint64_t zeros = ~y & kDnaDigitLow;  // lowest bit of every zero code
+  const uint32_t first_end = zeros ? (61u - (63u - (uint32_t)__clzll((long long)zeros))) / 3u : kDnaWidth;
+  const uint32_t room = cap - h;
+  const uint32_t keep = first_end < room ? first_end : room;
+  if (keep < kDnaWidth) x &= keep ? (~0ull << (64 - 3 * keep)) : 0ull;
+  return x;
+}
+
+// Key operations for both character encodings (dna = 0: bytes, 8 per key).
+__device__ __forceinline__ uint32_t key_width(uint32_t dna) { return dna ? kDnaWidth : 8u; }
+
+// Characters two keys at the same depth have in common (the whole key if equal).
+__device__ __forceinline__ uint32_t key_lcp(uint64_t a, uint64_t b, uint32_t dna) {
+  if (!dna) return lcp8(a, b);
+  const uint64_t x = a ^ b;
+  return x ? (uint32_t)__clzll((long long)x) / 3u : kDnaWidth;
+}
+
+// True if the key holds the end of its string.
+__device__ __forceinline__ bool key_end(uint64_t c, uint32_t dna) {
+  return dna ? (c & 0xEull) == 0 : (c & 0xFFull) == 0;
+}
+
+// Characters before the end inside a key that holds it.
+__device__ __forceinline__ uint32_t key_nnz(uint64_t c, uint32_t dna) {
+  if (!dna) return nnz_prefix(c);
+  const uint64_t y = c | (c >> 1) | (c >> 2);
+  const uint64_t zeros = ~y & kDnaDigitLow;
+  return zeros ? (61u - (63u - (uint32_t)__clzll((long long)zeros))) / 3u : kDnaWidth;
+}
+
+__device__ __forceinline__ uint64_t load_key(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
+                                             uint32_t dna) {
+  return dna ? dna_key(chars, off, h, cap) : load_cache(chars, off, h, cap);
+}
+
+// The KW keys at depths h, h + w, ..., h + (KW - 1) w (w = key_width) and how
+// many of them are determined (all of them for the packed codes, whose buffer
+// is padded; see load_windows for bytes).
+template <int KW>
+__device__ __forceinline__ uint32_t load_key_windows(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
+                                                     uint32_t dna, uint64_t (&w)[KW]) {
+  if (!dna) return load_windows<KW>(chars, off, h, cap, w);
+  bool ended = false;
+#pragma unroll
+  for (int j = 0; j < KW; ++j) {
+    w[j] = ended ? 0ull : dna_key(chars, off, h + kDnaWidth * (uint32_t)j, cap);
+    ended = ended || key_end(w[j], 1);
+  }
+  return KW;
 }
 
 // Counter-based hash for sample positions (SplitMix64 finaliser).

@@ -50,6 +50,9 @@ cudaError_t launch_init(const SortCtx& c, cudaStream_t st, const LaunchHook& hoo
 cudaError_t launch_small(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, uint32_t grid_cta,
                          cudaStream_t st, const LaunchHook& hook);
 cudaError_t launch_lcp_fix(const SortCtx& c, uint32_t grid, cudaStream_t st, const LaunchHook& hook);
+// Packs bytes over {A, C, G, T, 0} into 3-bit codes (dna_key's layout).
+cudaError_t launch_pack_dna(const uint8_t* chars, uint64_t len, uint64_t* out, uint64_t words, uint32_t* bad,
+                            uint32_t grid, cudaStream_t st, const LaunchHook& hook);
 cudaError_t launch_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t cap,
                                   const uint32_t* perm, const uint32_t* lcp, uint8_t* dchar, uint32_t* dprefix,
                                   unsigned long long* sum_d, uint32_t grid, cudaStream_t st, const LaunchHook& hook);

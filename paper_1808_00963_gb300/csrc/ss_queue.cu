@@ -107,7 +107,7 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
   const uint32_t par = task_par(t);
   const Rec* recs = c.rec[par] + t.begin;
   const uint32_t wide = c.wide[task_set(t)];
-  build_splitters<LOGV>(recs, t.len, mix64(c.seed ^ ((uint64_t)t.begin << 20) ^ t.depth), s.sp, s.u.bs);
+  build_splitters<LOGV>(recs, t.len, mix64(c.seed ^ ((uint64_t)t.begin << 20) ^ t.depth), s.sp, s.u.bs, sd.dna);
   unsigned long long bytes = threadIdx.x == 0 ? Gm::S * 8ull : 0ull;
 
   // classification (Algorithm 4.1): classify into the array o and count
@@ -121,7 +121,7 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
   block_excl_scan_smem(s.hist, s.bstart, Gm::KP);  // bstart[K] = len (hist[K] is 0)
   for (uint32_t b = threadIdx.x; b < Gm::K; b += kBlock) {
     const uint32_t size = s.hist[b];
-    s.desc[b] = size ? bucket_desc<LOGV>(b, size, t.depth, s.sp) : kFin;
+    s.desc[b] = size ? bucket_desc<LOGV>(b, size, t.depth, s.sp, sd.dna) : kFin;
     s.hist[b] = t.begin + s.bstart[b];
   }
   __syncthreads();

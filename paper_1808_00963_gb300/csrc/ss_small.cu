@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kBlock) k_init(SortCtx c) {
     const uint32_t i = r - sd.base;
     const uint64_t off = sd.offsets[i];
     if ((off >> 32) && !c.wide[s]) atomicOr(c.wide + s, 1u);
-    store_rec(c.rec[0] + r, load_cache(sd.chars, off, 0, sd.cap), i, (uint32_t)off);
+    store_rec(c.rec[0] + r, load_key(sd.chars, off, 0, sd.cap, sd.dna), i, (uint32_t)off);
     bytes += 32;  // offset 8 + 8 characters read, record 16 written
   }
   account(c, kKInit, bytes);
@@ -97,7 +97,7 @@ __device__ __forceinline__ void warp_sort(uint32_t& seg, uint64_t& key, uint32_t
 // a 64-character look-ahead, and is sorted again.  Writes lcp_g[j] for every
 // position j > 0 of each group and returns the index at the lane's position.
 __device__ uint32_t warp_refine(bool active, uint32_t g0, uint32_t nact, uint64_t key, uint32_t idx,
-                                uint64_t off, uint32_t depth, uint32_t cap, const uint8_t* chars,
+                                uint64_t off, uint32_t depth, uint32_t cap, const uint8_t* chars, uint32_t dna,
                                 uint32_t* lcp_g, uint32_t* status, unsigned long long& bytes) {
   const uint32_t lane = lane_id();
   uint32_t seg = active ? g0 : 0xFFFFFFFFu;
@@ -117,7 +117,7 @@ __device__ uint32_t warp_refine(bool active, uint32_t g0, uint32_t nact, uint64_
     const uint32_t ps = __shfl_up_sync(kFull, seg, 1);
     const uint64_t pk = __shfl_up_sync(kFull, key, 1);
     const bool start = lane == 0 || seg != ps || key != pk;
-    if (active && open && lane > g0 && seg == ps && key != pk && lcp_g) lcp_g[lane - g0] = depth + lcp8(pk, key);
+    if (active && open && lane > g0 && seg == ps && key != pk && lcp_g) lcp_g[lane - g0] = depth + key_lcp(pk, key, dna);
     const uint32_t starts = __ballot_sync(kFull, active && start);
     const uint32_t my_start = 31 - __clz(starts & upto);
     const uint32_t above = starts & ~upto;
@@ -125,9 +125,9 @@ __device__ uint32_t warp_refine(bool active, uint32_t g0, uint32_t nact, uint64_
     if (active && open) {
       if (next - my_start == 1) {
         open = 0;
-      } else if (has_nul(key)) {
+      } else if (key_end(key, dna)) {
         open = 0;
-        if (lane != my_start && lcp_g) lcp_g[lane - g0] = depth + nnz_prefix(key);
+        if (lane != my_start && lcp_g) lcp_g[lane - g0] = depth + key_nnz(key, dna);
       }
     }
     if (active) seg = my_start;
@@ -136,19 +136,20 @@ __device__ uint32_t warp_refine(bool active, uint32_t g0, uint32_t nact, uint64_
     // members of the run differ or end; the run continues there
     uint64_t w[kLookWindows];
     uint32_t nwin = 0;
-    if (active && open) nwin = load_windows<kLookWindows>(chars, off, depth + 8, cap, w);
+    const uint32_t kw = key_width(dna);
+    if (active && open) nwin = load_key_windows<kLookWindows>(chars, off, depth + kw, cap, dna, w);
     const uint32_t segmask = (next >= 32 ? kFull : ((1u << next) - 1)) & ~((1u << my_start) - 1);
     uint32_t jstop = kLookWindows - 1;
     bool found = false;
 #pragma unroll
     for (int j = 0; j < kLookWindows; ++j) {
       const uint64_t lw = __shfl_sync(kFull, w[j], my_start);
-      const bool stop = active && open && ((uint32_t)j >= nwin || w[j] != lw || has_nul(w[j]));
+      const bool stop = active && open && ((uint32_t)j >= nwin || w[j] != lw || key_end(w[j], dna));
       const uint32_t b = __ballot_sync(kFull, stop) & segmask;
       if (!found && b) { jstop = (uint32_t)j; found = true; }
     }
     if (active && open) {
-      const uint32_t nd = depth + 8 * (jstop + 1);
+      const uint32_t nd = depth + kw * (jstop + 1);
       if (nd > kMaxDepth) {
         latch_status(status, kStTooDeep);
         open = 0;
@@ -156,7 +157,7 @@ __device__ uint32_t warp_refine(bool active, uint32_t g0, uint32_t nact, uint64_
         uint64_t k = w[0];
 #pragma unroll
         for (int j = 1; j < kLookWindows; ++j) if ((uint32_t)j == jstop) k = w[j];
-        key = jstop < nwin ? k : load_cache(chars, off, nd, cap);
+        key = jstop < nwin ? k : load_key(chars, off, nd, cap, dna);
         depth = nd;
         bytes += 8ull * (jstop + 1);
       }
@@ -215,7 +216,7 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
       const uint32_t tdepth = __shfl_sync(kFull, mt.depth, k & 31);
       const uint32_t tmeta = __shfl_sync(kFull, mt.meta, k & 31);
       uint64_t key = 0, off = 0;
-      uint32_t id = 0, cap = kNoCap;
+      uint32_t id = 0, cap = kNoCap, dna = 0;
       const uint8_t* chars = nullptr;
       uint32_t* lcp_g = nullptr;
       uint32_t* perm = nullptr;
@@ -229,10 +230,11 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
         off = rec_offset(sd, c.wide[tmeta & 0x7FFFFFFFu], r.idx, r.off);
         cap = sd.cap;
         chars = sd.chars;
+        dna = sd.dna;
         lcp_g = sd.lcp ? sd.lcp + (tb - sd.base) : nullptr;
         perm = sd.perm + (tb - sd.base);
       }
-      const uint32_t fin = warp_refine(active, g0, nact, key, id, off, tdepth, cap, chars, lcp_g, c.status,
+      const uint32_t fin = warp_refine(active, g0, nact, key, id, off, tdepth, cap, chars, dna, lcp_g, c.status,
                                        bytes);
       if (active) {
         perm[lane - g0] = fin;
@@ -390,9 +392,10 @@ __device__ void block_max_scan(uint16_t* a, uint32_t n) {
 // Subsets with lo < len <= hi; while there are fewer than min_count subsets
 // in all, the narrow kernel (narrow = 1) leaves every subset to the wide one
 // (narrow = 0), which then takes all sizes.
-template <uint32_t NT>
+template <uint32_t NT, bool DNA>
 __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint32_t lo, uint32_t hi,
                                                   uint32_t min_count, uint32_t narrow) {
+  constexpr uint32_t dna = DNA ? 1u : 0u;  // the character encoding, fixed per instance
   extern __shared__ __align__(16) uint8_t smem[];
   CtaSmem m;
   m.key = reinterpret_cast<uint64_t*>(smem);
@@ -415,6 +418,7 @@ __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint
     const Task t = c.small_cta.items[ti];
     if (t.len <= lo || t.len > hi) continue;  // another block size takes this subset
     const SetDesc sd = c.sets[task_set(t)];
+    const uint32_t kw = key_width(dna);  // characters per key
     const uint32_t par = task_par(t);
     const uint32_t n = t.len;
     const uint32_t wide = c.wide[task_set(t)];
@@ -440,21 +444,21 @@ __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint
       for (uint32_t j = threadIdx.x; j < n; j += NT)
         if (m.key[j] != k0) s_neq = 1;
       __syncthreads();
-      if (s_neq || has_nul(k0) || depth + 8 * kLookWindows > kMaxDepth) break;
+      if (s_neq || key_end(k0, dna) || depth + kw * kLookWindows > kMaxDepth) break;
       if (threadIdx.x == 0) {
         uint64_t w[kLookWindows];
-        const uint32_t nwin = load_windows<kLookWindows>(sd.chars, m.off[0], depth + 8, sd.cap, w);
+        const uint32_t nwin = load_key_windows<kLookWindows>(sd.chars, m.off[0], depth + kw, sd.cap, dna, w);
         uint32_t js = kLookWindows - 1;
         for (int j = kLookWindows - 1; j >= 0; --j) {
           s_lead[j] = w[j];
-          if ((uint32_t)j >= nwin || has_nul(w[j])) js = (uint32_t)j;
+          if ((uint32_t)j >= nwin || key_end(w[j], dna)) js = (uint32_t)j;
         }
         s_jstop = js;
       }
       __syncthreads();
       for (uint32_t j = threadIdx.x + 1; j < n; j += NT) {
         uint64_t w[kLookWindows];
-        const uint32_t nwin = load_windows<kLookWindows>(sd.chars, m.off[j], depth + 8, sd.cap, w);
+        const uint32_t nwin = load_key_windows<kLookWindows>(sd.chars, m.off[j], depth + kw, sd.cap, dna, w);
         uint32_t js = kLookWindows;
 #pragma unroll
         for (int q = kLookWindows - 1; q >= 0; --q)
@@ -462,9 +466,9 @@ __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint
         if (js < kLookWindows) atomicMin(&s_jstop, js);
       }
       __syncthreads();
-      const uint32_t nd = depth + 8 * (s_jstop + 1);
+      const uint32_t nd = depth + kw * (s_jstop + 1);
       for (uint32_t j = threadIdx.x; j < n; j += NT) {
-        m.key[j] = load_cache(sd.chars, m.off[j], nd, sd.cap);
+        m.key[j] = load_key(sd.chars, m.off[j], nd, sd.cap, dna);
         bytes += 8ull * (s_jstop + 1);
       }
       depth = nd;
@@ -478,7 +482,7 @@ __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint
         const uint32_t tg = m.tag[j];
         const bool st = j == 0 || tag_seg(tg) != tag_seg(m.tag[j - 1]) || m.key[j] != m.key[j - 1];
         if (lcp && (tg & 1u) && j > 0 && tag_seg(tg) == tag_seg(m.tag[j - 1]) && m.key[j] != m.key[j - 1])
-          lcp[j] = depth + lcp8(m.key[j - 1], m.key[j]);
+          lcp[j] = depth + key_lcp(m.key[j - 1], m.key[j], dna);
         m.nseg[j] = st ? (uint16_t)j : 0;
         m.aux[j] = 0;
       }
@@ -497,9 +501,9 @@ __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint
           const uint32_t size = m.aux[s0];
           if (size == 1) {
             open = 0;
-          } else if (has_nul(m.key[j])) {
+          } else if (key_end(m.key[j], dna)) {
             open = 0;
-            if (lcp && j != s0) lcp[j] = depth + nnz_prefix(m.key[j]);
+            if (lcp && j != s0) lcp[j] = depth + key_nnz(m.key[j], dna);
           } else if (size <= 32) {
             open = 0;
             handed = kHanded;
@@ -514,14 +518,14 @@ __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint
       }
       __syncthreads();
       if (s_max_open == 0) break;
-      if (depth + 8 > kMaxDepth) {
+      if (depth + kw > kMaxDepth) {
         if (threadIdx.x == 0) latch_status(c.status, kStTooDeep);
         break;
       }
-      depth += 8;
+      depth += kw;
       for (uint32_t j = threadIdx.x; j < n; j += NT)
         if (m.tag[j] & 1u) {
-          m.key[j] = load_cache(sd.chars, m.off[tag_pos(m.tag[j])], depth, sd.cap);
+          m.key[j] = load_key(sd.chars, m.off[tag_pos(m.tag[j])], depth, sd.cap, dna);
           bytes += 8;
         }
       __syncthreads();
@@ -551,9 +555,9 @@ __global__ void __launch_bounds__(kBlock) k_lcp_fix(SortCtx c) {
     bytes += 4;
     if (j == 0 || !(v & kLcpMark)) continue;
     const uint32_t h = v & ~kLcpMark;
-    const uint64_t a = load_cache(sd.chars, sd.offsets[sd.perm[j - 1]], h, sd.cap);
-    const uint64_t b = load_cache(sd.chars, sd.offsets[sd.perm[j]], h, sd.cap);
-    sd.lcp[j] = h + lcp8(a, b);
+    const uint64_t a = load_key(sd.chars, sd.offsets[sd.perm[j - 1]], h, sd.cap, sd.dna);
+    const uint64_t b = load_key(sd.chars, sd.offsets[sd.perm[j]], h, sd.cap, sd.dna);
+    sd.lcp[j] = h + key_lcp(a, b, sd.dna);
     bytes += 44;  // lcp 4 written; per string: perm 4 + offset 8 + 8 characters read
   }
   account(c, kKLcpFix, bytes);
@@ -590,6 +594,31 @@ __global__ void __launch_bounds__(kBlock) k_distinguishing(const uint8_t* __rest
 
 }  // namespace
 
+// Packs a byte buffer over {A, C, G, T, terminator} into 3-bit codes (0 =
+// terminator, 1..4 = A, C, G, T), most significant first, character p at
+// bits [3p, 3p + 3) of the word stream; sets *bad if another byte occurs.
+__global__ void k_pack_dna(const uint8_t* __restrict__ chars, uint64_t len, uint64_t* __restrict__ out,
+                           uint64_t words, uint32_t* bad) {
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+       w += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t g0 = 64 * w;
+    uint64_t v = 0;
+    bool invalid = false;
+    for (uint64_t p = g0 / 3; p <= (g0 + 63) / 3; ++p) {
+      uint64_t code = 0;
+      if (p < len) {
+        const uint8_t ch = chars[p];
+        code = ch == 'A' ? 1 : ch == 'C' ? 2 : ch == 'G' ? 3 : ch == 'T' ? 4 : 0;
+        invalid = invalid || (ch != 0 && code == 0);
+      }
+      const int64_t s = (int64_t)(3 * p) - (int64_t)g0;  // first bit of the code, from the word's top
+      v |= s <= 61 ? code << (61 - s) : code >> (s - 61);
+    }
+    out[w] = v;
+    if (invalid) atomicOr(bad, 1u);
+  }
+}
+
 constexpr uint32_t kSmallCtaNarrowMax = 256;
 
 size_t small_cta_smem(uint32_t pmax) { return (size_t)pmax * (8 + 8 + 8 + 4 + 4 + 4 + 4 + 2); }
@@ -601,11 +630,12 @@ cudaError_t launch_init(const SortCtx& c, cudaStream_t st, const LaunchHook& hoo
   return cudaGetLastError();
 }
 
-cudaError_t launch_small(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, uint32_t grid_cta,
-                         cudaStream_t st, const LaunchHook& hook) {
+template <bool DNA>
+static cudaError_t launch_small_t(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, uint32_t grid_cta,
+                                  cudaStream_t st, const LaunchHook& hook) {
   static uint32_t attr_pmax = 0;
   if (pmax > attr_pmax) {
-    cudaError_t e = cudaFuncSetAttribute(k_small_cta<kBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_small_cta<kBlock, DNA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)small_cta_smem(pmax));
     if (e != cudaSuccess) return e;
     attr_pmax = pmax;
@@ -617,19 +647,31 @@ cudaError_t launch_small(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, ui
   const uint32_t min_count = 2 * grid_cta;
   if (pmax <= kSmallCtaNarrowMax) {
     hook.run("small_cta", [&] {
-      k_small_cta<64><<<grid_cta * 4, 64, small_cta_smem(pmax), st>>>(c, pmax, 0u, pmax, 0u, 1u);
+      k_small_cta<64, DNA><<<grid_cta * 4, 64, small_cta_smem(pmax), st>>>(c, pmax, 0u, pmax, 0u, 1u);
     });
   } else {
     hook.run("small_cta", [&] {
-      k_small_cta<64><<<grid_cta * 4, 64, small_cta_smem(kSmallCtaNarrowMax), st>>>(
+      k_small_cta<64, DNA><<<grid_cta * 4, 64, small_cta_smem(kSmallCtaNarrowMax), st>>>(
           c, kSmallCtaNarrowMax, 0u, kSmallCtaNarrowMax, min_count, 1u);
     });
     hook.run("small_cta", [&] {
-      k_small_cta<kBlock><<<grid_cta, kBlock, small_cta_smem(pmax), st>>>(c, pmax, kSmallCtaNarrowMax, 0xFFFFFFFFu,
-                                                                         min_count, 0u);
+      k_small_cta<kBlock, DNA><<<grid_cta, kBlock, small_cta_smem(pmax), st>>>(
+          c, pmax, kSmallCtaNarrowMax, 0xFFFFFFFFu, min_count, 0u);
     });
   }
   hook.run("small_warp", [&] { k_small_warp<<<grid_warp, kBlock, 0, st>>>(c); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_small(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, uint32_t grid_cta,
+                         cudaStream_t st, const LaunchHook& hook) {
+  return c.dna ? launch_small_t<true>(c, pmax, grid_warp, grid_cta, st, hook)
+               : launch_small_t<false>(c, pmax, grid_warp, grid_cta, st, hook);
+}
+
+cudaError_t launch_pack_dna(const uint8_t* chars, uint64_t len, uint64_t* out, uint64_t words, uint32_t* bad,
+                            uint32_t grid, cudaStream_t st, const LaunchHook& hook) {
+  hook.run("init", [&] { k_pack_dna<<<grid, kBlock, 0, st>>>(chars, len, out, words, bad); });
   return cudaGetLastError();
 }
 

@@ -96,7 +96,7 @@ __device__ __forceinline__ void warp_bitonic_u64(uint64_t (&v)[E]) {
 // no step-by-step synchronisation.  Ends with __syncthreads().
 template <int LOGV>
 __device__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint64_t hseed,
-                                Splitters<LOGV>& sp, BuildScratch<LOGV>& bs) {
+                                Splitters<LOGV>& sp, BuildScratch<LOGV>& bs, uint32_t dna) {
   using G = Geo<LOGV>;
   constexpr uint32_t C = G::S / kWarps;  // keys per warp
   constexpr int E = (int)(C / 32);       // keys per lane
@@ -172,7 +172,7 @@ __device__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint
   }
   __syncthreads();
   for (uint32_t r = threadIdx.x; r <= G::V; r += blockDim.x)
-    sp.hp[r] = (r == 0 || r == G::V) ? 0 : (uint8_t)lcp8(sp.x[r - 1], sp.x[r]);
+    sp.hp[r] = (r == 0 || r == G::V) ? 0 : (uint8_t)key_lcp(sp.x[r - 1], sp.x[r], dna);
   if (threadIdx.x == 0) sp.tree[0] = 0;
   __syncthreads();
 }
@@ -304,13 +304,13 @@ __device__ __forceinline__ uint32_t classify_count(const Rec* __restrict__ recs,
 // length); a single string is finished.
 template <int LOGV>
 __device__ __forceinline__ uint32_t bucket_desc(uint32_t b, uint32_t size, uint32_t depth,
-                                                const Splitters<LOGV>& sp) {
+                                                const Splitters<LOGV>& sp, uint32_t dna) {
   const uint32_t r = b >> 1;
   if (b & 1) {
     const uint64_t xr = sp.x[r];
-    if (has_nul(xr)) return kFin | kNulEq | (depth + nnz_prefix(xr));
+    if (key_end(xr, dna)) return kFin | kNulEq | (depth + key_nnz(xr, dna));
     if (size == 1) return kFin;
-    return depth + 8;
+    return depth + key_width(dna);
   }
   if (size == 1) return kFin;
   return depth + sp.hp[r];
@@ -441,7 +441,7 @@ __device__ __forceinline__ uint32_t move_batch(const SortCtx& c, const SetDesc& 
     uint64_t k = key[u];
     bytes += 34;
     if (nd != depth) {
-      k = load_cache(sd.chars, off[u], nd, sd.cap);
+      k = load_key(sd.chars, off[u], nd, sd.cap, sd.dna);
       bytes += 8;
     }
     store_rec(c.rec[par ^ 1] + dest, k, id[u], o32[u]);

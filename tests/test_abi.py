@@ -141,3 +141,17 @@ def test_suffix_array_argument_checks(lib):
     assert lib.ss_suffix_array(dummy, 10, dummy, None, (1 << 20) + 1, None) == 1
     if not _has_gpu():
         assert lib.ss_suffix_array(dummy, 10, dummy, None, 0, None) == 7
+
+
+def test_sort_dna_argument_checks(lib):
+    o = ss.make_options()
+    dummy = ctypes.c_void_p(4096)
+    assert lib.ss_sort_dna(None, 0, None, 0, None, None, ctypes.byref(o), None) == 0          # n = 0
+    assert lib.ss_sort_dna(dummy, 100, dummy, 1 << 32, dummy, None, ctypes.byref(o), None) == 4
+    assert lib.ss_sort_dna(None, 100, dummy, 5, dummy, None, ctypes.byref(o), None) == 1      # NULL chars
+    assert lib.ss_sort_dna(dummy, 0, dummy, 5, dummy, None, ctypes.byref(o), None) == 1       # no characters
+    assert lib.ss_sort_dna(dummy, 100, dummy, 5, None, None, ctypes.byref(o), None) == 1      # NULL output
+    bad = ss.make_options(small_cutoff=32)
+    assert lib.ss_sort_dna(dummy, 100, dummy, 5, dummy, None, ctypes.byref(bad), None) == 1
+    if not _has_gpu():
+        assert lib.ss_sort_dna(dummy, 100, dummy, 5, dummy, None, ctypes.byref(o), None) == 7
