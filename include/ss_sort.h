@@ -85,7 +85,16 @@ typedef struct ss_options {
                                   entered through a jump table over the key's
                                   top 12 bits (Section 4.4; multi-block steps,
                                   the others as 0).                             */
-    uint32_t flags;            /* reserved, must be 0                           */
+    uint32_t host_parts;       /* ss_sort_host only: the strings are cut into
+                                  this many parts by index, and part p is
+                                  sorted while part p + 1 is still being
+                                  copied; the sorted parts are LCP-merged
+                                  (Section 4.3).  0 or 1 = copy everything,
+                                  then sort (the default: over a host link
+                                  as fast as the sort, the parts' sorts and
+                                  merges cost more than the overlap saves);
+                                  else a power of two <= 16.  Ignored
+                                  elsewhere.                                  */
     void* workspace;           /* optional caller-owned device workspace of at
                                   least ss_workspace_size() bytes, 256-byte
                                   aligned.  NULL: the library allocates
@@ -115,7 +124,18 @@ size_t ss_workspace_size(uint64_t n, const ss_options* opt);
  * and the results copied back, all inside the call (pinned host buffers make
  * the copies fastest).  The device buffers are stream-ordered allocations
  * from the device's default memory pool, returned to the pool at the end of
- * the call. */
+ * the call.
+ * With more than one part (ss_options.host_parts) the offsets are copied
+ * first, then the characters part by part on a second stream, and part p is
+ * sorted as soon as its characters are in (the scheme of Section 4.3.1:
+ * sort parts independently, then K-way LCP-merge them).  That needs the
+ * strings packed in index order (string i lies in [offsets[i],
+ * offsets[i + 1]) with its terminator at offsets[i + 1] - 1, the last one
+ * ending at chars_len - 1), which is checked on the device once all bytes
+ * are in; a set that is not packed that way (overlapping strings, gaps,
+ * another order) is then sorted again as a whole, with the same result.
+ * offsets must then be host-readable memory (SS_ERR_INVALID for a device
+ * pointer).  The extra device memory of the parts is 64 bytes per string. */
 ss_status ss_sort_host(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets,
                        uint64_t n, uint32_t* out_perm, uint32_t* out_lcp,
                        const ss_options* opt, void* stream);

@@ -87,7 +87,7 @@ class Options(ctypes.Structure):
         ("big_threshold", ctypes.c_uint32),
         ("seed", ctypes.c_uint32),
         ("classifier", ctypes.c_uint32),
-        ("flags", ctypes.c_uint32),
+        ("host_parts", ctypes.c_uint32),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
     ]
@@ -326,7 +326,10 @@ def suffix_array(text, n: int | None = None, with_lcp: bool = True, initial_dept
 def sort_host(chars, offsets, max_len: int = 0, with_lcp: bool = True, perm=None, lcp=None, stream=None,
               **opts):
     """Sort a host string set (numpy arrays or CPU tensors, ideally pinned):
-    the copies to and from the device happen inside the library call."""
+    the copies to and from the device happen inside the library call.
+    host_parts=P (a power of two <= 16) sorts P parts while later ones are
+    still being copied and LCP-merges them (strings packed in index order;
+    other layouts are sorted again in one piece)."""
     import numpy as np
     lib = load()
 

@@ -151,12 +151,16 @@ struct Opts {
   uint32_t seed = 0x5EED;
   uint32_t classifier = 0;
   uint32_t mq_factor = 16;
+  uint32_t host_parts = 0;  // ss_sort_host: 0 = automatic
 };
+
+constexpr uint32_t kMaxHostParts = 16;
 
 static ss_status resolve_opts(const ss_options* o, Opts& r) {
   r = Opts();
   if (!o) return SS_OK;
-  if (o->flags != 0) return SS_ERR_INVALID;
+  if (o->host_parts > kMaxHostParts || (o->host_parts & (o->host_parts - 1))) return SS_ERR_INVALID;
+  r.host_parts = o->host_parts;
   if (o->max_len) r.cap = o->max_len;
   if (o->splitters_log2) {
     if (o->splitters_log2 < 8 || o->splitters_log2 > 10) return SS_ERR_INVALID;
@@ -300,9 +304,9 @@ static thread_local Pinned t_down, t_up;
 static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o, const DevInfo& dev,
                           bool big, cudaStream_t st) {
   const LaunchHook hook{st};
-  SS_CUDA(cudaMemsetAsync(ws + L.ctrl, 0, kCtrlBytes, st));
-  SS_CUDA(cudaMemsetAsync(ws + L.mq_ready, 0, (size_t)L.cap_mq * 4, st));
-  SS_CUDA(cudaMemsetAsync(ws + L.wide, 0, (size_t)c.num_sets * 4, st));
+  SS_CUDA(launch_upload(nullptr, ws + L.ctrl, kCtrlBytes, st, hook));
+  SS_CUDA(launch_upload(nullptr, ws + L.mq_ready, (size_t)L.cap_mq * 4, st, hook));
+  SS_CUDA(launch_upload(nullptr, ws + L.wide, (size_t)c.num_sets * 4, st, hook));
   SS_CUDA(launch_init(c, st, hook));
   if (big) {
     if (t_down.reserve(64 + (size_t)L.cap_big * sizeof(Task)) != SS_OK) return SS_ERR_OOM;
@@ -346,8 +350,8 @@ static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o
       }
       if (cnt > L.ncounters_max) return SS_ERR_QUEUE_FULL;
       std::memcpy(t_up.p, gts.data(), (size_t)G * sizeof(GenTask));
-      SS_CUDA(cudaMemcpyAsync(ws + L.gen, t_up.p, (size_t)G * sizeof(GenTask), cudaMemcpyHostToDevice, st));
-      SS_CUDA(cudaMemsetAsync(ws + L.ctrl + 4 * (cur ? kCBig0 : kCBig1), 0, 4, st));
+      SS_CUDA(launch_upload(t_up.p, ws + L.gen, (size_t)G * sizeof(GenTask), st, hook));
+      SS_CUDA(launch_upload(nullptr, ws + L.ctrl + 4 * (cur ? kCBig0 : kCBig1), 4, st, hook));
       BigStepArgs a;
       a.c = c;
       a.c.big_cur = cur;
@@ -417,7 +421,7 @@ static ss_status sort_device(const uint8_t* chars, const uint64_t* offsets, uint
     if (r == SS_OK) {
       // t_up is reused by the step planner: wait for this small copy first
       std::memcpy(t_up.p, &sd, sizeof(sd));
-      if (cudaMemcpyAsync(ws + L.sets, t_up.p, sizeof(sd), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      if (launch_upload(t_up.p, ws + L.sets, sizeof(sd), st, LaunchHook{st}) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess)
         r = SS_ERR_CUDA;
     }
@@ -821,28 +825,206 @@ ss_status ss_sort_dna(const uint8_t* chars, uint64_t chars_len, const uint64_t* 
   return r;
 }
 
+// ---- host buffers ------------------------------------------------------------------
+
+// With the default (0) the whole set is copied, then sorted: on the GB300's
+// host link (about 210 GB/s) sorting the parts and merging them costs more
+// than the overlap saves (20 M URL-like strings: 13.5 ms in one piece, 14.5 /
+// 16.0 / 20.4 ms in 2 / 4 / 8 parts).
+constexpr uint32_t kPipeAutoParts = 1;
+// Merges of the parts use a sample step between these two, the largest that
+// still gives about 1024 pieces per SM (a piece is merged by one thread).
+constexpr uint32_t kPipeMinStep = 16, kPipeMaxStep = 128;
+static_assert(sizeof(SetDesc) % 4 == 0 && sizeof(GenTask) % 4 == 0, "uploads move whole words");
+
+// A copy stream and its events, per thread and device.
+struct CopyLane {
+  cudaStream_t cs = nullptr;
+  cudaEvent_t start = nullptr, offs = nullptr, chunk[kMaxHostParts] = {};
+  bool ready = false;
+};
+static thread_local std::map<int, CopyLane> t_lanes;
+
+static ss_status copy_lane(CopyLane*& out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SS_ERR_NO_DEVICE;
+  CopyLane& l = t_lanes[dev];
+  if (!l.ready) {
+    bool ok = cudaStreamCreateWithFlags(&l.cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaEventCreateWithFlags(&l.start, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&l.offs, cudaEventDisableTiming) == cudaSuccess;
+    for (uint32_t p = 0; ok && p < kMaxHostParts; ++p)
+      ok = cudaEventCreateWithFlags(&l.chunk[p], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return SS_ERR_CUDA;
+    l.ready = true;
+  }
+  out = &l;
+  return SS_OK;
+}
+
+// One binary LCP merge of two adjacent sorted ranges [lo, mid) and [mid, hi)
+// of a record buffer (into the same range of dst, or of the outputs if dst is
+// null).
+static bool merge_pair(const uint8_t* chars, const uint64_t* offsets, uint32_t cap, const MergeRec* src,
+                       MergeRec* dst, uint32_t lo, uint32_t mid, uint32_t hi, uint32_t* perm, uint32_t* lcp,
+                       uint32_t* cut, uint32_t* counter, uint32_t sms, cudaStream_t st, const LaunchHook& hook) {
+  uint32_t S = kPipeMaxStep;
+  while (S > kPipeMinStep && (hi - lo) / S < sms * 1024u) S >>= 1;
+  MergeRoundArgs ra{};
+  ra.chars = chars;
+  ra.offsets = offsets;
+  ra.cap = cap;
+  ra.ncur = 2;
+  ra.S = S;
+  ra.src = src + lo;
+  ra.dst = dst ? dst + lo : nullptr;
+  ra.cut = cut;
+  ra.out_perm = perm + lo;
+  ra.out_lcp = lcp + lo;
+  ra.counter = counter;
+  ra.start[0] = 0;
+  ra.start[1] = mid - lo;
+  ra.start[2] = hi - lo;
+  ra.sbase[0] = 0;
+  ra.sbase[1] = (mid - lo) / S;
+  ra.sbase[2] = ra.sbase[1] + (hi - mid) / S;
+  ra.nsamples = ra.sbase[2];
+  return launch_upload(nullptr, counter, sizeof(uint32_t), st, hook) == cudaSuccess &&
+         launch_merge_round(ra, sms, st, hook) == cudaSuccess;
+}
+
+// The copy overlapped with the sort (the scheme of Section 4.3.1 for NUMA
+// machines, with the host link in the role of the slow interconnect): the
+// strings are cut into P parts by index; part p's characters are copied on a
+// second stream while part p - 1 is sorted; each sorted part becomes a run of
+// 32-byte merge records, and adjacent runs are LCP-merged as soon as both
+// exist (a binary tree, the last level writing the outputs).  This needs
+// every part's strings inside its own stretch of chars (strings packed in
+// index order), which k_layout_check verifies on the device once everything
+// has arrived; a set that fails is sorted again as a whole (the parts'
+// results are discarded).  Returns SS_OK with *done = false when the layout
+// check failed.
+static ss_status sort_host_parts(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets, uint64_t n,
+                                 uint32_t P, uint8_t* dchars, uint64_t* doff, uint32_t* dperm, uint32_t* dlcp,
+                                 uint8_t* scratch, const Opts& o, const ss_options* opt, const DevInfo& dev,
+                                 cudaStream_t st, bool* done) {
+  *done = false;
+  CopyLane* lane = nullptr;
+  ss_status s = copy_lane(lane);
+  if (s != SS_OK) return s;
+  // whatever happens below, no copy is still writing the buffers on return
+  struct Drain {
+    cudaStream_t cs;
+    ~Drain() { cudaStreamSynchronize(cs); }
+  } drain{lane->cs};
+  const LaunchHook hook{st};
+  const uint32_t sms = (uint32_t)dev.sms;
+  const size_t recb = align256(n * sizeof(MergeRec));
+  MergeRec* rec[2] = {reinterpret_cast<MergeRec*>(scratch), reinterpret_cast<MergeRec*>(scratch + recb)};
+  uint32_t* cut = reinterpret_cast<uint32_t*>(scratch + 2 * recb);
+  uint32_t* ctl = reinterpret_cast<uint32_t*>(scratch + 2 * recb + align256((n / kPipeMinStep + 4) * 4));
+  uint32_t* counter = ctl;
+  uint32_t* bad = ctl + 1;
+  // part p = strings [a[p], a[p + 1]); its characters [b[p], b[p + 1])
+  uint64_t a[kMaxHostParts + 1], b[kMaxHostParts + 1];
+  for (uint32_t p = 0; p <= P; ++p) a[p] = n * p / P;
+  b[0] = 0;
+  for (uint32_t p = 1; p < P; ++p) b[p] = std::max(b[p - 1], std::min<uint64_t>(offsets[a[p]], chars_len));
+  b[P] = chars_len;
+  SS_CUDA(launch_upload(nullptr, ctl, 8, st, hook));
+  SS_CUDA(cudaEventRecord(lane->start, st));
+  SS_CUDA(cudaStreamWaitEvent(lane->cs, lane->start, 0));
+  SS_CUDA(cudaMemcpyAsync(doff, offsets, n * 8, cudaMemcpyHostToDevice, lane->cs));
+  SS_CUDA(cudaEventRecord(lane->offs, lane->cs));
+  for (uint32_t p = 0; p < P; ++p) {
+    if (b[p + 1] > b[p])
+      SS_CUDA(cudaMemcpyAsync(dchars + b[p], chars + b[p], b[p + 1] - b[p], cudaMemcpyHostToDevice, lane->cs));
+    SS_CUDA(cudaEventRecord(lane->chunk[p], lane->cs));
+  }
+  SS_CUDA(cudaStreamWaitEvent(st, lane->offs, 0));
+  const uint32_t cap = std::min<uint32_t>(o.cap, 1u << 30);
+  for (uint32_t p = 0; p < P; ++p) {
+    SS_CUDA(cudaStreamWaitEvent(st, lane->chunk[p], 0));
+    const uint32_t lo = (uint32_t)a[p], np = (uint32_t)(a[p + 1] - a[p]);
+    s = sort_device(dchars, doff + lo, np, dperm + lo, dlcp + lo, opt, st);
+    if (s != SS_OK) return s;
+    MergePrepArgs pa{};
+    pa.chars = dchars;
+    pa.offsets = doff;
+    pa.cap = cap;
+    pa.K = 1;
+    pa.total = np;
+    pa.dst = rec[0] + lo;
+    pa.start[0] = 0;
+    pa.start[1] = np;
+    pa.perm[0] = dperm + lo;
+    pa.lcp[0] = dlcp + lo;
+    pa.ibase[0] = lo;
+    SS_CUDA(launch_merge_prep(pa, sms, st, hook));
+    // merge every complete pair of runs up the tree
+    for (uint32_t w = 2, lvl = 1; w <= P && (p + 1) % w == 0; w <<= 1, ++lvl) {
+      const uint32_t q0 = p + 1 - w;
+      MergeRec* dst = w == P ? nullptr : rec[lvl & 1];
+      if (!merge_pair(dchars, doff, cap, rec[(lvl - 1) & 1], dst, (uint32_t)a[q0], (uint32_t)a[q0 + w / 2],
+                      (uint32_t)a[p + 1], dperm, dlcp, cut, counter, sms, st, hook))
+        return SS_ERR_CUDA;
+    }
+  }
+  SS_CUDA(launch_layout_check(dchars, chars_len, doff, (uint32_t)n, bad, sms, st, hook));
+  if (t_down.reserve(256) != SS_OK) return SS_ERR_OOM;
+  uint32_t* hbad = static_cast<uint32_t*>(t_down.p);
+  SS_CUDA(cudaMemcpyAsync(hbad, bad, 4, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  *done = *hbad == 0;
+  return SS_OK;
+}
+
 ss_status ss_sort_host(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets, uint64_t n,
                        uint32_t* out_perm, uint32_t* out_lcp, const ss_options* opt, void* stream) {
   if (n >= 0xFFFFFFFFull) return SS_ERR_TOO_LARGE;
   if (n == 0) return SS_OK;
   if (!chars || !offsets || !out_perm || chars_len == 0) return SS_ERR_INVALID;
+  Opts o;
+  ss_status s = resolve_opts(opt, o);
+  if (s != SS_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   DevInfo dev;
-  ss_status s = device_info(dev);
+  s = device_info(dev);
   if (s != SS_OK) return s;
+  uint32_t P = o.host_parts;
+  if (P == 0) P = kPipeAutoParts;
+  if (n < 2ull * P) P = 1;
+  if (P > 1) {  // the part boundaries are read from the offsets on the host
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, offsets) != cudaSuccess) {
+      cudaGetLastError();
+      return SS_ERR_INVALID;
+    }
+    if (at.type == cudaMemoryTypeDevice) return SS_ERR_INVALID;
+  }
   const size_t cb = align256(chars_len + 16), ob = align256(n * 8), pb = align256(n * 4);
-  const size_t need = cb + ob + 2 * pb;
+  const size_t scratch = P > 1 ? 2 * align256(n * sizeof(MergeRec)) + align256((n / kPipeMinStep + 4) * 4) + 256
+                               : 0;
+  const size_t need = cb + ob + 2 * pb + scratch;
   uint8_t* d = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&d), need, st) != cudaSuccess) return SS_ERR_OOM;
   uint8_t* dchars = d;
   uint64_t* doff = reinterpret_cast<uint64_t*>(d + cb);
   uint32_t* dperm = reinterpret_cast<uint32_t*>(d + cb + ob);
-  uint32_t* dlcp = out_lcp ? reinterpret_cast<uint32_t*>(d + cb + ob + pb) : nullptr;
+  uint32_t* dlcp = reinterpret_cast<uint32_t*>(d + cb + ob + pb);
   ss_status r = SS_OK;
-  if (cudaMemcpyAsync(dchars, chars, chars_len, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(doff, offsets, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    r = SS_ERR_CUDA;
-  if (r == SS_OK) r = sort_device(dchars, doff, n, dperm, dlcp, opt, st);
+  // zeros after the last byte: a read past it finds a terminator
+  if (cudaMemsetAsync(dchars + chars_len, 0, cb - chars_len, st) != cudaSuccess) r = SS_ERR_CUDA;
+  bool done = false;
+  if (r == SS_OK && P > 1)
+    r = sort_host_parts(chars, chars_len, offsets, n, P, dchars, doff, dperm, dlcp, d + cb + ob + 2 * pb, o, opt,
+                        dev, st, &done);
+  if (r == SS_OK && !done) {
+    if (P == 1 && (cudaMemcpyAsync(dchars, chars, chars_len, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                   cudaMemcpyAsync(doff, offsets, n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess))
+      r = SS_ERR_CUDA;
+    if (r == SS_OK) r = sort_device(dchars, doff, n, dperm, out_lcp ? dlcp : nullptr, opt, st);
+  }
   if (r == SS_OK) {
     if (cudaMemcpyAsync(out_perm, dperm, n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) r = SS_ERR_CUDA;
     if (out_lcp && cudaMemcpyAsync(out_lcp, dlcp, n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)

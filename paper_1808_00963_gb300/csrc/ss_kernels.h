@@ -51,6 +51,9 @@ cudaError_t launch_small(const SortCtx& c, uint32_t pmax, uint32_t grid_warp, ui
                          cudaStream_t st, const LaunchHook& hook);
 cudaError_t launch_lcp_fix(const SortCtx& c, uint32_t grid, cudaStream_t st, const LaunchHook& hook);
 // Packs bytes over {A, C, G, T, 0} into 3-bit codes (dna_key's layout).
+// Copies bytes (a multiple of 4, 4-byte aligned) from pinned host memory
+// with a kernel, or zero-fills dst when host_src is null.
+cudaError_t launch_upload(const void* host_src, void* dst, size_t bytes, cudaStream_t st, const LaunchHook& hook);
 cudaError_t launch_pack_dna(const uint8_t* chars, uint64_t len, uint64_t* out, uint64_t words, uint32_t* bad,
                             uint32_t grid, cudaStream_t st, const LaunchHook& hook);
 cudaError_t launch_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t cap,
@@ -79,6 +82,7 @@ struct MergePrepArgs {
   uint32_t start[kMergeMaxRuns + 1];
   const uint32_t* perm[kMergeMaxRuns];
   const uint32_t* lcp[kMergeMaxRuns];
+  uint32_t ibase[kMergeMaxRuns];  // added to run k's entries (runs sorted with local indices)
 };
 
 // One round: current run c at [start[c], start[c + 1]); runs 2p and 2p + 1
@@ -105,6 +109,10 @@ cudaError_t launch_merge_prep(const MergePrepArgs& a, uint32_t sms, cudaStream_t
 cudaError_t launch_merge_round(const MergeRoundArgs& a, uint32_t sms, cudaStream_t st, const LaunchHook& hook);
 cudaError_t launch_merge_copy(const uint32_t* perm, const uint32_t* lcp, uint32_t n, uint32_t* out_perm,
                               uint32_t* out_lcp, uint32_t sms, cudaStream_t st, const LaunchHook& hook);
+// Sets *bad unless every string i lies in [offsets[i], offsets[i + 1]) with
+// its terminator at offsets[i + 1] - 1 (the last one ending at chars_len - 1).
+cudaError_t launch_layout_check(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets, uint32_t n,
+                                uint32_t* bad, uint32_t sms, cudaStream_t st, const LaunchHook& hook);
 
 // Suffix array by prefix doubling (ss_sa.cu).
 enum class SaKernel { kIota, kHeads0, kName0, kCompact, kEncode, kApply, kRename, kLongFlags, kLcp };

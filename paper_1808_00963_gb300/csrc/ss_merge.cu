@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) k_merge_prep(MergePrepArgs a) {
     const uint32_t k = find_range(a.start, a.K, g);
     const uint32_t j = g - a.start[k];
     MergeRec r;
-    r.idx = a.perm[k][j];
+    r.idx = a.perm[k][j] + a.ibase[k];
     r.h = j ? a.lcp[k][j] : 0u;
     r.off = a.offsets[r.idx];
     load_words(a.chars, a.cap, r.off, r.h, r.w0, r.w1);
@@ -299,6 +299,21 @@ __global__ void k_merge_copy(const uint32_t* __restrict__ perm, const uint32_t* 
   }
 }
 
+// Strings packed one after the other in index order: string i starts after
+// string i - 1's terminator.  A set that passes can be sorted in parts while
+// later parts are still being copied (each part's strings lie in its own
+// stretch of chars).
+__global__ void k_layout_check(const uint8_t* __restrict__ chars, uint64_t chars_len,
+                               const uint64_t* __restrict__ offsets, uint32_t n, uint32_t* bad) {
+  bool ok = true;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t o = offsets[i];
+    const uint64_t e = i + 1 < n ? offsets[i + 1] : chars_len;
+    ok = ok && o < e && e <= chars_len && chars[e - 1] == 0;
+  }
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) *bad = 1u;
+}
+
 uint32_t grid_for(uint64_t items, uint32_t block, uint32_t sms, uint32_t per_sm) {
   const uint64_t g = (items + block - 1) / block;
   return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(g, (uint64_t)sms * per_sm));
@@ -327,6 +342,13 @@ cudaError_t launch_merge_copy(const uint32_t* perm, const uint32_t* lcp, uint32_
                               uint32_t* out_lcp, uint32_t sms, cudaStream_t st, const LaunchHook& hook) {
   hook.run("merge_round",
            [&] { k_merge_copy<<<grid_for(n, 256, sms, 16), 256, 0, st>>>(perm, lcp, n, out_perm, out_lcp); });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_layout_check(const uint8_t* chars, uint64_t chars_len, const uint64_t* offsets, uint32_t n,
+                                uint32_t* bad, uint32_t sms, cudaStream_t st, const LaunchHook& hook) {
+  hook.run("layout_check",
+           [&] { k_layout_check<<<grid_for(n, 256, sms, 8), 256, 0, st>>>(chars, chars_len, offsets, n, bad); });
   return cudaGetLastError();
 }
 

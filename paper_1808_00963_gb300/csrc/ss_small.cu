@@ -675,6 +675,28 @@ cudaError_t launch_pack_dna(const uint8_t* chars, uint64_t len, uint64_t* out, u
   return cudaGetLastError();
 }
 
+// Small host-to-device transfers and zero fills done by a kernel rather than
+// by the copy engines, which a large copy queued on another stream can hold
+// up for milliseconds: src is pinned host memory, which the device reads
+// directly (null: write zeros).
+__global__ void k_upload(const uint32_t* __restrict__ src, uint32_t* __restrict__ dst, uint32_t words) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x)
+    dst[i] = src ? src[i] : 0u;
+}
+
+cudaError_t launch_upload(const void* host_src, void* dst, size_t bytes, cudaStream_t st, const LaunchHook& hook) {
+  if (bytes == 0) return cudaSuccess;
+  if ((bytes & 3) || (reinterpret_cast<uintptr_t>(dst) & 3) || (reinterpret_cast<uintptr_t>(host_src) & 3) ||
+      bytes >= (4ull << 32))
+    return cudaErrorInvalidValue;
+  const uint32_t words = (uint32_t)(bytes / 4);
+  const uint32_t grid = std::min<uint32_t>((words + kBlock - 1) / kBlock, 1024);
+  hook.run("upload", [&] {
+    k_upload<<<grid, kBlock, 0, st>>>(static_cast<const uint32_t*>(host_src), static_cast<uint32_t*>(dst), words);
+  });
+  return cudaGetLastError();
+}
+
 cudaError_t launch_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint32_t n, uint32_t cap,
                                   const uint32_t* perm, const uint32_t* lcp, uint8_t* dchar, uint32_t* dprefix,
                                   unsigned long long* sum_d, uint32_t grid, cudaStream_t st, const LaunchHook& hook) {
