@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kBlock) k_big_emit(SortCtx c, const GenTask* _
 }
 
 template <int LOGV>
-__global__ void __launch_bounds__(kBlock, 3) k_big_scatter(SortCtx c, const GenTask* __restrict__ gt, uint32_t G,
+__global__ void __launch_bounds__(kBlock, 4) k_big_scatter(SortCtx c, const GenTask* __restrict__ gt, uint32_t G,
                                                         const uint32_t* __restrict__ scanned,
                                                         const uint32_t* __restrict__ gstart,
                                                         const uint32_t* __restrict__ gdesc, uint32_t R) {

@@ -300,13 +300,31 @@ struct Pinned {
 };
 static thread_local Pinned t_down, t_up;
 
+// Small uploads and zero fills of the sort: on the copy engines, except while
+// a large copy on another stream holds them (the overlapped host path), when
+// a kernel that reads the pinned staging memory does them instead.  (A kernel
+// reading host memory costs 6-55 us per launch on the GB300 machine, more than
+// the copy engine when it is free.)
+static thread_local bool t_kernel_copies = false;
+
+static cudaError_t small_h2d(void* dst, const void* pinned_src, size_t bytes, cudaStream_t st,
+                             const LaunchHook& hook) {
+  if (t_kernel_copies) return launch_upload(pinned_src, dst, bytes, st, hook);
+  return cudaMemcpyAsync(dst, pinned_src, bytes, cudaMemcpyHostToDevice, st);
+}
+
+static cudaError_t zero_fill(void* dst, size_t bytes, cudaStream_t st, const LaunchHook& hook) {
+  if (t_kernel_copies) return launch_upload(nullptr, dst, bytes, st, hook);
+  return cudaMemsetAsync(dst, 0, bytes, st);
+}
+
 // Enqueues everything after the set descriptors are in place.
 static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o, const DevInfo& dev,
                           bool big, cudaStream_t st) {
   const LaunchHook hook{st};
-  SS_CUDA(launch_upload(nullptr, ws + L.ctrl, kCtrlBytes, st, hook));
-  SS_CUDA(launch_upload(nullptr, ws + L.mq_ready, (size_t)L.cap_mq * 4, st, hook));
-  SS_CUDA(launch_upload(nullptr, ws + L.wide, (size_t)c.num_sets * 4, st, hook));
+  SS_CUDA(zero_fill(ws + L.ctrl, kCtrlBytes, st, hook));
+  SS_CUDA(zero_fill(ws + L.mq_ready, (size_t)L.cap_mq * 4, st, hook));
+  SS_CUDA(zero_fill(ws + L.wide, (size_t)c.num_sets * 4, st, hook));
   SS_CUDA(launch_init(c, st, hook));
   if (big) {
     if (t_down.reserve(64 + (size_t)L.cap_big * sizeof(Task)) != SS_OK) return SS_ERR_OOM;
@@ -350,8 +368,8 @@ static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o
       }
       if (cnt > L.ncounters_max) return SS_ERR_QUEUE_FULL;
       std::memcpy(t_up.p, gts.data(), (size_t)G * sizeof(GenTask));
-      SS_CUDA(launch_upload(t_up.p, ws + L.gen, (size_t)G * sizeof(GenTask), st, hook));
-      SS_CUDA(launch_upload(nullptr, ws + L.ctrl + 4 * (cur ? kCBig0 : kCBig1), 4, st, hook));
+      SS_CUDA(small_h2d(ws + L.gen, t_up.p, (size_t)G * sizeof(GenTask), st, hook));
+      SS_CUDA(zero_fill(ws + L.ctrl + 4 * (cur ? kCBig0 : kCBig1), 4, st, hook));
       BigStepArgs a;
       a.c = c;
       a.c.big_cur = cur;
@@ -421,7 +439,7 @@ static ss_status sort_device(const uint8_t* chars, const uint64_t* offsets, uint
     if (r == SS_OK) {
       // t_up is reused by the step planner: wait for this small copy first
       std::memcpy(t_up.p, &sd, sizeof(sd));
-      if (launch_upload(t_up.p, ws + L.sets, sizeof(sd), st, LaunchHook{st}) != cudaSuccess ||
+      if (small_h2d(ws + L.sets, t_up.p, sizeof(sd), st, LaunchHook{st}) != cudaSuccess ||
           cudaStreamSynchronize(st) != cudaSuccess)
         r = SS_ERR_CUDA;
     }
@@ -912,11 +930,16 @@ static ss_status sort_host_parts(const uint8_t* chars, uint64_t chars_len, const
   CopyLane* lane = nullptr;
   ss_status s = copy_lane(lane);
   if (s != SS_OK) return s;
-  // whatever happens below, no copy is still writing the buffers on return
+  // whatever happens below, no copy is still writing the buffers on return,
+  // and the sort's small uploads are back on the copy engines
   struct Drain {
     cudaStream_t cs;
-    ~Drain() { cudaStreamSynchronize(cs); }
+    ~Drain() {
+      cudaStreamSynchronize(cs);
+      t_kernel_copies = false;
+    }
   } drain{lane->cs};
+  t_kernel_copies = true;
   const LaunchHook hook{st};
   const uint32_t sms = (uint32_t)dev.sms;
   const size_t recb = align256(n * sizeof(MergeRec));

@@ -319,7 +319,7 @@ __device__ __forceinline__ uint32_t bucket_desc(uint32_t b, uint32_t size, uint3
 // Records moved per batch of one warp in the distribution: the loads of a
 // batch are issued together so that each warp keeps kMoveBatch rounds of
 // memory accesses in flight.  4 (not 8) keeps the multi-block distribution at
-// 80 registers, 3 blocks per SM: more warps in flight beat deeper batches.
+// 64 registers, 4 blocks per SM: more warps in flight beat deeper batches.
 constexpr int kMoveBatch = 4;
 constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 
