@@ -198,7 +198,7 @@ static uint32_t pmax_of(uint32_t cutoff) {
 constexpr uint32_t kCtrlWords = 64;                          // status and list counters
 constexpr size_t kCtrlBytes = kCtrlWords * 4 + kKClasses * 8;  // + algorithmic byte counters
 enum Ctrl : uint32_t { kCStatus = 0, kCBig0 = 1, kCBig1 = 2, kCHead = 3, kCTail = 4, kCPending = 5,
-                       kCSmallW = 6, kCSmallC = 7 };
+                       kCSmallW = 6, kCSmallC = 7, kCSmallD = 8 };
 
 struct Layout {
   size_t ctrl, sets, wide, rec0, rec1, bucket_of, big0, big1, gen, spl, counters, partials, gstart, gdesc,
@@ -213,7 +213,9 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
   L.cap_big = big ? (uint32_t)(M / ((uint64_t)o.big_thr + 1) + 2) : 0;
   L.cap_mq = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, std::max<uint64_t>(4096, o.mq_factor * (M / o.cutoff) + 1024));
-  L.cap_sw = (uint32_t)(M + 2);  // direct warp tasks (<= M/2) plus runs passed on by the block sort (<= M/2)
+  // warp tasks: subsets and runs the block sort passes on, disjoint and of at
+  // least 2 strings (<= M/2), then as many deferred runs (<= M/2)
+  L.cap_sw = (uint32_t)(M / 2 + 1);
   L.cap_sc = (uint32_t)(M / 33 + 2);
   const uint64_t KP = 2ull << o.logv_big;
   const uint64_t tiles_max = big ? M / (kBlock * 8) + L.cap_big : 0;
@@ -234,7 +236,7 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   L.gdesc = take((size_t)L.cap_big * KP * 4);
   L.mq_items = take((size_t)L.cap_mq * sizeof(Task));
   L.mq_ready = take((size_t)L.cap_mq * 4);
-  L.sw_items = take((size_t)L.cap_sw * sizeof(Task));
+  L.sw_items = take(2 * (size_t)L.cap_sw * sizeof(Task));
   L.sc_items = take((size_t)L.cap_sc * sizeof(Task));
   L.total = off;
   return L;
@@ -257,6 +259,7 @@ static SortCtx make_ctx(uint8_t* ws, const Layout& L, uint32_t num_sets, uint32_
   c.mq = WorkQueue{reinterpret_cast<Task*>(ws + L.mq_items), reinterpret_cast<uint32_t*>(ws + L.mq_ready),
                    ctrl + kCHead, ctrl + kCTail, ctrl + kCPending, L.cap_mq, 1u};
   c.small_warp = TaskList{reinterpret_cast<Task*>(ws + L.sw_items), ctrl + kCSmallW, L.cap_sw};
+  c.small_deep = TaskList{reinterpret_cast<Task*>(ws + L.sw_items) + L.cap_sw, ctrl + kCSmallD, L.cap_sw};
   c.small_cta = TaskList{reinterpret_cast<Task*>(ws + L.sc_items), ctrl + kCSmallC, L.cap_sc};
   c.small_cutoff = o.cutoff;
   c.big_threshold = o.big_thr;

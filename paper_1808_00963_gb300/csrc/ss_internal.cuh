@@ -113,6 +113,7 @@ struct SortCtx {
   TaskList big[2];         // multi-block tasks, ping-pong by step
   WorkQueue mq;            // tasks for the persistent single-block kernel
   TaskList small_warp;     // 2..32 records
+  TaskList small_deep;     // runs the first warp pass deferred (long common prefixes)
   TaskList small_cta;      // 33..small_cutoff records
   uint32_t small_cutoff;
   uint32_t big_threshold;  // tasks longer than this go to big[] (if big_enabled)

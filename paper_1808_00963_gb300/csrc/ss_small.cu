@@ -96,12 +96,20 @@ __device__ __forceinline__ void warp_sort(uint32_t& seg, uint64_t& key, uint32_t
 // every other run jumps over the characters all its members share, found with
 // a 64-character look-ahead, and is sorted again.  Writes lcp_g[j] for every
 // position j > 0 of each group and returns the index at the lane's position.
+// With max_jumps > 0, runs still open after that many look-aheads are handed
+// to defer(position in group, run's first position, run length, cache, index,
+// offset, depth) on each of their lanes and left unfinished: a few long
+// common prefixes would otherwise keep whole warps busy while most of their
+// lanes idle (their lcp_g entries after the run's first one stay unwritten).
+template <typename Defer>
 __device__ uint32_t warp_refine(bool active, uint32_t g0, uint32_t nact, uint64_t key, uint32_t idx,
                                 uint64_t off, uint32_t depth, uint32_t cap, const uint8_t* chars, uint32_t dna,
-                                uint32_t* lcp_g, uint32_t* status, unsigned long long& bytes) {
+                                uint32_t* lcp_g, uint32_t* status, unsigned long long& bytes, uint32_t max_jumps,
+                                Defer&& defer) {
   const uint32_t lane = lane_id();
   uint32_t seg = active ? g0 : 0xFFFFFFFFu;
   uint32_t open = active ? 1u : 0u;
+  uint32_t jumps = 0;
   if (!active) { key = ~0ull; idx = 0xFFFFFFFFu; off = 0; depth = 0; }
   const uint32_t upto = (lane == 31) ? kFull : ((2u << lane) - 1);
   while (true) {
@@ -132,6 +140,11 @@ __device__ uint32_t warp_refine(bool active, uint32_t g0, uint32_t nact, uint64_
     }
     if (active) seg = my_start;
     if (!__any_sync(kFull, active && open)) break;
+    if (max_jumps && jumps == max_jumps) {
+      if (active && open) defer(lane - g0, my_start - g0, next - my_start, key, idx, off, depth);
+      break;
+    }
+    ++jumps;
     // look-ahead: the first window (8, 16, ... characters deeper) where the
     // members of the run differ or end; the run continues there
     uint64_t w[kLookWindows];
@@ -198,11 +211,19 @@ __device__ __forceinline__ void pack_rounds(uint32_t nt, uint32_t my_len, Round&
 // Warps take runs of up to 16 consecutive small tasks and pack as many whole
 // tasks as fit into 32 lanes per round.
 constexpr uint32_t kPackChunk = 16;
+// Passes over the warp tasks: look-aheads (64 characters each) a run may take
+// in each pass before it is deferred to the next one (0: no limit).
+constexpr uint32_t kWarpPassJumps[] = {1, 0};
+constexpr uint32_t kWarpPasses = sizeof(kWarpPassJumps) / sizeof(kWarpPassJumps[0]);
+static_assert(kWarpPassJumps[kWarpPasses - 1] == 0, "the last pass finishes every run");
 
-__global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
+// One pass over a list of warp tasks.  With max_jumps > 0, runs with long
+// common prefixes are deferred to the list `out`: their records go back to
+// the record buffer at their current positions, and each run becomes a task.
+__global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c, TaskList list, TaskList out, uint32_t max_jumps) {
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t count = min(*c.small_warp.count, c.small_warp.cap);
+  const uint32_t count = min(*list.count, list.cap);
   const uint32_t lane = lane_id();
   unsigned long long bytes = 0;
   // few tasks: one per warp (parallelism); many: up to 16 per warp (packing)
@@ -210,7 +231,7 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
   for (uint32_t c0 = warp * chunk; c0 < count; c0 += nwarps * chunk) {
     const uint32_t nt = min(chunk, count - c0);
     Task mt{0, 0, 0, 0};
-    if (lane < nt) mt = c.small_warp.items[c0 + lane];
+    if (lane < nt) mt = list.items[c0 + lane];
     pack_rounds(nt, mt.len, [&](bool active, uint32_t g0, uint32_t nact, uint32_t k) {
       const uint32_t tb = __shfl_sync(kFull, mt.begin, k & 31);
       const uint32_t tdepth = __shfl_sync(kFull, mt.depth, k & 31);
@@ -220,9 +241,9 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
       const uint8_t* chars = nullptr;
       uint32_t* lcp_g = nullptr;
       uint32_t* perm = nullptr;
+      const uint32_t par = tmeta >> 31;
       if (active) {
         const SetDesc sd = c.sets[tmeta & 0x7FFFFFFFu];
-        const uint32_t par = tmeta >> 31;
         const uint32_t e = lane - g0;
         const Rec r = load_rec(c.rec[par] + tb + e);
         key = r.key;
@@ -234,8 +255,13 @@ __global__ void __launch_bounds__(kBlock) k_small_warp(SortCtx c) {
         lcp_g = sd.lcp ? sd.lcp + (tb - sd.base) : nullptr;
         perm = sd.perm + (tb - sd.base);
       }
-      const uint32_t fin = warp_refine(active, g0, nact, key, id, off, tdepth, cap, chars, dna, lcp_g, c.status,
-                                       bytes);
+      const uint32_t fin = warp_refine(
+          active, g0, nact, key, id, off, tdepth, cap, chars, dna, lcp_g, c.status, bytes, max_jumps,
+          [&](uint32_t e, uint32_t rs, uint32_t rl, uint64_t k, uint32_t ix, uint64_t o, uint32_t d) {
+            store_rec(c.rec[par] + tb + e, k, ix, (uint32_t)o);
+            bytes += 16;
+            if (e == rs) list_push(out, Task{tb + rs, rl, d, tmeta}, c.status);
+          });
       if (active) {
         perm[lane - g0] = fin;
         bytes += lcp_g ? 24 : 20;  // record 16 read; perm 4 (+ lcp 4) written
@@ -659,7 +685,16 @@ static cudaError_t launch_small_t(const SortCtx& c, uint32_t pmax, uint32_t grid
           c, pmax, kSmallCtaNarrowMax, 0xFFFFFFFFu, min_count, 0u);
     });
   }
-  hook.run("small_warp", [&] { k_small_warp<<<grid_warp, kBlock, 0, st>>>(c); });
+  // the lists alternate: a pass reads one and defers into the other, emptied first
+  for (uint32_t p = 0; p < kWarpPasses; ++p) {
+    const TaskList in = (p & 1) ? c.small_deep : c.small_warp;
+    const TaskList out = (p & 1) ? c.small_warp : c.small_deep;
+    if (p > 0 && kWarpPassJumps[p] > 0) {
+      const cudaError_t e = launch_upload(nullptr, out.count, 4, st, hook);
+      if (e != cudaSuccess) return e;
+    }
+    hook.run("small_warp", [&] { k_small_warp<<<grid_warp, kBlock, 0, st>>>(c, in, out, kWarpPassJumps[p]); });
+  }
   return cudaGetLastError();
 }
 

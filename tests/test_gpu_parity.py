@@ -72,6 +72,27 @@ def test_long_common_prefix(n):
     assert_parity(s, p, l)
 
 
+@pytest.mark.parametrize("cap", [0, 100, 130])
+def test_deep_runs_in_small_subsets(cap):
+    """Many small subsets whose runs share 70 to 400 more characters, mixed
+    with ones settled after one look-ahead: the warp pass that defers deep runs
+    and the pass that finishes them, including runs that end inside, before or
+    after a cap."""
+    rng = np.random.default_rng(cap + 11)
+    strs = []
+    for g in range(3000):
+        stem = bytes(rng.integers(97, 123, size=6).astype(np.uint8))
+        deep = g % 3 != 0
+        shared = bytes(rng.integers(97, 100, size=int(rng.integers(70, 400)) if deep else 3).astype(np.uint8))
+        for _ in range(int(rng.integers(2, 9))):
+            tail = bytes(rng.integers(97, 100, size=int(rng.integers(0, 4))).astype(np.uint8))
+            strs.append(stem + shared + tail)
+    order = rng.permutation(len(strs))
+    s = from_strings([strs[i] for i in order], max_len=cap)
+    p, l = gpu_sort(s)
+    assert_parity(s, p, l)
+
+
 @pytest.mark.parametrize("cap", [1, 7, 8, 9, 16, 500])
 def test_caps(cap):
     s = gen.random_set(5000, 11, 0, 40, ord("a"), ord("c"))
