@@ -203,6 +203,32 @@ def test_config2_full():
     assert np.array_equal(np.sort(sub)[sp], sub)
 
 
+def test_offsets_above_4gib():
+    """Strings beyond byte 2^32 of the character buffer.  A record keeps only
+    the low 32 bits of its string's offset, so a set with larger offsets takes
+    them from the offset array; here mixed with strings below 2^32, and with
+    every string of the lower part repeated above (ties across the boundary),
+    uncapped and capped."""
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    base = gen.url_set(60_000, 21)
+    hi = (1 << 32) + 4096 + 3  # an unaligned start above 2^32
+    chars = np.zeros(hi + base.N + 64, np.uint8)
+    chars[:base.N] = base.chars
+    chars[hi:hi + base.N] = base.chars
+    offsets = np.concatenate([base.offsets[:30_000], base.offsets + np.uint64(hi)])
+    dchars = torch.from_numpy(chars).cuda()
+    doffs = torch.from_numpy(offsets.view(np.int64)).cuda()
+    for cap in (0, 30):
+        perm, lcp = ss.sort(dchars, doffs, max_len=cap)
+        torch.cuda.synchronize()
+        s = gen.StringSet(chars, offsets, cap)
+        assert_parity(s, perm.cpu().numpy().view(np.uint32), lcp.cpu().numpy().view(np.uint32))
+    del dchars, doffs
+    torch.cuda.empty_cache()
+
+
 def test_sort_host_matches_device():
     import paper_1808_00963_gb300 as ss
     s = gen.url_set(100000, 9)
