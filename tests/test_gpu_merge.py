@@ -155,3 +155,22 @@ def test_merge_full_size_urls():
     p = perm.cpu().numpy().view(np.uint32)
     l = lcp.cpu().numpy().view(np.uint32)
     assert oracle.check(s.chars, s.offsets, p, l, s.max_len) == -1
+
+
+def test_merge_offsets_above_4gib():
+    """Runs whose strings lie beyond byte 2^32 of the character buffer (the
+    merge records carry full 64-bit offsets), mixed with strings below it and
+    with every lower string repeated above."""
+    base = gen.url_set(40_000, 23)
+    hi = (1 << 32) + 777
+    chars = np.zeros(hi + base.N + 64, np.uint8)
+    chars[:base.N] = base.chars
+    chars[hi:hi + base.N] = base.chars
+    offsets = np.concatenate([base.offsets[:20_000], base.offsets + np.uint64(hi)])
+    s = gen.StringSet(chars, offsets, 0)
+    assign = np.random.default_rng(4).integers(0, 5, s.n)
+    runs = cpu_runs(s, assign, 5)
+    perm, lcp = gpu_merge(s, runs)
+    assert_merge_parity(s, runs, perm, lcp)
+    import torch
+    torch.cuda.empty_cache()
