@@ -203,6 +203,40 @@ def test_config2_full():
     assert np.array_equal(np.sort(sub)[sp], sub)
 
 
+def _prefix_sets():
+    rng = np.random.default_rng(44)
+
+    def tails(n, lo, hi, alpha=b"abc"):
+        a = np.frombuffer(alpha, np.uint8)
+        return [bytes(a[rng.integers(0, len(a), int(rng.integers(lo, hi + 1)))]) for _ in range(n)]
+
+    pre = bytes(rng.integers(97, 123, 45).astype(np.uint8))
+    sets = {}
+    sets["long_prefix"] = [pre + t for t in tails(50_000, 0, 10)]
+    sets["short_prefix_dups"] = [pre[:12] + t for t in tails(30_000, 0, 2)]
+    sets["outlier_first"] = [b"zzzzzzzzzz"] + [pre + t for t in tails(30_000, 1, 6)]
+    groups = [bytes(rng.integers(97, 123, int(rng.integers(9, 60))).astype(np.uint8)) for _ in range(5)]
+    sets["hosts"] = [groups[int(rng.integers(0, 5))] + b"/" + t for t in tails(60_000, 0, 12, b"abcdefgh")]
+    sets["prefix_ends"] = [pre[:int(rng.integers(8, 45))] for _ in range(20_000)]  # prefixes of one string
+    return sets
+
+
+PREFIX_SETS = _prefix_sets()
+
+
+@pytest.mark.parametrize("cap", [0, 20, 40])
+@pytest.mark.parametrize("opts", [dict(big_threshold=2048), dict(big_threshold=4096, classifier=2), dict()])
+@pytest.mark.parametrize("name", sorted(PREFIX_SETS))
+def test_subsets_with_long_common_prefixes(name, opts, cap):
+    """Multi-block subsets whose whole sample is one key (steps that walk a
+    common prefix 8 characters at a time) against the oracle: prefixes of
+    45 and 12 characters, strings ending inside them, caps inside them, a
+    first member that differs, several hosts."""
+    s = from_strings(PREFIX_SETS[name], max_len=cap)
+    p, l = gpu_sort(s, **opts)
+    assert_parity(s, p, l)
+
+
 def test_offsets_above_4gib():
     """Strings beyond byte 2^32 of the character buffer.  A record keeps only
     the low 32 bits of its string's offset, so a set with larger offsets takes
