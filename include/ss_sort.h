@@ -236,7 +236,10 @@ size_t ss_merge_workspace_size(const ss_run* runs, uint32_t num_runs, uint32_t s
  *            the suffixes out_sa[j-1] and out_sa[j].
  * Synchronous: waits for the result (the host reads the number of unsorted
  * suffixes after each round).  Device memory of about 63 bytes per text
- * character is taken from the stream-ordered pool for the call.  Returns
+ * character is taken from the stream-ordered pool for the call, plus, with
+ * an LCP output, 4 bytes per character for every round (the names of each
+ * round: an LCP above initial_depth is found by descending through them,
+ * O(rounds + initial_depth / 256) per entry however long it is).  Returns
  * SS_ERR_TOO_LARGE for n >= 2^32 - 2, SS_ERR_INVALID for NULL pointers or
  * initial_depth > 2^20. */
 ss_status ss_suffix_array(const uint8_t* text, uint64_t n, uint32_t* out_sa, uint32_t* out_lcp,

@@ -715,6 +715,16 @@ ss_status ss_suffix_array(const uint8_t* text, uint64_t n, uint32_t* out_sa, uin
   x.gs = gs;
   x.flag = flag;
   x.h = h0;
+  // with an LCP output: the names after every round, for the LCPs above h0
+  std::vector<uint32_t*> snaps;
+  auto snapshot = [&]() {
+    if (!out_lcp) return true;
+    if (snaps.size() >= kSaMaxSnaps) return false;  // cannot happen: at most 33 rounds for n < 2^32
+    uint32_t* q = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void**>(&q), n * 4, st) != cudaSuccess) return false;
+    snaps.push_back(q);
+    return cudaMemcpyAsync(q, isa, n * 4, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+  };
   bool ok = sa_launch(SaKernel::kIota, x, grid_for(n), st, hook) == cudaSuccess;
   // round 0: the string sort by the first h0 characters
   if (ok) {
@@ -728,7 +738,7 @@ ss_status ss_suffix_array(const uint8_t* text, uint64_t n, uint32_t* out_sa, uin
     ok = sa_launch(SaKernel::kHeads0, x, grid_for(n), st, hook) == cudaSuccess &&
          sa_scan_max(gs, n, tot, st, hook) == cudaSuccess &&
          sa_launch(SaKernel::kName0, x, grid_for(n), st, hook) == cudaSuccess &&
-         sa_scan_sum(flag, n, tot, st, hook) == cudaSuccess && read_u32(flag + n - 1, &M);
+         sa_scan_sum(flag, n, tot, st, hook) == cudaSuccess && read_u32(flag + n - 1, &M) && snapshot();
     SaArgs c = x;
     c.vals = nullptr;
     c.out = cpos[0];
@@ -757,7 +767,7 @@ ss_status ss_suffix_array(const uint8_t* text, uint64_t n, uint32_t* out_sa, uin
       ok = sa_launch(SaKernel::kApply, r, grid_for(M), st, hook) == cudaSuccess &&
            sa_scan_max(gs, M, tot, st, hook) == cudaSuccess &&
            sa_launch(SaKernel::kRename, r, grid_for(M), st, hook) == cudaSuccess &&
-           sa_scan_sum(flag, M, tot, st, hook) == cudaSuccess && read_u32(flag + M - 1, &M2);
+           sa_scan_sum(flag, M, tot, st, hook) == cudaSuccess && read_u32(flag + M - 1, &M2) && snapshot();
     if (ok && M2) {
       SaArgs c = r;
       c.n = M;
@@ -774,6 +784,8 @@ ss_status ss_suffix_array(const uint8_t* text, uint64_t n, uint32_t* out_sa, uin
     // LCPs of at least h0: list those positions, then one warp each
     SaArgs l = x;
     l.lcp_out = out_lcp;
+    l.snaps.count = (uint32_t)snaps.size();
+    for (size_t k = 0; k < snaps.size(); ++k) l.snaps.p[k] = snaps[k];
     uint32_t L = 0;
     ok = sa_launch(SaKernel::kLongFlags, l, grid_for(n), st, hook) == cudaSuccess &&
          sa_scan_sum(flag, n, tot, st, hook) == cudaSuccess && read_u32(flag + n - 1, &L);
@@ -787,6 +799,7 @@ ss_status ss_suffix_array(const uint8_t* text, uint64_t n, uint32_t* out_sa, uin
            sa_launch(SaKernel::kLcp, l, grid_for(32ull * L), st, hook) == cudaSuccess;
     }
   }
+  for (uint32_t* q : snaps) cudaFreeAsync(q, st);
   cudaFreeAsync(ws, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && ok) ok = false;
   collect_profile();

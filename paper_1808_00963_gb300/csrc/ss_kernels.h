@@ -117,6 +117,14 @@ cudaError_t launch_layout_check(const uint8_t* chars, uint64_t chars_len, const 
 // Suffix array by prefix doubling (ss_sa.cu).
 enum class SaKernel { kIota, kHeads0, kName0, kCompact, kEncode, kApply, kRename, kLongFlags, kLcp };
 
+// Name arrays of the suffixes after each round (ISA^{h0 2^k}, k = 0..count-1),
+// kept for the LCPs above h0.
+constexpr uint32_t kSaMaxSnaps = 40;
+struct SaSnaps {
+  const uint32_t* p[kSaMaxSnaps];
+  uint32_t count;
+};
+
 struct SaArgs {
   const uint8_t* text = nullptr;
   uint64_t n = 0;             // strings the kernel runs over (suffixes, or members M)
@@ -137,6 +145,7 @@ struct SaArgs {
   uint64_t* eoff = nullptr;
   const uint32_t* perm2 = nullptr;
   const uint32_t* lcp2 = nullptr;
+  SaSnaps snaps{};
 };
 
 size_t sa_scan_totals(uint64_t n);  // entries of the scan's tile-total buffer

@@ -203,18 +203,25 @@ __global__ void k_sa_rename(const uint32_t* member, const uint32_t* perm2, const
 // Final LCP array.  Entries below h0 come from the first sort (they sit at the
 // starts of h0-groups, whose members were only permuted inside the group);
 // k_sa_long_flags marks the others (flag 1 for j >= 1 with lcp >= h0) and
-// k_sa_lcp gives each of them one warp that compares the two suffixes from
-// depth h0 on, 256 characters per step: lane k compares the 8-character
-// windows at h + 8k, and the first lane that sees a difference (or the end of
-// the shorter suffix) gives the LCP.  A suffix at a has n - a characters, so
-// no lane reads past the text.
+// k_sa_lcp gives each of them one warp.  Its first lane climbs down the name
+// arrays of the rounds: suffixes a and b share their first h0 2^k characters
+// from t on iff their names after round k at a + t and b + t agree, so taking
+// each k from the last round down whenever they agree gives the largest
+// multiple t of h0 with a and b equal in their first t characters (names do
+// not agree past the end of the text).  The warp then compares the two
+// suffixes from t on, 256 characters per step: lane k compares the
+// 8-character windows at h + 8k, and the first lane that sees a difference
+// (or the end of the shorter suffix) gives the LCP, fewer than h0 characters
+// on.  The work per entry is O(rounds + h0 / 256) however long the LCP (a
+// direct comparison from h0 took seconds on periodic texts).  A suffix at a
+// has n - a characters, so no lane reads past the text.
 __global__ void k_sa_long_flags(const uint32_t* lcp, uint32_t n, uint32_t h0, uint32_t* flag) {
   for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
     flag[j] = (j > 0 && lcp[j] >= h0) ? 1u : 0u;
 }
 
 __global__ void k_sa_lcp(const uint8_t* text, const uint32_t* sa, uint32_t n, uint32_t h0, const uint32_t* pos,
-                         uint32_t count, uint32_t* lcp) {
+                         uint32_t count, uint32_t* lcp, SaSnaps sn) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warps = gridDim.x * (blockDim.x / 32);
   for (uint32_t w = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); w < count; w += warps) {
@@ -222,7 +229,16 @@ __global__ void k_sa_lcp(const uint8_t* text, const uint32_t* sa, uint32_t n, ui
     const uint64_t a = sa[j - 1], b = sa[j];
     const uint64_t la = n - a, lb = n - b;
     const uint64_t lmin = la < lb ? la : lb;
-    uint64_t h = h0;
+    unsigned long long t = h0;
+    if (lane == 0 && sn.count) {
+      t = 0;
+      for (int k = (int)sn.count - 1; k >= 0; --k) {
+        const uint32_t* nm = sn.p[k];
+        if (a + t < n && b + t < n && nm[a + t] == nm[b + t]) t += (unsigned long long)h0 << k;
+      }
+    }
+    t = __shfl_sync(0xFFFFFFFFu, t, 0);
+    uint64_t h = t;
     uint64_t result = 0;
     while (true) {
       const uint64_t d = h + 8ull * lane;
@@ -302,7 +318,7 @@ cudaError_t sa_launch(SaKernel k, const SaArgs& x, uint32_t grid, cudaStream_t s
       break;
     case SaKernel::kLcp:
       hook.run("sa_lcp", [&] {
-        k_sa_lcp<<<grid, 256, 0, st>>>(x.text, x.sa, (uint32_t)x.n, x.h, x.cpos, x.M, x.lcp_out);
+        k_sa_lcp<<<grid, 256, 0, st>>>(x.text, x.sa, (uint32_t)x.n, x.h, x.cpos, x.M, x.lcp_out, x.snaps);
       });
       break;
   }

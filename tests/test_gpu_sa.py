@@ -94,3 +94,55 @@ def test_suffix_array_full_size_dna():
     sa, lcp = gpu_sa(text)
     chars = np.frombuffer(text + b"\0", np.uint8).copy()
     assert oracle.check(chars, np.arange(len(text), dtype=np.uint64), sa, lcp, 0) == -1
+
+
+REPEAT_TEXTS = {
+    "period997": bytes(np.tile(np.random.default_rng(31).integers(97, 100, 997).astype(np.uint8), 20)),
+    "unary": b"a" * 12_000,
+    "fibonacci": fibonacci(15_000),
+}
+_REPEAT_WANT = {}
+
+
+@pytest.mark.parametrize("depth", [0, 8, 1000])
+@pytest.mark.parametrize("name", sorted(REPEAT_TEXTS))
+def test_long_repeats_exact(name, depth):
+    """Periodic texts whose LCPs run far beyond the first sort's depth (the
+    LCPs above it come from the rounds' names), element by element."""
+    text = REPEAT_TEXTS[name]
+    if name not in _REPEAT_WANT:
+        _REPEAT_WANT[name] = oracle.suffix_array(text)
+    want_sa, want_lcp = _REPEAT_WANT[name]
+    sa, lcp = gpu_sa(text, initial_depth=depth)
+    assert np.array_equal(sa, want_sa)
+    assert np.array_equal(lcp, want_lcp)
+
+
+def test_unary_closed_form():
+    """a^n: the suffixes in order of length, shortest first, and LCP[j] = j
+    (the closed form, at a size whose LCP sum no direct comparison could
+    afford: 2^21 characters, 21 doubling rounds)."""
+    n = 1 << 21
+    sa, lcp = gpu_sa(b"a" * n)
+    assert np.array_equal(sa, np.arange(n - 1, -1, -1, dtype=np.uint32))
+    assert np.array_equal(lcp, np.arange(n, dtype=np.uint32))
+
+
+def test_periodic_large_sampled():
+    """A 2M-character text of one 40000-character block repeated: adjacent
+    suffix pairs checked one by one on a sample (order and exact LCP by
+    direct comparison), plus the permutation property."""
+    rng = np.random.default_rng(32)
+    text = bytes(np.tile(rng.integers(97, 101, 40_000).astype(np.uint8), 50))
+    n = len(text)
+    sa, lcp = gpu_sa(text)
+    assert np.array_equal(np.sort(sa), np.arange(n, dtype=np.uint32))
+    tb = np.frombuffer(text, np.uint8)
+    for j in rng.choice(np.arange(1, n), 300, replace=False):
+        a, b, h = int(sa[j - 1]), int(sa[j]), int(lcp[j])
+        m = min(n - a, n - b)
+        assert h <= m and np.array_equal(tb[a:a + h], tb[b:b + h])
+        if h < m:
+            assert tb[a + h] < tb[b + h]
+        else:
+            assert n - a < n - b  # a proper prefix comes first
