@@ -26,13 +26,78 @@ __device__ __forceinline__ uint64_t cnt_base(const GenTask& g) {
   return ((uint64_t)g.cnt_base_hi << 32) | g.cnt_base_lo;
 }
 
+// Prefix jump.  A step sees 8 characters, so a subset whose strings share a
+// long prefix (many URLs of one site, repeated records) would be moved once
+// for every 8 shared characters.  When the whole sample of a subset is one key
+// without a terminator, the sampling block measures how far the sampled
+// strings agree with one of them over the next kPjWindows windows; if they
+// agree beyond 32 characters, the classification measures the same for every
+// string, and if the whole subset then falls into that key's equality bucket,
+// the bucket continues at depth + the smallest agreement instead of depth + 8.
+// Any depth up to the subset's common prefix is correct: the jump only skips
+// work, and the check on the sample keeps its cost away from subsets that
+// share only the key.
+constexpr int kPjWindows = 8;        // 64 characters
+constexpr uint32_t kPjMinSample = 32;  // sampled agreement that turns the check on
+
 // Splitters of one multi-block task, with the jump table of its tree (filled
-// for the jump-table classifier only).
+// for the jump-table classifier only) and the prefix-jump state.
 template <int LOGV>
 struct BigSplitters {
   Splitters<LOGV> sp;
   uint16_t jump[kJumpSize];
+  uint64_t pj_ref;  // offset of the reference string (the first sampled one)
+  uint32_t pj_on;   // check every string of the subset
+  uint32_t pj_lcp;  // smallest agreement with the reference from the depth (atomicMin)
 };
+
+// The kPjWindows windows of a string from depth h (no terminator before h).
+// load_windows reads only the 4 KiB block holding byte h; the windows it
+// leaves open lie past that block, and since the string has not ended before
+// them, they are read one at a time (load_cache reads the next block only
+// while the string continues).  This happens for about 1 string in 64.
+__device__ __forceinline__ void load_pj_windows(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
+                                                uint64_t (&w)[kPjWindows]) {
+  const uint32_t nw = load_windows<kPjWindows>(chars, off, h, cap, w);
+  for (uint32_t j = nw; j < (uint32_t)kPjWindows; ++j) {
+    w[j] = load_cache(chars, off, h + 8 * j, cap);
+    if (has_nul(w[j])) break;  // the later windows stay 0
+  }
+}
+
+// How many characters from the depth a string shares with the reference.
+__device__ __forceinline__ uint32_t window_lcp(const uint64_t (&w)[kPjWindows], const uint64_t* ref) {
+#pragma unroll
+  for (int j = 0; j < kPjWindows; ++j) {
+    if (w[j] != ref[j]) return 8u * j + lcp8(w[j], ref[j]);
+    if (has_nul(w[j])) return 8u * j + nnz_prefix(w[j]);
+  }
+  return 8u * kPjWindows;
+}
+
+// Smallest agreement with ref over the strings of records [0, n) taken by this
+// block's threads (pos(i) gives the record of item i), reduced over the block.
+template <typename Pos>
+__device__ uint32_t block_min_agreement(const SortCtx& c, const Rec* recs, const SetDesc& sd, uint32_t wide,
+                                        uint32_t depth, uint32_t items, Pos&& pos, const uint64_t* ref,
+                                        unsigned long long& bytes) {
+  __shared__ uint32_t bmin;
+  if (threadIdx.x == 0) bmin = 0xFFFFFFFFu;
+  __syncthreads();
+  uint32_t mn = 0xFFFFFFFFu;
+  for (uint32_t i = threadIdx.x; i < items; i += blockDim.x) {
+    const Rec r = load_rec(recs + pos(i));
+    uint64_t w[kPjWindows];
+    load_pj_windows(sd.chars, rec_offset(sd, wide, r.idx, r.off), depth, sd.cap, w);
+    mn = min(mn, window_lcp(w, ref));
+    bytes += 8 + 8 * kPjWindows;  // the record's index and offset, the windows
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+  if ((threadIdx.x & 31u) == 0 && mn != 0xFFFFFFFFu) atomicMin(&bmin, mn);
+  __syncthreads();
+  return bmin;
+}
 
 template <int LOGV>
 __global__ void __launch_bounds__(kBlock) k_big_sample(SortCtx c, const GenTask* __restrict__ gt,
@@ -47,6 +112,34 @@ __global__ void __launch_bounds__(kBlock) k_big_sample(SortCtx c, const GenTask*
   uint64_t* dst = reinterpret_cast<uint64_t*>(&out[blockIdx.x].sp);
   for (uint32_t i = threadIdx.x; i < sizeof(Splitters<LOGV>) / 8; i += blockDim.x) dst[i] = src[i];
   unsigned long long bytes = threadIdx.x == 0 ? Geo<LOGV>::S * 8ull + sizeof(Splitters<LOGV>) : 0ull;
+  // prefix jump: a one-key sample whose strings agree beyond kPjMinSample
+  // characters turns on the check of the whole subset
+  const SetDesc sd = c.sets[task_set(g.t)];
+  const uint64_t k0 = bs.sample[0];  // the sorted sample
+  const bool one_key = !sd.dna && k0 == bs.sample[Geo<LOGV>::S - 1] && !key_end(k0, 0u);
+  uint32_t on = 0;
+  uint64_t ref_off = 0;
+  if (one_key) {  // uniform over the block
+    const uint64_t hseed = mix64(c.seed ^ ((uint64_t)g.t.begin << 20) ^ g.t.depth);
+    auto sample_pos = [&](uint32_t i) { return (uint32_t)(((mix64(hseed + i) >> 32) * (uint64_t)g.t.len) >> 32); };
+    const uint32_t wide = c.wide[task_set(g.t)];
+    __shared__ uint64_t ref[kPjWindows];
+    const Rec r0 = load_rec(recs + sample_pos(0));
+    ref_off = rec_offset(sd, wide, r0.idx, r0.off);
+    if (threadIdx.x == 0) {
+      uint64_t w[kPjWindows];
+      load_pj_windows(sd.chars, ref_off, g.t.depth, sd.cap, w);
+      for (int j = 0; j < kPjWindows; ++j) ref[j] = w[j];
+    }
+    __syncthreads();
+    const uint32_t agree = block_min_agreement(c, recs, sd, wide, g.t.depth, Geo<LOGV>::S, sample_pos, ref, bytes);
+    on = agree > kPjMinSample && agree != 0xFFFFFFFFu ? 1u : 0u;
+  }
+  if (threadIdx.x == 0) {
+    out[blockIdx.x].pj_on = on;
+    out[blockIdx.x].pj_lcp = 0xFFFFFFFFu;
+    out[blockIdx.x].pj_ref = ref_off;
+  }
   if (c.classifier == kClassifyUIJ) {
     for (uint32_t p = threadIdx.x; p < kJumpSize; p += blockDim.x)
       out[blockIdx.x].jump[p] = (uint16_t)jump_entry<LOGV>(p, sp.tree);
@@ -92,6 +185,20 @@ __global__ void __launch_bounds__(kBlock) k_big_classify(SortCtx c, const GenTas
   // per record: cache 8 read + bucket index 2 written; per tile: K counters written
   unsigned long long bytes = 10ull * mine;
   if (threadIdx.x == 0) bytes += 4ull * Gm::K;
+  if (spl[s_g].pj_on) {  // prefix jump: every string's agreement with the reference
+    const SetDesc sd = c.sets[task_set(g.t)];
+    __shared__ uint64_t ref[kPjWindows];
+    if (threadIdx.x == 0) {
+      uint64_t w[kPjWindows];
+      load_pj_windows(sd.chars, spl[s_g].pj_ref, g.t.depth, sd.cap, w);
+      for (int j = 0; j < kPjWindows; ++j) ref[j] = w[j];
+    }
+    __syncthreads();
+    const uint32_t bmin = block_min_agreement(c, recs, sd, c.wide[task_set(g.t)], g.t.depth, tl,
+                                              [](uint32_t i) { return i; }, ref, bytes);
+    if (threadIdx.x == 0 && bmin != 0xFFFFFFFFu)
+      atomicMin(&const_cast<BigSplitters<LOGV>*>(spl)[s_g].pj_lcp, bmin);
+  }
   account(c, kKBigClassify, bytes);
 }
 
@@ -116,6 +223,12 @@ __global__ void __launch_bounds__(kBlock) k_big_emit(SortCtx c, const GenTask* _
     uint32_t desc = kFin;
     if (size) {
       desc = bucket_desc<LOGV>(b, size, g.t.depth, sp, sd.dna);
+      // prefix jump: the whole subset is the key's equality bucket, and every
+      // string agrees with the reference for pj_lcp characters from the depth
+      if (spl[blockIdx.x].pj_on && (b & 1u) && size == g.t.len && !(desc & kFin)) {
+        const uint32_t J = spl[blockIdx.x].pj_lcp;
+        if (J > 8u && J != 0xFFFFFFFFu) desc = g.t.depth + J;
+      }
       emit_bucket(c, sd, g.t, s, size, desc, next_big);
     }
     gdesc[(uint64_t)blockIdx.x * Gm::KP + b] = desc;

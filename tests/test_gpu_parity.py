@@ -218,6 +218,9 @@ def _prefix_sets():
     groups = [bytes(rng.integers(97, 123, int(rng.integers(9, 60))).astype(np.uint8)) for _ in range(5)]
     sets["hosts"] = [groups[int(rng.integers(0, 5))] + b"/" + t for t in tails(60_000, 0, 12, b"abcdefgh")]
     sets["prefix_ends"] = [pre[:int(rng.integers(8, 45))] for _ in range(20_000)]  # prefixes of one string
+    pre300 = bytes(rng.integers(97, 123, 300).astype(np.uint8))
+    sets["prefix300"] = [pre300 + t for t in tails(20_000, 0, 6)]  # several jumps in a row
+    sets["identical150"] = [pre300[:150]] * 12_000 + [pre300[:149]] * 50
     return sets
 
 
@@ -228,10 +231,12 @@ PREFIX_SETS = _prefix_sets()
 @pytest.mark.parametrize("opts", [dict(big_threshold=2048), dict(big_threshold=4096, classifier=2), dict()])
 @pytest.mark.parametrize("name", sorted(PREFIX_SETS))
 def test_subsets_with_long_common_prefixes(name, opts, cap):
-    """Multi-block subsets whose whole sample is one key (steps that walk a
-    common prefix 8 characters at a time) against the oracle: prefixes of
-    45 and 12 characters, strings ending inside them, caps inside them, a
-    first member that differs, several hosts."""
+    """Multi-block subsets whose whole sample is one key, where the step
+    jumps over the subset's common prefix (up to 64 characters at a time)
+    instead of walking it 8 characters per step, against the oracle:
+    prefixes of 12, 45 and 300 characters, identical strings, strings ending
+    inside the prefix, caps inside it, a first member that differs (no jump),
+    several hosts."""
     s = from_strings(PREFIX_SETS[name], max_len=cap)
     p, l = gpu_sort(s, **opts)
     assert_parity(s, p, l)
