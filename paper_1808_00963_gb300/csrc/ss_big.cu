@@ -29,16 +29,18 @@ __device__ __forceinline__ uint64_t cnt_base(const GenTask& g) {
 // Prefix jump.  A step sees 8 characters, so a subset whose strings share a
 // long prefix (many URLs of one site, repeated records) would be moved once
 // for every 8 shared characters.  When the whole sample of a subset is one key
-// without a terminator, the sampling block measures how far the sampled
-// strings agree with one of them over the next kPjWindows windows; if they
-// agree beyond 32 characters, the classification measures the same for every
-// string, and if the whole subset then falls into that key's equality bucket,
+// without a terminator, the sampling block measures how far 64 of the
+// sampled strings agree with one of them over the next kPjWindows windows;
+// if they agree beyond 32 characters, the classification measures the same
+// for every string, and if the whole subset then falls into that key's
+// equality bucket,
 // the bucket continues at depth + the smallest agreement instead of depth + 8.
 // Any depth up to the subset's common prefix is correct: the jump only skips
 // work, and the check on the sample keeps its cost away from subsets that
 // share only the key.
 constexpr int kPjWindows = 8;        // 64 characters
 constexpr uint32_t kPjMinSample = 32;  // sampled agreement that turns the check on
+constexpr uint32_t kPjSampleChecks = 64;  // sampled strings compared (of the sample's S)
 
 // Splitters of one multi-block task, with the jump table of its tree (filled
 // for the jump-table classifier only) and the prefix-jump state.
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(kBlock) k_big_sample(SortCtx c, const GenTask*
       for (int j = 0; j < kPjWindows; ++j) ref[j] = w[j];
     }
     __syncthreads();
-    const uint32_t agree = block_min_agreement(c, recs, sd, wide, g.t.depth, Geo<LOGV>::S, sample_pos, ref, bytes);
+    const uint32_t agree = block_min_agreement(c, recs, sd, wide, g.t.depth, kPjSampleChecks, sample_pos, ref, bytes);
     on = agree > kPjMinSample && agree != 0xFFFFFFFFu ? 1u : 0u;
   }
   if (threadIdx.x == 0) {
