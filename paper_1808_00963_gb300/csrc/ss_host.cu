@@ -321,6 +321,10 @@ static cudaError_t zero_fill(void* dst, size_t bytes, cudaStream_t st, const Lau
   return cudaMemsetAsync(dst, 0, bytes, st);
 }
 
+// Writes a set descriptor into the workspace: a kernel parameter, so the host
+// neither stages it nor waits for a copy before enqueuing the sort.
+__global__ void k_set_desc(SetDesc* dst, SetDesc v) { *dst = v; }
+
 // Enqueues everything after the set descriptors are in place.
 static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o, const DevInfo& dev,
                           bool big, cudaStream_t st) {
@@ -438,14 +442,8 @@ static ss_status sort_device(const uint8_t* chars, const uint64_t* offsets, uint
     }
     SetDesc sd{chars, offsets, perm, lcp, (uint32_t)n, o.cap, 0, dna};
     ss_status r = SS_OK;
-    if (t_up.reserve(sizeof(SetDesc)) != SS_OK) r = SS_ERR_OOM;
-    if (r == SS_OK) {
-      // t_up is reused by the step planner: wait for this small copy first
-      std::memcpy(t_up.p, &sd, sizeof(sd));
-      if (small_h2d(ws + L.sets, t_up.p, sizeof(sd), st, LaunchHook{st}) != cudaSuccess ||
-          cudaStreamSynchronize(st) != cudaSuccess)
-        r = SS_ERR_CUDA;
-    }
+    LaunchHook{st}.run("init", [&] { k_set_desc<<<1, 1, 0, st>>>(reinterpret_cast<SetDesc*>(ws + L.sets), sd); });
+    if (cudaGetLastError() != cudaSuccess) r = SS_ERR_CUDA;
     SortCtx ctx = make_ctx(ws, L, 1, (uint32_t)n, o, big);
     ctx.dna = dna;
     if (r == SS_OK) r = run_sort(ws, L, ctx, o, dev, big, st);
@@ -1201,8 +1199,6 @@ constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static uint8_t* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
 
-// Writes the set descriptor into the scratch (no host staging buffer needed).
-__global__ void k_noalloc_set(SetDesc* dst, SetDesc v) { *dst = v; }
 
 // Device address of the scratch on the current device, looked up once per
 // device.  Host code only ever passes this address to kernels: the name
@@ -1242,7 +1238,7 @@ extern "C" ss_status ss_sort_noalloc(const uint8_t* chars, const uint64_t* offse
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const SetDesc sd{chars, offsets, out_perm, out_lcp, (uint32_t)n, o.cap, 0, 0};
   const LaunchHook hook{st};
-  hook.run("init", [&] { k_noalloc_set<<<1, 1, 0, st>>>(reinterpret_cast<SetDesc*>(ws + L.sets), sd); });
+  hook.run("init", [&] { k_set_desc<<<1, 1, 0, st>>>(reinterpret_cast<SetDesc*>(ws + L.sets), sd); });
   if (cudaGetLastError() != cudaSuccess) return SS_ERR_CUDA;
   // run_sort clears the control words and the queue flags, the only scratch
   // that must start at zero; everything else is written before it is read.
