@@ -180,12 +180,39 @@ def d_and_l(lcp: np.ndarray):
     return int(np.maximum(h, nxt).sum() + h.size), int(h[1:].sum())
 
 
-def source_hash():
+# translation unit of each kernel whose DRAM traffic is recorded in
+# profiles/traffic.json
+KERNEL_UNITS = {"big_scatter": "ss_big.cu", "merge_round": "ss_merge.cu"}
+
+
+def kernel_sources(kernel: str | None):
+    """The files a kernel is compiled from: its translation unit and the
+    headers it includes (transitively); all library sources when unknown."""
     d = os.path.join(ROOT, "paper_1808_00963_gb300", "csrc")
+    unit = KERNEL_UNITS.get(kernel or "")
+    if unit is None:
+        return sorted(os.path.join(d, f) for f in os.listdir(d))
+    seen, todo = [], [os.path.join(d, unit)]
+    while todo:
+        f = os.path.normpath(todo.pop())
+        if f in seen or not os.path.exists(f):
+            continue
+        seen.append(f)
+        with open(f) as fh:
+            for line in fh:
+                line = line.strip()
+                if line.startswith('#include "'):
+                    todo.append(os.path.join(os.path.dirname(f), line.split('"')[1]))
+    return sorted(seen)
+
+
+def source_hash(kernel: str | None = None):
+    """Hash of the sources a kernel is compiled from (a recorded traffic
+    figure is used only while they are unchanged)."""
     hsh = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        with open(os.path.join(d, f), "rb") as fh:
-            hsh.update(f.encode() + fh.read())
+    for f in kernel_sources(kernel):
+        with open(f, "rb") as fh:
+            hsh.update(os.path.basename(f).encode() + fh.read())
     return hsh.hexdigest()[:16]
 
 
@@ -209,7 +236,7 @@ def ncu_traffic(kernel: str, config: str):
     except Exception:
         return None
     e = t.get(config, {}).get(kernel)
-    if not e or e.get("source_hash") != source_hash():
+    if not e or e.get("source_hash") != source_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 

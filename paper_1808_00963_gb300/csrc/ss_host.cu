@@ -874,6 +874,13 @@ struct CopyLane {
   cudaStream_t cs = nullptr;
   cudaEvent_t start = nullptr, offs = nullptr, chunk[kMaxHostParts] = {};
   bool ready = false;
+  ~CopyLane() {
+    for (cudaEvent_t e : chunk)
+      if (e) cudaEventDestroy(e);
+    if (offs) cudaEventDestroy(offs);
+    if (start) cudaEventDestroy(start);
+    if (cs) cudaStreamDestroy(cs);
+  }
 };
 static thread_local std::map<int, CopyLane> t_lanes;
 
