@@ -333,6 +333,23 @@ def pin_prefix_doubling_names(lib):
     assert sa2.tolist() == [int(x) for x in g["perm"].split()][1:]   # without the empty suffix
 
 
+def pin_suffix_array_closed_forms(lib):
+    """Texts whose suffix and LCP arrays have a closed form: a^n (suffixes by
+    length, shortest first; LCP[j] = j) and (ab)^k (the a-suffixes by length,
+    LCPs 0, 2, 4, ...; then the b-suffixes by length, LCPs 0, 1, 3, 5, ...)."""
+    for n in (1, 2, 7, 40):
+        sa, lcp = oracle.suffix_array(b"a" * n, lib=lib)
+        assert sa.tolist() == list(range(n - 1, -1, -1)), n
+        assert lcp.tolist() == list(range(n)), n
+    for k in (1, 2, 5, 17):
+        n = 2 * k
+        sa, lcp = oracle.suffix_array(b"ab" * k, lib=lib)
+        want_sa = list(range(n - 2, -1, -2)) + list(range(n - 1, 0, -2))
+        want_lcp = [2 * m for m in range(k)] + [0] + [2 * m - 1 for m in range(1, k)]
+        assert sa.tolist() == want_sa, k
+        assert lcp.tolist() == want_lcp, k
+
+
 ALL_PINS = [pin_paper_suffix_examples, pin_word_list_ties, pin_lemma_2_1, pin_brute_force,
             pin_library_sort, pin_checker, pin_cache, pin_bucket_and_tree, pin_distinguishing,
-            pin_lemma_4_1, pin_merge, pin_prefix_doubling_names]
+            pin_lemma_4_1, pin_merge, pin_prefix_doubling_names, pin_suffix_array_closed_forms]
