@@ -155,3 +155,20 @@ def test_sort_dna_argument_checks(lib):
     assert lib.ss_sort_dna(dummy, 100, dummy, 5, dummy, None, ctypes.byref(bad), None) == 1
     if not _has_gpu():
         assert lib.ss_sort_dna(dummy, 100, dummy, 5, dummy, None, ctypes.byref(o), None) == 7
+
+
+def test_sort_host_argument_checks(lib):
+    o = ss.make_options()
+    dummy = ctypes.c_void_p(4096)
+    assert lib.ss_sort_host(None, 0, None, 0, None, None, ctypes.byref(o), None) == 0            # n = 0
+    assert lib.ss_sort_host(dummy, 100, dummy, 1 << 32, dummy, None, ctypes.byref(o), None) == 4
+    assert lib.ss_sort_host(None, 100, dummy, 5, dummy, None, ctypes.byref(o), None) == 1        # NULL chars
+    assert lib.ss_sort_host(dummy, 0, dummy, 5, dummy, None, ctypes.byref(o), None) == 1         # no characters
+    assert lib.ss_sort_host(dummy, 100, None, 5, dummy, None, ctypes.byref(o), None) == 1        # NULL offsets
+    assert lib.ss_sort_host(dummy, 100, dummy, 5, None, None, ctypes.byref(o), None) == 1        # NULL output
+    for parts in (3, 5, 32):  # host_parts: a power of two up to 16
+        bad = ss.make_options(host_parts=parts)
+        assert lib.ss_sort_host(dummy, 100, dummy, 5, dummy, None, ctypes.byref(bad), None) == 1, parts
+    if not _has_gpu():
+        good = ss.make_options(host_parts=4)
+        assert lib.ss_sort_host(dummy, 100, dummy, 5, dummy, None, ctypes.byref(good), None) == 7
