@@ -4,7 +4,12 @@
 Default workload (one GPU): the plain sort of 20 M synthetic URL-like strings
 (~59 B mean, Zipf hosts, 1.19 GB of characters), inputs resident in HBM.  One
 step = one complete sort through the C-ABI (ss_sort_ex), producing the
-permutation and the LCP array.  Prints one JSON line.
+permutation and the LCP array.  Prints one JSON line.  On one GPU that line
+also carries the metric's batched and served parts: "batched" (configuration
+4: 4096 sets as one batch replayed from a CUDA graph against 4096 plain calls)
+and "served" (configuration 5: 2000 Poisson requests through the serving loop
+against a one-at-a-time plain loop, p50/p99 latency and throughput), each
+with its parity check (--no-batched leaves them out).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                   [--config c1|c2|c3|c4|c5|m2|s3|d3]
@@ -479,6 +484,18 @@ def run_ours(args, ws, rank, local):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(s, args.config)
 
+    # the metric's other two parts, on the same GPU: the batched form
+    # (configuration 4) and the served form (configuration 5), each against
+    # per-request plain calls
+    batched = served = None
+    if args.config == "c2" and ws == 1 and not args.no_batched:
+        del work, perm, lcp
+        torch.cuda.empty_cache()
+        batched = batch_workload(args.sets, 3, min(args.steps, 20))
+        torch.cuda.empty_cache()
+        served = served_workload(args.requests)
+        torch.cuda.empty_cache()
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "strings/s", "n_gpus": ws, "steps": args.steps,
@@ -497,6 +514,9 @@ def run_ours(args, ws, rank, local):
             "clocks": clocks,
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 4), "alg_bytes": v[2]} for k, v in stats.items()},
         }
+        if batched is not None:
+            line["batched"] = batched
+            line["served"] = served
         print(json.dumps(line), flush=True)
 
 
@@ -775,15 +795,16 @@ def run_sa(args, ws, rank, local):
 
 # ---- batched workload (configuration 4) ---------------------------------------------------------
 
-def run_batch(args, ws, rank, local):
-    """4096 independent string sets (log-uniform 100..200k strings, random /
-    URL / DNA generators) sorted as one batch (one persistent launch sequence,
-    captured into a CUDA graph) against 4096 plain calls on one stream."""
+def batch_workload(num: int, warmup: int, steps: int):
+    """Configuration 4: num independent string sets (log-uniform 100..200k
+    strings, random / URL / DNA generators) sorted as one batch (one launch
+    sequence, captured into a CUDA graph) against num plain calls on one
+    stream.  The plain calls write their own buffers, which must equal the
+    batch's.  Returns a dict for the JSON line."""
     import torch
 
     import paper_1808_00963_gb300 as ss
     ss.load()
-    num = args.sets
     specs = gen.batch_specs(num, 4)
     sets = [gen.make_set(k, n, sd) for (k, n, sd) in specs]
     chars, offsets, cbase, first, mls = gen.concat(sets)
@@ -802,7 +823,7 @@ def run_batch(args, ws, rank, local):
     batch = ss.Batch(descs, **tuned)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(max(warmup, 3)):
             batch.run()
     batch.status(stream)
     graph = torch.cuda.CUDAGraph()
@@ -820,40 +841,66 @@ def run_batch(args, ws, rank, local):
         return e0.elapsed_time(e1) / k
 
     launches0 = ss.launch_count()
-    ms_graph = timed(graph.replay, args.steps)
+    ms_graph = timed(graph.replay, steps)
     batch.status()
     with torch.cuda.stream(stream):
-        ms_nograph = timed(lambda: batch.run(stream), args.steps)
+        ms_nograph = timed(lambda: batch.run(stream), steps)
     batch.status(stream)
     launches = ss.launch_count() - launches0
-    # plain: one ss_sort call per set, one after another
+    # the batch's result (every set) before the plain loop runs
+    batch_perm, batch_lcp = perm_d.clone(), lcp_d.clone()
+    # plain: one ss_sort call per set, one after another, into its own buffers
+    plain_perm = torch.full_like(perm_d, -1)
+    plain_lcp = torch.full_like(lcp_d, -1)
     lat = []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for (ch, of, ml, p, l) in descs:
+    for i, (ch, of, ml, _, _) in enumerate(descs):
         a = time.perf_counter()
-        ss.sort(ch, of, max_len=ml, out=(p, l))
+        lo, hi = int(first[i]), int(first[i]) + sets[i].n
+        ss.sort(ch, of, max_len=ml, out=(plain_perm[lo:hi], plain_lcp[lo:hi]))
+        torch.cuda.current_stream().synchronize()
         lat.append((time.perf_counter() - a) * 1e3)
     plain_s = time.perf_counter() - t0
     lat = np.array(lat)
-    line = {
-        "metric": METRIC, "value": total / (ms_graph / 1e3), "unit": "strings/s", "n_gpus": ws,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_graph, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": f"batched: {num} sets, log-uniform 100-200k strings, random/URL/DNA generators",
-                   "sets": num, "strings": total, "chars_bytes": int(chars.shape[0]),
-                   "per_step": "one batch (all sets sorted, perm + LCP), CUDA graph replay",
-                   "options": tuned or "compiled defaults", "options_source": "autotuner table (tuned.json)"},
-        "batched_graph": {"ms": ms_graph, "strings_per_s": total / (ms_graph / 1e3),
-                          "latency_ms_every_set": ms_graph},
-        "batched_no_graph": {"ms": ms_nograph, "strings_per_s": total / (ms_nograph / 1e3)},
+    # parity: the batch (graph replay) and the plain calls give identical arrays
+    if not (torch.equal(batch_perm, plain_perm) and torch.equal(batch_lcp, plain_lcp)):
+        raise SystemExit("batched and plain results differ")
+    done = np.cumsum(lat)
+    return {
+        "workload": f"batched: {num} sets, log-uniform 100-200k strings, random/URL/DNA generators",
+        "sets": num, "strings": total, "chars_bytes": int(chars.shape[0]),
+        "options": tuned or "compiled defaults",
+        "graph": {"ms": ms_graph, "strings_per_s": total / (ms_graph / 1e3),
+                  "completion_ms_p50": ms_graph, "completion_ms_p99": ms_graph},
+        "no_graph": {"ms": ms_nograph, "strings_per_s": total / (ms_nograph / 1e3)},
         "plain_loop": {"ms": plain_s * 1e3, "strings_per_s": total / plain_s,
                        "per_call_ms_p50": float(np.percentile(lat, 50)),
                        "per_call_ms_p99": float(np.percentile(lat, 99)),
-                       "completion_ms_p50": float(np.percentile(np.cumsum(lat), 50)),
-                       "completion_ms_p99": float(np.percentile(np.cumsum(lat), 99))},
+                       "completion_ms_p50": float(np.percentile(done, 50)),
+                       "completion_ms_p99": float(np.percentile(done, 99))},
         "speedup_vs_plain": plain_s * 1e3 / ms_graph,
+        "p99_completion_speedup": float(np.percentile(done, 99)) / ms_graph,
+        "parity": ("checked: every set's permutation and LCP array from the batch equal those of its own "
+                   "ss_sort call"),
         "gpu_launches": launches,
+    }
+
+
+def run_batch(args, ws, rank, local):
+    """Configuration 4 on its own line (value: batch strings/s, graph replay)."""
+    r = batch_workload(args.sets, args.warmup, args.steps)
+    line = {
+        "metric": METRIC, "value": r["graph"]["strings_per_s"], "unit": "strings/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": r["graph"]["ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": r["workload"], "sets": r["sets"], "strings": r["strings"],
+                   "chars_bytes": r["chars_bytes"],
+                   "per_step": "one batch (all sets sorted, perm + LCP), CUDA graph replay",
+                   "options": r["options"], "options_source": "autotuner table (tuned.json)"},
+        "batched_graph": r["graph"], "batched_no_graph": r["no_graph"], "plain_loop": r["plain_loop"],
+        "speedup_vs_plain": r["speedup_vs_plain"], "p99_completion_speedup": r["p99_completion_speedup"],
+        "parity": r["parity"], "gpu_launches": r["gpu_launches"],
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -861,23 +908,55 @@ def run_batch(args, ws, rank, local):
 
 # ---- served workload (configuration 5) ----------------------------------------------------------
 
-def run_served(args, ws, rank, local):
-    """A Poisson stream of sort requests (log-uniform 1k..5M strings, mixed
-    generators) replayed against the serving loop (admission by a 30 GB HBM
-    budget, continuous batching on 4 streams) and against a one-at-a-time
-    plain loop on the same trace.  Arrival rate: 0.8 x the plain loop's
-    measured capacity."""
+SERVED_POOL = 150
+
+
+def served_trace(num_requests: int, pool_size: int = SERVED_POOL):
+    """Configuration 5: a Poisson trace of num_requests sort requests (unit
+    rate; log-uniform 1k..5M strings, mixed generators).  Request j replays
+    set j mod pool_size of a pool generated from the trace's first pool_size
+    entries, so that 2000 requests need no more host memory than 150."""
+    spec = gen.trace(num_requests, 5, 1.0, smin=1000, smax=5_000_000)
+    pool = [gen.make_set(kind, size, sd) for (_, kind, size, sd) in spec[:pool_size]]
+    return spec, pool
+
+
+def served_workload(num_requests: int, pool_size: int = SERVED_POOL, check: bool = True):
+    """The served form against a one-at-a-time plain loop on the same trace
+    (arrival rate 0.8 x the plain loop's measured capacity), plus both at
+    saturation (every request available at once).  With check, every pool set
+    is first sorted alone (ss_sort) and verified by the oracle's O(n + D)
+    checker, and a last served pass at saturation compares every request's
+    result with its set's.  Returns a dict for the JSON line."""
+    import dataclasses
+
     import torch
 
     import paper_1808_00963_gb300 as ss
     from paper_1808_00963_gb300.serve import Server, make_request
     ss.load()
-    spec = gen.trace(args.requests, 5, 1.0, smin=1000, smax=5_000_000)
+    spec, pool = served_trace(num_requests, pool_size)
+    base = [make_request(i, 0.0, st.chars, st.offsets, st.max_len) for i, st in enumerate(pool)]
     reqs = []
-    for i, (t, kind, size, sd) in enumerate(spec):
-        st = gen.make_set(kind, size, sd)
-        reqs.append(make_request(i, t, st.chars, st.offsets, st.max_len))
+    for j, (t, _, _, _) in enumerate(spec):
+        r = dataclasses.replace(base[j % len(pool)], rid=j, arrival=t, meta={"pool": j % len(pool)})
+        reqs.append(r)
     total = sum(r.n for r in reqs)
+
+    expected = None
+    if check:
+        import oracle
+        expected = []
+        for st in pool:
+            ch = torch.from_numpy(st.chars).cuda()
+            of = torch.from_numpy(st.offsets.view(np.int64)).cuda()
+            p, l = ss.sort(ch, of, max_len=st.max_len)
+            hp, hl = p.cpu().numpy().view(np.uint32), l.cpu().numpy().view(np.uint32)
+            r = oracle.check(st.chars, st.offsets, hp, hl, st.max_len)
+            if r != -1:
+                raise SystemExit(f"served pool set {st.name}: oracle check fails at {r}")
+            expected.append((hp, hl))
+        del ch, of, p, l
 
     def reset(arrivals):
         for r, a in zip(reqs, arrivals):
@@ -897,21 +976,55 @@ def run_served(args, ws, rank, local):
     plain = Server(mode="plain").run(reqs)
     reset(arrivals)
     served = Server(mode="served", budget_bytes=30 << 30, streams=4).run(reqs)
-    line = {
-        "metric": METRIC, "value": served["strings_per_s"], "unit": "strings/s", "n_gpus": ws, "steps": 1,
-        "warmup": 1, "ms_per_step": served["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": f"served: Poisson stream of {len(reqs)} sort requests, log-uniform 1k-5M strings, "
-                               "mixed generators, 30 GB HBM budget",
-                   "requests": len(reqs), "strings": total, "offered_load": 0.8,
-                   "plain_capacity_strings_per_s": capacity, "arrival_rate_per_s": rate,
-                   "per_step": "the whole trace; latency = completion (results on the host) - arrival"},
+    parity = "not checked"
+    if check:
+        checked = [0]
+
+        def verify(r):
+            hp, hl = expected[r.meta["pool"]]
+            if not (np.array_equal(r.perm.numpy().view(np.uint32), hp)
+                    and np.array_equal(r.lcp.numpy().view(np.uint32), hl)):
+                raise RuntimeError(f"request {r.rid}: served result differs from its set sorted alone")
+            checked[0] += 1
+
+        reset([0.0] * len(reqs))
+        v = Server(mode="served", budget_bytes=30 << 30, streams=4, on_done=verify).run(reqs)
+        if v["errors"] or checked[0] != len(reqs):
+            raise SystemExit(f"served parity check failed: {v['errors'][:3]}")
+        parity = (f"checked: all {len(reqs)} served results equal their set sorted alone; the {len(pool)} pool "
+                  "sets pass the oracle's O(n + D) checker")
+    return {
+        "workload": (f"served: Poisson stream of {len(reqs)} sort requests, log-uniform 1k-5M strings, mixed "
+                     f"generators, 30 GB HBM budget (a pool of {len(pool)} generated sets replayed)"),
+        "requests": len(reqs), "strings": total, "offered_load": 0.8,
+        "plain_capacity_strings_per_s": capacity, "arrival_rate_per_s": rate,
         "served": served, "plain": plain,
         "saturated": {"plain_strings_per_s": capacity, "served_strings_per_s": cap_served["strings_per_s"],
                       "served_mean_batch": cap_served["mean_batch"],
                       "throughput_ratio": cap_served["strings_per_s"] / capacity},
         "p99_speedup": plain["latency_ms_p99"] / served["latency_ms_p99"],
         "throughput_ratio": served["strings_per_s"] / plain["strings_per_s"],
+        "parity": parity,
+    }
+
+
+def run_served(args, ws, rank, local):
+    """A Poisson stream of sort requests (log-uniform 1k..5M strings, mixed
+    generators) replayed against the serving loop (admission by a 30 GB HBM
+    budget, continuous batching on 4 streams) and against a one-at-a-time
+    plain loop on the same trace.  Arrival rate: 0.8 x the plain loop's
+    measured capacity."""
+    r = served_workload(args.requests)
+    served = r["served"]
+    line = {
+        "metric": METRIC, "value": served["strings_per_s"], "unit": "strings/s", "n_gpus": ws, "steps": 1,
+        "warmup": 1, "ms_per_step": served["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": r["workload"], "requests": r["requests"], "strings": r["strings"],
+                   "offered_load": 0.8, "plain_capacity_strings_per_s": r["plain_capacity_strings_per_s"],
+                   "arrival_rate_per_s": r["arrival_rate_per_s"],
+                   "per_step": "the whole trace; latency = completion (results on the host) - arrival"},
+        **{k: r[k] for k in ("served", "plain", "saturated", "p99_speedup", "throughput_ratio", "parity")},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -924,10 +1037,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "m2", "s3", "d3"])
-    ap.add_argument("--requests", type=int, default=150, help="number of requests (c5)")
+    ap.add_argument("--requests", type=int, default=2000, help="number of requests (c5)")
     ap.add_argument("--sets", type=int, default=4096, help="number of sets (c4)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="leave out the batched (configuration 4) and served (configuration 5) parts of the "
+                         "default line")
     ap.add_argument("--n", type=int, default=None, help="reduced string count (c2 and m2; profiler captures)")
     args = ap.parse_args()
     if args.impl == "reference":

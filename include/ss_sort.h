@@ -31,8 +31,8 @@
  * stream).  All work is enqueued on it.
  *
  * Errors: argument errors are returned at once, before any work is enqueued.
- * Errors found on the device (queue overflow, a bounded wait that expired,
- * a string longer than 2^30 bytes) are latched in a device status word and
+ * Errors found on the device (a bounded wait that expired, a string longer
+ * than 2^30 bytes) are latched in a device status word and
  * returned by the call that waits for the result (ss_sort, ss_sort_ex,
  * ss_sort_host, ss_sort_batch) or by ss_batch_status().
  */
@@ -53,7 +53,9 @@ typedef enum ss_status {
     SS_ERR_CUDA = 3,        /* a CUDA runtime call failed                         */
     SS_ERR_TOO_LARGE = 4,   /* n >= 2^32, or a string of 2^30 bytes or more       */
     SS_ERR_TIMEOUT = 5,     /* a device-side bounded wait expired                 */
-    SS_ERR_QUEUE_FULL = 6,  /* a device task list overflowed its capacity         */
+    SS_ERR_QUEUE_FULL = 6,  /* a device task list overflowed its capacity (every
+                               list is sized by an exact bound on its tasks, so
+                               this reports an internal inconsistency)        */
     SS_ERR_NO_DEVICE = 7    /* no CUDA device, or the device is not sm_103        */
 } ss_status;
 
@@ -95,6 +97,18 @@ typedef struct ss_options {
                                   merges cost more than the overlap saves);
                                   else a power of two <= 16.  Ignored
                                   elsewhere.                                  */
+    uint32_t wait_limit_us;    /* bound, in microseconds, on every device-side
+                                  wait of the sort (a block waiting for the
+                                  work queue's next task or for a queue slot
+                                  to be read); when one expires the sort
+                                  stops with SS_ERR_TIMEOUT and its outputs
+                                  are undefined (default 30 s).  Lets a caller
+                                  that must not hang detect a stalled device
+                                  sooner.  An idle block of the work-queue
+                                  kernel waits while other blocks split the
+                                  subsets that will feed it, so a limit far
+                                  below the sort's own duration stops ordinary
+                                  sorts too.                                  */
     void* workspace;           /* optional caller-owned device workspace of at
                                   least ss_workspace_size() bytes, 256-byte
                                   aligned.  NULL: the library allocates

@@ -88,6 +88,7 @@ class Options(ctypes.Structure):
         ("seed", ctypes.c_uint32),
         ("classifier", ctypes.c_uint32),
         ("host_parts", ctypes.c_uint32),
+        ("wait_limit_us", ctypes.c_uint32),
         ("workspace", ctypes.c_void_p),
         ("workspace_bytes", ctypes.c_size_t),
     ]
@@ -241,6 +242,12 @@ def sort(chars, offsets, max_len: int = 0, with_lcp: bool = True, out=None, stre
                             ctypes.c_void_p(perm.data_ptr()), lp, ctypes.byref(o), _stream_ptr(stream))
         _check(rc, "ss_sort_ex")
     return perm, lcp
+
+
+def stream_status(stream=None):
+    """ss_stream_status: wait for the stream and raise SortError if a sort
+    enqueued on it latched a device-side error."""
+    _check(load().ss_stream_status(_stream_ptr(stream)), "ss_stream_status")
 
 
 def distinguishing(chars, offsets, perm, lcp, max_len: int = 0, stream=None):

@@ -141,6 +141,9 @@ static ss_status device_info(DevInfo& out) {
 // ---- options and workspace layout -----------------------------------------------------
 
 // Defaults come from the autotuner's table (ss_tuned.h).
+// Bound on every device-side wait of a sort (queue slots, flags).
+constexpr uint64_t kDefaultWaitNs = 30ull * 1000 * 1000 * 1000;
+
 struct Opts {
   uint32_t cap = kNoCap;
   int logv = SS_TUNED_SPLITTERS_LOG2;           // single-block steps
@@ -150,8 +153,8 @@ struct Opts {
   uint32_t big_thr = SS_TUNED_BIG_THRESHOLD;
   uint32_t seed = 0x5EED;
   uint32_t classifier = 0;
-  uint32_t mq_factor = 16;
   uint32_t host_parts = 0;  // ss_sort_host: 0 = automatic
+  uint64_t wait_ns = kDefaultWaitNs;
 };
 
 constexpr uint32_t kMaxHostParts = 16;
@@ -184,6 +187,7 @@ static ss_status resolve_opts(const ss_options* o, Opts& r) {
   if (o->classifier > 3) return SS_ERR_INVALID;
   r.classifier = o->classifier;
   if (o->workspace && ((uintptr_t)o->workspace & 255)) return SS_ERR_INVALID;
+  if (o->wait_limit_us) r.wait_ns = (uint64_t)o->wait_limit_us * 1000;
   return SS_OK;
 }
 
@@ -212,7 +216,9 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
   L.cap_big = big ? (uint32_t)(M / ((uint64_t)o.big_thr + 1) + 2) : 0;
-  L.cap_mq = (uint32_t)std::min<uint64_t>(0xFFFFFFF0ull, std::max<uint64_t>(4096, o.mq_factor * (M / o.cutoff) + 1024));
+  // the work queue's ring: more slots than disjoint subsets of > cutoff
+  // records can exist, so it never overflows (see WorkQueue)
+  L.cap_mq = (uint32_t)std::max<uint64_t>(4096, M / ((uint64_t)o.cutoff + 1) + 1024);
   // warp tasks: subsets and runs the block sort passes on, disjoint and of at
   // least 2 strings (<= M/2), then as many deferred runs (<= M/2)
   L.cap_sw = (uint32_t)(M / 2 + 1);
@@ -257,7 +263,7 @@ static SortCtx make_ctx(uint8_t* ws, const Layout& L, uint32_t num_sets, uint32_
   c.big[0] = TaskList{reinterpret_cast<Task*>(ws + L.big0), ctrl + kCBig0, L.cap_big};
   c.big[1] = TaskList{reinterpret_cast<Task*>(ws + L.big1), ctrl + kCBig1, L.cap_big};
   c.mq = WorkQueue{reinterpret_cast<Task*>(ws + L.mq_items), reinterpret_cast<uint32_t*>(ws + L.mq_ready),
-                   ctrl + kCHead, ctrl + kCTail, ctrl + kCPending, L.cap_mq, 1u};
+                   ctrl + kCHead, ctrl + kCTail, ctrl + kCPending, L.cap_mq};
   c.small_warp = TaskList{reinterpret_cast<Task*>(ws + L.sw_items), ctrl + kCSmallW, L.cap_sw};
   c.small_deep = TaskList{reinterpret_cast<Task*>(ws + L.sw_items) + L.cap_sw, ctrl + kCSmallD, L.cap_sw};
   c.small_cta = TaskList{reinterpret_cast<Task*>(ws + L.sc_items), ctrl + kCSmallC, L.cap_sc};
@@ -267,6 +273,7 @@ static SortCtx make_ctx(uint8_t* ws, const Layout& L, uint32_t num_sets, uint32_
   c.seed = o.seed;
   c.classifier = o.classifier;
   c.big_cur = 0;
+  c.wait_ns = o.wait_ns;
   return c;
 }
 
@@ -429,37 +436,30 @@ static ss_status sort_device(const uint8_t* chars, const uint64_t* offsets, uint
   DevInfo dev;
   if ((s = device_info(dev)) != SS_OK) return s;
   const bool big = n > o.big_thr;
-  for (int attempt = 0; attempt < 3; ++attempt) {
-    const Layout L = make_layout(n, 1, o, big);
-    uint8_t* ws = nullptr;
-    bool owned = false;
-    if (opt && opt->workspace) {
-      if (opt->workspace_bytes < L.total) return SS_ERR_INVALID;
-      ws = static_cast<uint8_t*>(opt->workspace);
-    } else {
-      if (cudaMallocAsync(reinterpret_cast<void**>(&ws), L.total, st) != cudaSuccess) return SS_ERR_OOM;
-      owned = true;
-    }
-    SetDesc sd{chars, offsets, perm, lcp, (uint32_t)n, o.cap, 0, dna};
-    ss_status r = SS_OK;
-    LaunchHook{st}.run("init", [&] { k_set_desc<<<1, 1, 0, st>>>(reinterpret_cast<SetDesc*>(ws + L.sets), sd); });
-    if (cudaGetLastError() != cudaSuccess) r = SS_ERR_CUDA;
-    SortCtx ctx = make_ctx(ws, L, 1, (uint32_t)n, o, big);
-    ctx.dna = dna;
-    if (r == SS_OK) r = run_sort(ws, L, ctx, o, dev, big, st);
-    ss_status r2 = read_status(ws, L, st);
-    if (r == SS_OK) r = r2;
-    if (owned) {
-      cudaFreeAsync(ws, st);
-      cudaStreamSynchronize(st);
-    }
-    if (r == SS_ERR_QUEUE_FULL && !(opt && opt->workspace)) {
-      o.mq_factor *= 8;
-      continue;
-    }
-    return r;
+  const Layout L = make_layout(n, 1, o, big);
+  uint8_t* ws = nullptr;
+  bool owned = false;
+  if (opt && opt->workspace) {
+    if (opt->workspace_bytes < L.total) return SS_ERR_INVALID;
+    ws = static_cast<uint8_t*>(opt->workspace);
+  } else {
+    if (cudaMallocAsync(reinterpret_cast<void**>(&ws), L.total, st) != cudaSuccess) return SS_ERR_OOM;
+    owned = true;
   }
-  return SS_ERR_QUEUE_FULL;
+  SetDesc sd{chars, offsets, perm, lcp, (uint32_t)n, o.cap, 0, dna};
+  ss_status r = SS_OK;
+  LaunchHook{st}.run("init", [&] { k_set_desc<<<1, 1, 0, st>>>(reinterpret_cast<SetDesc*>(ws + L.sets), sd); });
+  if (cudaGetLastError() != cudaSuccess) r = SS_ERR_CUDA;
+  SortCtx ctx = make_ctx(ws, L, 1, (uint32_t)n, o, big);
+  ctx.dna = dna;
+  if (r == SS_OK) r = run_sort(ws, L, ctx, o, dev, big, st);
+  ss_status r2 = read_status(ws, L, st);
+  if (r == SS_OK) r = r2;
+  if (owned) {
+    cudaFreeAsync(ws, st);
+    cudaStreamSynchronize(st);
+  }
+  return r;
 }
 
 }  // namespace ss

@@ -84,16 +84,21 @@ struct TaskList {
   uint32_t cap;
 };
 
-// Work queue of the persistent kernel: a linear array of slots; a slot is
-// ready once its flag equals the epoch of the current sort.
+// Work queue of the persistent kernel: a ring of cap slots.  Push number k
+// (and claim number k) uses slot k mod cap in lap k / cap; the slot's flag is
+// 2 * lap while it waits for that lap's task, 2 * lap + 1 once the task is in,
+// and the claim sets it to 2 * lap + 2 after reading it.  Flags start at 0.
+// The tasks pushed and not yet claimed are disjoint subsets of more than
+// small_cutoff records, so a ring of more than (records / (small_cutoff + 1))
+// slots never holds a slot's next task before its last one has been claimed:
+// the queue cannot overflow, however many times subsets are requeued.
 struct WorkQueue {
   Task* items;
   uint32_t* ready;
-  uint32_t* head;      // next slot to claim
-  uint32_t* tail;      // next slot to fill
+  uint32_t* head;      // claims so far
+  uint32_t* tail;      // pushes so far
   uint32_t* pending;   // tasks pushed and not yet finished
   uint32_t cap;
-  uint32_t epoch;
 };
 
 // Kernel classes for launch statistics and algorithmic-byte accounting.
@@ -122,6 +127,7 @@ struct SortCtx {
   uint32_t classifier;     // classification variant (kClassifyUI / UIC / E)
   uint32_t big_cur;        // which big[] list the current step reads
   uint32_t dna;            // every set holds 3-bit character codes (SetDesc::dna)
+  uint64_t wait_ns;        // bound on every device-side wait (then kStTimeout)
 };
 
 // ---------------------------------------------------------------------------
@@ -382,25 +388,43 @@ __device__ __forceinline__ void list_push(const TaskList& l, const Task& t, uint
   else latch_status(status, kStQueueFull);
 }
 
-// Push to the work queue of the persistent kernel.
-__device__ __forceinline__ void queue_push(const WorkQueue& q, const Task& t, uint32_t* status) {
+// Waits (bounded by wait_ns) until *flag == want; false if the wait expired.
+__device__ __forceinline__ bool wait_flag(const uint32_t* flag, uint32_t want, uint64_t wait_ns) {
+  volatile const uint32_t* f = flag;
+  if (*f == want) return true;
+  const uint64_t t0 = globaltimer_ns();
+  uint32_t ns = 32;
+  while (*f != want) {
+    if (globaltimer_ns() - t0 > wait_ns) return false;
+    __nanosleep(ns);
+    ns = ns < 1024 ? ns * 2 : ns;
+  }
+  return true;
+}
+
+// Push to the work queue of the persistent kernel.  The slot's previous task
+// has always been claimed already (see WorkQueue); the wait only covers the
+// moment between that claim and its read.
+__device__ __forceinline__ void queue_push(const WorkQueue& q, const Task& t, uint32_t* status, uint64_t wait_ns) {
   atomicAdd(q.pending, 1u);
-  uint32_t slot = atomicAdd(q.tail, 1u);
-  if (slot >= q.cap) {
-    latch_status(status, kStQueueFull);
+  const uint32_t k = atomicAdd(q.tail, 1u);
+  const uint32_t slot = k % q.cap, lap = k / q.cap;
+  if (!wait_flag(q.ready + slot, 2 * lap, wait_ns)) {
+    latch_status(status, kStTimeout);
     atomicSub(q.pending, 1u);
     return;
   }
+  __threadfence();
   q.items[slot] = t;
   __threadfence();
-  atomicExch(q.ready + slot, q.epoch);
+  atomicExch(q.ready + slot, 2 * lap + 1);
 }
 
 // Route a new subset (len >= 2, not finished) to the list that handles its size.
 __device__ __forceinline__ void route_task(const SortCtx& c, const Task& t, uint32_t next_big) {
   if (t.depth > kMaxDepth) { latch_status(c.status, kStTooDeep); return; }
   if (c.big_enabled && t.len > c.big_threshold) list_push(c.big[next_big], t, c.status);
-  else if (t.len > c.small_cutoff) queue_push(c.mq, t, c.status);
+  else if (t.len > c.small_cutoff) queue_push(c.mq, t, c.status, c.wait_ns);
   else if (t.len > 32) list_push(c.small_cta, t, c.status);
   else list_push(c.small_warp, t, c.status);
 }

@@ -8,16 +8,14 @@
 //
 // Termination: `pending` counts tasks pushed and not yet finished; a block
 // that finds its claimed slot empty exits once pending is 0.  Every wait is
-// bounded by a wall-clock budget, after which the status word is latched and
-// the block exits.
+// bounded (SortCtx::wait_ns of wall-clock time), after which the status word
+// is latched and the block exits.
 #include "ss_kernels.h"
 #include "ss_step.cuh"
 
 namespace ss {
 
 namespace {
-
-constexpr uint64_t kQueueWaitNs = 30ull * 1000 * 1000 * 1000;
 
 template <int LOGV>
 struct QueueSmem {
@@ -36,23 +34,26 @@ struct QueueSmem {
   uint32_t got;
 };
 
-// Claims the next slot; waits (bounded) until it is filled or all work is done.
-__device__ bool claim_task(const WorkQueue& q, Task* out, uint32_t* status) {
-  const uint32_t slot = atomicAdd(q.head, 1u);
-  if (slot >= q.cap) return false;
+// Claims the next task: waits (bounded) until it has been pushed, or until all
+// work is done (no task pending: nothing can be pushed any more).
+__device__ bool claim_task(const WorkQueue& q, Task* out, uint32_t* status, uint64_t wait_ns) {
+  const uint32_t k = atomicAdd(q.head, 1u);
+  const uint32_t slot = k % q.cap, lap = k / q.cap;
   const uint64_t t0 = globaltimer_ns();
   uint32_t ns = 64;
   volatile uint32_t* ready = q.ready;
   volatile uint32_t* pending = q.pending;
   while (true) {
-    if (ready[slot] == q.epoch) {
+    if (ready[slot] == 2 * lap + 1) {
       __threadfence();
       const uint4 v = __ldcg(reinterpret_cast<const uint4*>(q.items + slot));
       *out = Task{v.x, v.y, v.z, v.w};
+      __threadfence();  // the task is read before the slot is handed to the next lap
+      atomicExch(q.ready + slot, 2 * lap + 2);
       return true;
     }
     if (*pending == 0) return false;
-    if (globaltimer_ns() - t0 > kQueueWaitNs) {
+    if (globaltimer_ns() - t0 > wait_ns) {
       latch_status(status, kStTimeout);
       return false;
     }
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_queue(SortCtx c, uint32_t R) {
   QueueSmem<LOGV>& s = *reinterpret_cast<QueueSmem<LOGV>*>(smem);
   unsigned long long bytes = 0;
   while (true) {
-    if (threadIdx.x == 0) s.got = claim_task(c.mq, &s.task, c.status) ? 1u : 0u;
+    if (threadIdx.x == 0) s.got = claim_task(c.mq, &s.task, c.status, c.wait_ns) ? 1u : 0u;
     __syncthreads();
     if (!s.got) break;
     const Task t = s.task;

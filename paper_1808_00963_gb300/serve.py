@@ -64,8 +64,12 @@ def make_request(rid: int, arrival: float, chars: np.ndarray, offsets: np.ndarra
 
 class Server:
     def __init__(self, budget_bytes: int = 30 << 30, streams: int = 4, batch_max: int = 512,
-                 big: int = 65536, mode: str = "served"):
+                 big: int = 65536, mode: str = "served", on_done=None):
+        """on_done(request), if given, is called by the worker for every
+        completed request once its results are on the host (for checks; it
+        delays that worker's next batch)."""
         assert mode in ("served", "plain")
+        self.on_done = on_done
         self.budget = budget_bytes
         self.nstreams = 1 if mode == "plain" else streams
         self.batch_max = 1 if mode == "plain" else batch_max
@@ -127,6 +131,9 @@ class Server:
             for r in group:
                 r.done = now
             del dev
+        if self.on_done is not None:
+            for r in group:
+                self.on_done(r)
 
     def _worker(self, t0):
         import torch

@@ -123,3 +123,70 @@ def test_sort_batch_convenience():
     rc = lib.ss_sort_batch(arr, len(dev), None, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 0
     _check(sets, dev)
+
+
+def _config4_device(sets):
+    """The sets of configuration 4 in one device buffer (as bench.py lays them
+    out): descriptors of (chars from the set's base, offsets, cap, perm, lcp)."""
+    import torch
+    chars, offsets, cbase, first, mls = gen.concat(sets)
+    chars_d = torch.from_numpy(chars).cuda()
+    offs_d = torch.from_numpy(offsets.view(np.int64)).cuda()
+    total = int(offsets.shape[0])
+    perm_d = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+    lcp_d = torch.full((total,), -1, dtype=torch.int32, device="cuda")
+    descs, spans = [], []
+    for i, st in enumerate(sets):
+        a, b = int(first[i]), int(first[i]) + st.n
+        descs.append((chars_d[int(cbase[i]):], offs_d[a:b], int(mls[i]), perm_d[a:b], lcp_d[a:b]))
+        spans.append((a, b))
+    return descs, spans, perm_d, lcp_d
+
+
+@pytest.mark.slow
+def test_config4_full_batch_direct_and_graph_replay():
+    """Configuration 4 at its stated size: 4096 sets of 100..200k strings
+    (random, URL-like and DNA-suffix generators; 110 M strings), sorted as one
+    batch directly and by CUDA-graph replay.  Every set is checked by the
+    oracle's complete O(n + D) checker (permutation, order, ties by index,
+    every LCP), the replay must reproduce the direct run exactly, and 100 sets
+    (the 50 largest and 50 others) must equal single ss_sort calls."""
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    from paper_1808_00963_gb300 import tune
+    sets = gen.batch_sets(4096, 4)
+    descs, spans, perm_d, lcp_d = _config4_device(sets)
+    tuned = {k: v for k, v in tune.options_for(batched=True).items() if v}
+    b = ss.Batch(descs, **tuned)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b.run()
+    b.status(stream)
+    perm_h = perm_d.cpu().numpy().view(np.uint32)
+    lcp_h = lcp_d.cpu().numpy().view(np.uint32)
+    for s, (a, e) in zip(sets, spans):
+        r = oracle.check(s.chars, s.offsets, perm_h[a:e], lcp_h[a:e], s.max_len)
+        assert r == -1, f"{s.name}: oracle check fails at position {r}"
+    first_p, first_l = perm_d.clone(), lcp_d.clone()
+    perm_d.fill_(-1)
+    lcp_d.fill_(-1)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        b.run()
+    for _ in range(2):
+        perm_d.fill_(-1)
+        lcp_d.fill_(-1)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        b.status()
+        assert torch.equal(perm_d, first_p) and torch.equal(lcp_d, first_l)
+    b.close()
+    by_size = sorted(range(len(sets)), key=lambda i: -sets[i].n)
+    pick = by_size[:50] + by_size[50::(len(sets) - 50) // 50][:50]
+    for i in pick:
+        ch, of, ml, _, _ = descs[i]
+        a, e = spans[i]
+        p1, l1 = ss.sort(ch, of, max_len=ml)
+        assert torch.equal(p1, first_p[a:e]) and torch.equal(l1, first_l[a:e]), sets[i].name

@@ -56,3 +56,30 @@ def test_admission_respects_budget():
     assert not stats["errors"]
     assert srv.free == budget
     assert all(r.done >= r.start >= 0 for r in reqs)
+
+
+@pytest.mark.slow
+def test_served_requests_up_to_millions_of_strings():
+    """Requests of configuration 5's size range (log-uniform 1k..5M strings,
+    mixed generators), many at once so that batches and requests sorted alone
+    on the multi-block path overlap on four streams: every result passes the
+    oracle's O(n + D) checker and equals the request sorted alone."""
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    from paper_1808_00963_gb300.serve import Server
+    reqs = _requests(24, 17, rate=400.0, smax=5_000_000)
+    assert max(r.n for r in reqs) > 1_000_000
+    srv = Server(budget_bytes=16 << 30, streams=4, mode="served")
+    stats = srv.run(reqs)
+    assert not stats["errors"]
+    for r in reqs:
+        s = r.meta["set"]
+        gp = r.perm.numpy().view(np.uint32)
+        gl = r.lcp.numpy().view(np.uint32)
+        assert oracle.check(s.chars, s.offsets, gp, gl, s.max_len) == -1, r.rid
+        ch = torch.from_numpy(s.chars).cuda()
+        of = torch.from_numpy(s.offsets.view(np.int64)).cuda()
+        p, l = ss.sort(ch, of, max_len=s.max_len)
+        assert np.array_equal(p.cpu().numpy().view(np.uint32), gp)
+        assert np.array_equal(l.cpu().numpy().view(np.uint32), gl)

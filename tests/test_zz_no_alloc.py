@@ -56,3 +56,35 @@ def test_noalloc_rejects_more_than_its_limit():
     lib = ss.load()
     dummy = ctypes.c_void_p(256)
     assert lib.ss_sort_noalloc(dummy, dummy, ss.NOALLOC_MAX_STRINGS + 1, 0, dummy, dummy, None) == 4
+
+
+def test_noalloc_subsets_requeued_many_times():
+    """63 groups of 1040 identical 600-byte strings (65 520 strings): every
+    group is an equality bucket above the small cutoff that goes back to the
+    work queue 75 times, 4725 queue pushes in all.  The queue is a ring sized
+    by the number of disjoint subsets it can hold, so this fits the fixed
+    scratch; the result equals ss_sort_ex's, on two calls in a row."""
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    ss.build()
+    lib = ss.load()
+    groups = []
+    for g in range(63):
+        body = bytes((ord("a") + (g * 7 + k) % 26) for k in range(592))
+        groups.append(b"%08d" % (g * 7919 % 100000) + body)
+    strs = [groups[i % 63] for i in range(63 * 1040)]
+    chars_np = np.frombuffer(b"".join(x + b"\0" for x in strs), np.uint8).copy()
+    offs_np = np.arange(len(strs), dtype=np.uint64) * 601
+    s = gen.StringSet(chars_np, offs_np)
+    chars, offsets = _dev(s)
+    want_p, want_l = ss.sort(chars, offsets)
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for _ in range(2):
+        p = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
+        l = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
+        rc = lib.ss_sort_noalloc(ctypes.c_void_p(chars.data_ptr()), ctypes.c_void_p(offsets.data_ptr()), s.n,
+                                 0, ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(l.data_ptr()), stream)
+        assert rc == 0, ss.STATUS.get(rc, rc)
+        assert torch.equal(p, want_p)
+        assert torch.equal(l, want_l)
