@@ -402,8 +402,8 @@ def run_ours(args, ws, rank, local):
 
     dna = args.config == "d3"
 
-    def step():
-        ss.sort(chars, offsets, max_len=s.max_len, out=(perm, lcp), dna=dna, **opts)
+    def step():  # enqueues one sort (ss_sort_ex is asynchronous); the status is read after the timed steps
+        ss.sort(chars, offsets, max_len=s.max_len, out=(perm, lcp), dna=dna, sync=dna, **opts)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -424,11 +424,13 @@ def run_ours(args, ws, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     sampler.mark(t_start, time.perf_counter())
+    ss.stream_status(stream)  # raises if a timed sort latched a device-side error
     launches = ss.launch_count() - launches0
     barrier(ws)
     clocks = sampler.stop()
     ms, value = weak_scaling_value(e0.elapsed_time(e1), ws, n, args.steps)
     stats, prof_ms = profiled_pass(step, args.steps, stream)
+    ss.stream_status(stream)
     d_rate = ws * D * args.steps / (ms / 1e3)
 
     # roofline of the dominant kernel (largest share of device time)

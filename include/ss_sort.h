@@ -32,9 +32,13 @@
  *
  * Errors: argument errors are returned at once, before any work is enqueued.
  * Errors found on the device (a bounded wait that expired, a string longer
- * than 2^30 bytes) are latched in a device status word and
- * returned by the call that waits for the result (ss_sort, ss_sort_ex,
- * ss_sort_host, ss_sort_batch) or by ss_batch_status().
+ * than 2^30 bytes) are latched in a device status word: the asynchronous
+ * calls (ss_sort, ss_sort_ex, ss_batch_run) leave it to be read by
+ * ss_stream_status() / ss_batch_status(); the calls that wait for their
+ * result (ss_sort_host, ss_sort_dna, ss_suffix_array, ss_sort_batch,
+ * ss_sort_noalloc) return it.  A sort that latched a device-side error writes
+ * the identity permutation and zero LCPs to its outputs, so that no index in
+ * them is out of range.
  */
 #ifndef SS_SORT_H
 #define SS_SORT_H
@@ -102,7 +106,8 @@ typedef struct ss_options {
                                   work queue's next task or for a queue slot
                                   to be read); when one expires the sort
                                   stops with SS_ERR_TIMEOUT and its outputs
-                                  are undefined (default 30 s).  Lets a caller
+                                  hold the identity permutation and zero
+                                  LCPs (default 30 s).  Lets a caller
                                   that must not hang detect a stalled device
                                   sooner.  An idle block of the work-queue
                                   kernel waits while other blocks split the
@@ -117,10 +122,19 @@ typedef struct ss_options {
 } ss_options;
 
 /* Sort n strings.  Section 2.1 (problem), Algorithm 4.1 (one S^5 step),
- * Section 4.2.8 (parallel S^5 and the LCP array).  Enqueues the sort on
- * `stream` and waits for it (large inputs need the host to plan each
- * multi-block step).  n = 0 is a no-op; n = 1 gives perm = [0], lcp = [0].
- * Returns SS_ERR_TOO_LARGE for n >= 2^32. */
+ * Section 4.2.8 (parallel S^5 and the LCP array).  Asynchronous: enqueues the
+ * sort on `stream` and returns without waiting for it.  The rounds of
+ * multi-block steps (subsets above the big threshold) are planned on the
+ * device and run as one CUDA graph launch with a conditional WHILE node (one
+ * graph per stream, built on the first such call); the rest is a fixed
+ * sequence of launches.  The return value reports argument and launch errors;
+ * device-side errors go to the stream's status word (ss_stream_status).
+ * The first call on a stream allocates that stream's status word and loop
+ * control block (4 KiB, kept until exit).  Without a caller workspace the
+ * workspace is stream-ordered memory, freed on `stream` after the sort.
+ * The caller's buffers must stay valid until the stream has run the sort.
+ * n = 0 is a no-op; n = 1 gives perm = [0], lcp = [0].  Returns
+ * SS_ERR_TOO_LARGE for n >= 2^32. */
 ss_status ss_sort(const uint8_t* chars, const uint64_t* offsets, uint64_t n,
                   uint32_t* out_perm, uint32_t* out_lcp, void* stream);
 
@@ -283,19 +297,23 @@ ss_status ss_batch_create(const ss_set* sets, uint32_t num_sets, const ss_option
 size_t ss_batch_workspace_size(const ss_set* sets, uint32_t num_sets, const ss_options* opt);
 
 /* Enqueue the sort of every set of the batch on `stream`.  Asynchronous: no
- * host synchronisation, no allocation, a fixed sequence of kernel launches
- * (one persistent work-queue launch does the splitting), so the call can be
- * captured into a CUDA graph and replayed.  Device-side errors are latched
- * and read by ss_batch_status(). */
+ * host synchronisation and no allocation.  Sets above the big threshold take
+ * multi-block steps, run by the loop of ss_sort (a graph with a conditional
+ * WHILE node over the batch's own control block: launched as a graph, or,
+ * when `stream` is being captured, added to the caller's graph); the rest is
+ * a fixed sequence of launches (one persistent work-queue launch does the
+ * single-block splitting).  So the call can be captured into a CUDA graph and
+ * replayed.  Device-side errors are latched and read by ss_batch_status(). */
 ss_status ss_batch_run(ss_batch* b, void* stream);
 
 /* Wait for `stream` and return the device status latched by the last
  * ss_batch_run of this plan. */
 ss_status ss_batch_status(ss_batch* b, void* stream);
 
-/* Wait for `stream` and return the device status latched by the last
- * ss_batch_run enqueued on it (SS_OK if none is known; ss_sort, ss_sort_ex
- * and ss_sort_host return their status directly). */
+/* Wait for `stream` and return the device status of the work enqueued on it:
+ * first the status word of its ss_sort / ss_sort_ex calls since the last
+ * ss_stream_status (which clears it), then that of the last ss_batch_run
+ * enqueued on it.  SS_OK if there is neither. */
 ss_status ss_stream_status(void* stream);
 
 /* Release a plan (and its workspace if the library allocated it). */
@@ -338,7 +356,10 @@ ss_status ss_sort_noalloc(const uint8_t* chars, const uint64_t* offsets, uint64_
 /* Static description of a status code. */
 const char* ss_status_string(ss_status s);
 
-/* Number of kernel launches this library has issued in this process. */
+/* Number of kernel launches this library has issued in this process: the
+ * launches made from the host plus the kernels launched by its multi-block
+ * loop graphs on the current device (counted on the device; reading that
+ * count waits for the device). */
 uint64_t ss_launch_count(void);
 
 /* Per-kernel device timing.  When enabled, the library records CUDA events

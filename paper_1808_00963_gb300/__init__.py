@@ -208,16 +208,20 @@ def _check(code, what):
 
 
 def sort(chars, offsets, max_len: int = 0, with_lcp: bool = True, out=None, stream=None, dna: bool = False,
-         **opts):
+         sync: bool = True, **opts):
     """Sort the strings of a device string set.
 
     chars   : torch.uint8 CUDA tensor (NUL-terminated strings)
     offsets : torch.int64 CUDA tensor (start of each string)
     dna     : the bytes of chars are only A, C, G, T and terminators: sort
               with 3-bit character codes, 21 characters per key
+    sync    : wait for the sort and raise SortError on a device-side error
+              (ss_stream_status); False only enqueues it (ss_sort_ex is
+              asynchronous), and the caller reads the status later with
+              stream_status()
     Returns (perm, lcp) as torch.int32 CUDA tensors holding uint32 values
-    (lcp is None when with_lcp is False).  Runs on the current stream (or
-    ``stream``) and returns when the sort has finished.
+    (lcp is None when with_lcp is False), on the current stream (or
+    ``stream``).
     """
     import torch
     lib = load()
@@ -241,6 +245,8 @@ def sort(chars, offsets, max_len: int = 0, with_lcp: bool = True, out=None, stre
         rc = lib.ss_sort_ex(ctypes.c_void_p(chars.data_ptr()), ctypes.c_void_p(offsets.data_ptr()), n,
                             ctypes.c_void_p(perm.data_ptr()), lp, ctypes.byref(o), _stream_ptr(stream))
         _check(rc, "ss_sort_ex")
+        if sync:
+            _check(lib.ss_stream_status(_stream_ptr(stream)), "ss_sort_ex (device status)")
     return perm, lcp
 
 

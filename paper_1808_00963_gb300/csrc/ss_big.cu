@@ -26,15 +26,15 @@ __device__ __forceinline__ uint64_t cnt_base(const GenTask& g) {
   return ((uint64_t)g.cnt_base_hi << 32) | g.cnt_base_lo;
 }
 
-// Prefix jump.  A step sees 8 characters, so a subset whose strings share a
+// Prefix jump.  A step sees 16 characters, so a subset whose strings share a
 // long prefix (many URLs of one site, repeated records) would be moved once
-// for every 8 shared characters.  When the whole sample of a subset is one key
+// for every 16 shared characters.  When the whole sample of a subset is one key
 // without a terminator, the sampling block measures how far 64 of the
 // sampled strings agree with one of them over the next kPjWindows windows;
 // if they agree beyond 32 characters, the classification measures the same
 // for every string, and if the whole subset then falls into that key's
 // equality bucket,
-// the bucket continues at depth + the smallest agreement instead of depth + 8.
+// the bucket continues at depth + the smallest agreement instead of depth + 16.
 // Any depth up to the subset's common prefix is correct: the jump only skips
 // work, and the check on the sample keeps its cost away from subsets that
 // share only the key.
@@ -46,7 +46,7 @@ constexpr uint32_t kPjSampleChecks = 64;  // sampled strings compared (of the sa
 // for the jump-table classifier only) and the prefix-jump state.
 template <int LOGV>
 struct BigSplitters {
-  Splitters<LOGV> sp;
+  Splitters<LOGV, u128> sp;  // wide keys
   uint16_t jump[kJumpSize];
   uint64_t pj_ref;  // offset of the reference string (the first sampled one)
   uint32_t pj_on;   // check every string of the subset
@@ -77,20 +77,19 @@ __device__ __forceinline__ uint32_t window_lcp(const uint64_t (&w)[kPjWindows], 
   return 8u * kPjWindows;
 }
 
-// Smallest agreement with ref over the strings of records [0, n) taken by this
-// block's threads (pos(i) gives the record of item i), reduced over the block.
-template <typename Pos>
-__device__ uint32_t block_min_agreement(const SortCtx& c, const Rec* recs, const SetDesc& sd, uint32_t wide,
-                                        uint32_t depth, uint32_t items, Pos&& pos, const uint64_t* ref,
-                                        unsigned long long& bytes) {
+// Smallest agreement with ref over the strings of items [0, items) taken by
+// this block's threads (off_of(i) gives the string offset of item i), reduced
+// over the block.
+template <typename OffOf>
+__device__ uint32_t block_min_agreement(const SetDesc& sd, uint32_t depth, uint32_t items, OffOf&& off_of,
+                                        const uint64_t* ref, unsigned long long& bytes) {
   __shared__ uint32_t bmin;
   if (threadIdx.x == 0) bmin = 0xFFFFFFFFu;
   __syncthreads();
   uint32_t mn = 0xFFFFFFFFu;
   for (uint32_t i = threadIdx.x; i < items; i += blockDim.x) {
-    const Rec r = load_rec(recs + pos(i));
     uint64_t w[kPjWindows];
-    load_pj_windows(sd.chars, rec_offset(sd, wide, r.idx, r.off), depth, sd.cap, w);
+    load_pj_windows(sd.chars, off_of(i), depth, sd.cap, w);
     mn = min(mn, window_lcp(w, ref));
     bytes += 8 + 8 * kPjWindows;  // the record's index and offset, the windows
   }
@@ -101,148 +100,305 @@ __device__ uint32_t block_min_agreement(const SortCtx& c, const Rec* recs, const
   return bmin;
 }
 
-template <int LOGV>
-__global__ void __launch_bounds__(kBlock) k_big_sample(SortCtx c, const GenTask* __restrict__ gt,
-                                                       BigSplitters<LOGV>* __restrict__ out) {
-  __shared__ __align__(16) Splitters<LOGV> sp;
-  __shared__ __align__(16) BuildScratch<LOGV> bs;
-  const GenTask g = gt[blockIdx.x];
-  const Rec* recs = c.rec[task_par(g.t)] + g.t.begin;
-  build_splitters<LOGV>(recs, g.t.len, mix64(c.seed ^ ((uint64_t)g.t.begin << 20) ^ g.t.depth), sp, bs,
-                        c.sets[task_set(g.t)].dna);
-  const uint64_t* src = reinterpret_cast<const uint64_t*>(&sp);
-  uint64_t* dst = reinterpret_cast<uint64_t*>(&out[blockIdx.x].sp);
-  for (uint32_t i = threadIdx.x; i < sizeof(Splitters<LOGV>) / 8; i += blockDim.x) dst[i] = src[i];
-  unsigned long long bytes = threadIdx.x == 0 ? Geo<LOGV>::S * 8ull + sizeof(Splitters<LOGV>) : 0ull;
-  // prefix jump: a one-key sample whose strings agree beyond kPjMinSample
-  // characters turns on the check of the whole subset
-  const SetDesc sd = c.sets[task_set(g.t)];
-  const uint64_t k0 = bs.sample[0];  // the sorted sample
-  const bool one_key = !sd.dna && k0 == bs.sample[Geo<LOGV>::S - 1] && !key_end(k0, 0u);
-  uint32_t on = 0;
-  uint64_t ref_off = 0;
-  if (one_key) {  // uniform over the block
-    const uint64_t hseed = mix64(c.seed ^ ((uint64_t)g.t.begin << 20) ^ g.t.depth);
-    auto sample_pos = [&](uint32_t i) { return (uint32_t)(((mix64(hseed + i) >> 32) * (uint64_t)g.t.len) >> 32); };
-    const uint32_t wide = c.wide[task_set(g.t)];
-    __shared__ uint64_t ref[kPjWindows];
-    const Rec r0 = load_rec(recs + sample_pos(0));
-    ref_off = rec_offset(sd, wide, r0.idx, r0.off);
-    if (threadIdx.x == 0) {
-      uint64_t w[kPjWindows];
-      load_pj_windows(sd.chars, ref_off, g.t.depth, sd.cap, w);
-      for (int j = 0; j < kPjWindows; ++j) ref[j] = w[j];
+// ---- plan of a round ------------------------------------------------------------------
+
+__device__ unsigned long long g_graph_launches;  // kernels launched by loop graphs (this device)
+
+constexpr uint32_t kPlanThreads = 1024;
+
+// Exclusive scan of one 64-bit value per thread of a kPlanThreads block;
+// returns the block total.
+__device__ uint64_t plan_scan(uint64_t v, uint64_t& excl) {
+  __shared__ uint64_t wsum[kPlanThreads / 32];
+  const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+  uint64_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= (uint32_t)o) inc += t;
+  }
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint64_t x = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t t = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= (uint32_t)o) x += t;
     }
-    __syncthreads();
-    const uint32_t agree = block_min_agreement(c, recs, sd, wide, g.t.depth, kPjSampleChecks, sample_pos, ref, bytes);
-    on = agree > kPjMinSample && agree != 0xFFFFFFFFu ? 1u : 0u;
+    wsum[lane] = x;
+  }
+  __syncthreads();
+  excl = inc - v + (w ? wsum[w - 1] : 0ull);
+  const uint64_t total = wsum[kPlanThreads / 32 - 1];
+  __syncthreads();
+  return total;
+}
+
+// Turns the big subsets left by the previous round (list ctl->cur) into the
+// task table of this round: for every subset its tiles, its first tile, its
+// first record among the round's records and its first counter (the host
+// plan of a multi-block step, done on the device).  With use_cond it sets the
+// loop graph's condition: 1 while there is a round to run.
+__global__ void __launch_bounds__(kPlanThreads) k_big_plan(BigCtl* __restrict__ ctl,
+                                                           cudaGraphConditionalHandle h, uint32_t use_cond) {
+  __shared__ uint32_t s_G;
+  const SortCtx& c = ctl->c;
+  const uint32_t cur = ctl->cur;
+  if (threadIdx.x == 0) {
+    uint32_t g = min(*c.big[cur].count, ctl->cap_big);
+    if (g && (*c.status != 0 || ctl->round >= kMaxBigRounds)) {
+      if (ctl->round >= kMaxBigRounds) latch_status(c.status, kStTooDeep);
+      g = 0;  // stop: this sort has latched an error, or the loop ran too long
+    }
+    s_G = g;
+  }
+  __syncthreads();
+  uint32_t G = s_G;
+  // strings in this round's subsets, for the tile size
+  uint64_t mine = 0;
+  for (uint32_t g = threadIdx.x; g < G; g += kPlanThreads) mine += c.big[cur].items[g].len;
+  uint64_t ex;
+  const uint64_t total = plan_scan(mine, ex);
+  uint32_t R = ctl->R_fixed;
+  if (!R) {
+    const uint64_t per = total / ((uint64_t)ctl->sms * 2 * kBlock) + 1;
+    R = (uint32_t)(per < 8 ? 8 : (per > kMaxRounds ? kMaxRounds : per));
+  }
+  const uint32_t T = kBlock * R;
+  const uint64_t K = ctl->K;
+  uint64_t tiles0 = 0, rec0 = 0, cnt0 = 0;
+  for (uint32_t g0 = 0; g0 < G; g0 += kPlanThreads) {
+    const uint32_t g = g0 + threadIdx.x;
+    Task t{0, 0, 0, 0};
+    if (g < G) t = c.big[cur].items[g];
+    const uint32_t tl = (t.len + T - 1) / T;
+    uint64_t e_tiles, e_rec, e_cnt;
+    const uint64_t s_tiles = plan_scan(tl, e_tiles);
+    const uint64_t s_rec = plan_scan(t.len, e_rec);
+    const uint64_t s_cnt = plan_scan(K * tl, e_cnt);
+    if (g < G) {
+      GenTask x;
+      x.t = t;
+      x.tile_start = (uint32_t)(tiles0 + e_tiles);
+      x.tiles = tl;
+      x.rec_base = (uint32_t)(rec0 + e_rec);
+      const uint64_t cb = cnt0 + e_cnt;
+      x.cnt_base_lo = (uint32_t)cb;
+      x.cnt_base_hi = (uint32_t)(cb >> 32);
+      x.pad[0] = x.pad[1] = x.pad[2] = 0;
+      ctl->gt[g] = x;
+    }
+    tiles0 += s_tiles;
+    rec0 += s_rec;
+    cnt0 += s_cnt;
   }
   if (threadIdx.x == 0) {
-    out[blockIdx.x].pj_on = on;
-    out[blockIdx.x].pj_lcp = 0xFFFFFFFFu;
-    out[blockIdx.x].pj_ref = ref_off;
+    if (cnt0 > ctl->ncounters_max) {  // cannot happen: the counters are sized for the largest round
+      latch_status(c.status, kStQueueFull);
+      G = 0;
+    }
+    ctl->G = G;
+    ctl->tiles = G ? (uint32_t)tiles0 : 0u;
+    ctl->R = R;
+    ctl->ncounters = G ? cnt0 : 0ull;
+    ctl->next_big = cur ^ 1u;
+    for (int k = 0; k < 4; ++k) ctl->next_item[k] = 0;
+    if (G) {
+      *c.big[cur ^ 1u].count = 0;  // the list the round's new big subsets go to
+      ctl->cur = cur ^ 1u;
+      ctl->round += 1;
+    }
+    if (use_cond) {
+      atomicAdd(&g_graph_launches, 1ull + (G ? kBigRoundKernels : 0ull));
+      cudaGraphSetConditional(h, G ? 1u : 0u);
+    }
   }
-  if (c.classifier == kClassifyUIJ) {
-    for (uint32_t p = threadIdx.x; p < kJumpSize; p += blockDim.x)
-      out[blockIdx.x].jump[p] = (uint16_t)jump_entry<LOGV>(p, sp.tree);
-    if (threadIdx.x == 0) bytes += 2ull * kJumpSize;
+}
+
+// ---- the kernels of one round -----------------------------------------------------------
+
+// Records per lane moved together by the multi-block distribution (a wide
+// record and its loads take twice the registers of a narrow one).
+constexpr int kWideMoveBatch = 2;
+
+// The next item (subset or tile) of a round's kernel for this block: taken
+// from the kernel's work counter by one thread and shared with the block.
+__device__ __forceinline__ uint32_t next_item(uint32_t* counter) {
+  __shared__ uint32_t s_item;
+  __syncthreads();  // every thread has read the previous item
+  if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
+  __syncthreads();
+  return s_item;
+}
+
+template <int LOGV>
+__global__ void __launch_bounds__(kBlock) k_big_sample(const BigCtl* __restrict__ ctl, uint32_t* __restrict__ work) {
+  __shared__ __align__(16) Splitters<LOGV, u128> sp;
+  __shared__ __align__(16) BuildScratch<LOGV, u128> bs;
+  __shared__ uint64_t ref[kPjWindows];
+  const uint32_t G = ctl->G;
+  const SortCtx& c = ctl->c;
+  BigSplitters<LOGV>* out = reinterpret_cast<BigSplitters<LOGV>*>(ctl->splitters);
+  unsigned long long bytes = 0;
+  for (uint32_t gi = next_item(work); gi < G; gi = next_item(work)) {
+    const GenTask g = ctl->gt[gi];
+    const uint32_t par = task_par(g.t);
+    const Rec* recs = c.rec[par] + g.t.begin;
+    const uint2* wids = c.wid[par] + g.t.begin;
+    const SetDesc sd = c.sets[task_set(g.t)];
+    const uint64_t hseed = mix64(c.seed ^ ((uint64_t)g.t.begin << 20) ^ g.t.depth);
+    build_splitters_k<LOGV, u128>([&](uint32_t pos) { return load_wkey(recs + pos); }, g.t.len, hseed, sp, bs,
+                                  sd.dna);
+    const uint4* src = reinterpret_cast<const uint4*>(&sp);
+    uint4* dst = reinterpret_cast<uint4*>(&out[gi].sp);
+    for (uint32_t i = threadIdx.x; i < sizeof(sp) / 16; i += blockDim.x) dst[i] = src[i];
+    if (threadIdx.x == 0) bytes += Geo<LOGV>::S * 16ull + sizeof(sp);
+    // prefix jump: a one-key sample whose strings agree beyond kPjMinSample
+    // characters turns on the check of the whole subset
+    const u128 k0 = bs.sample[0];  // the sorted sample
+    const bool one_key = !sd.dna && k0 == bs.sample[Geo<LOGV>::S - 1] && !KeyOps<u128>::end(k0, 0u);
+    uint32_t on = 0;
+    uint64_t ref_off = 0;
+    if (one_key) {  // uniform over the block
+      auto sample_pos = [&](uint32_t i) {
+        return (uint32_t)(((mix64(hseed + i) >> 32) * (uint64_t)g.t.len) >> 32);
+      };
+      const uint32_t wide = c.wide[task_set(g.t)];
+      auto off_of = [&](uint32_t i) {
+        const uint2 w = wids[sample_pos(i)];
+        return rec_offset(sd, wide, w.x, w.y);
+      };
+      ref_off = off_of(0);
+      if (threadIdx.x == 0) {
+        uint64_t w[kPjWindows];
+        load_pj_windows(sd.chars, ref_off, g.t.depth, sd.cap, w);
+        for (int j = 0; j < kPjWindows; ++j) ref[j] = w[j];
+      }
+      __syncthreads();
+      const uint32_t agree = block_min_agreement(sd, g.t.depth, kPjSampleChecks, off_of, ref, bytes);
+      on = agree > kPjMinSample && agree != 0xFFFFFFFFu ? 1u : 0u;
+    }
+    if (threadIdx.x == 0) {
+      out[gi].pj_on = on;
+      out[gi].pj_lcp = 0xFFFFFFFFu;
+      out[gi].pj_ref = ref_off;
+    }
+    if (c.classifier == kClassifyUIJ) {
+      for (uint32_t p = threadIdx.x; p < kJumpSize; p += blockDim.x)
+        out[gi].jump[p] = (uint16_t)jump_entry<LOGV, u128>(p, sp.tree);
+      if (threadIdx.x == 0) bytes += 2ull * kJumpSize;
+    }
   }
   // sample reads + splitter (and jump table) writes
   account(c, kKBigSample, bytes);
 }
 
 template <int LOGV>
-__global__ void __launch_bounds__(kBlock) k_big_classify(SortCtx c, const GenTask* __restrict__ gt,
-                                                         uint32_t G, const BigSplitters<LOGV>* __restrict__ spl,
-                                                         uint32_t* __restrict__ counters, uint32_t R) {
+__global__ void __launch_bounds__(kBlock) k_big_classify(const BigCtl* __restrict__ ctl, uint32_t* __restrict__ work) {
   using Gm = Geo<LOGV>;
-  __shared__ __align__(16) uint64_t tree[Gm::V + 1];
-  __shared__ __align__(16) uint64_t x[Gm::V + 1];
+  __shared__ __align__(16) u128 tree[Gm::V + 1];
+  __shared__ __align__(16) u128 x[Gm::V + 1];
   __shared__ uint32_t hist[Gm::KP];
   __shared__ __align__(16) uint16_t jump[kJumpSize];
+  __shared__ uint64_t ref[kPjWindows];
   __shared__ uint32_t s_g;
-  if (threadIdx.x == 0) s_g = find_gen_task(gt, G, blockIdx.x);
-  for (uint32_t b = threadIdx.x; b < Gm::KP; b += blockDim.x) hist[b] = 0;
-  __syncthreads();
-  const GenTask g = gt[s_g];
-  const Splitters<LOGV>& sp = spl[s_g].sp;
-  for (uint32_t i = threadIdx.x; i <= Gm::V; i += blockDim.x) { tree[i] = sp.tree[i]; x[i] = sp.x[i]; }
+  const uint32_t G = ctl->G, tiles = ctl->tiles, R = ctl->R;
+  const SortCtx& c = ctl->c;
+  const GenTask* __restrict__ gt = ctl->gt;
+  BigSplitters<LOGV>* spl = reinterpret_cast<BigSplitters<LOGV>*>(ctl->splitters);
   const bool use_jump = c.classifier == kClassifyUIJ;
-  if (use_jump) {
-    const uint4* js = reinterpret_cast<const uint4*>(spl[s_g].jump);
-    uint4* jd = reinterpret_cast<uint4*>(jump);
-    for (uint32_t i = threadIdx.x; i < kJumpSize * 2 / 16; i += blockDim.x) jd[i] = js[i];
-  }
-  __syncthreads();
-  const uint32_t tile = blockIdx.x - g.tile_start;
-  const uint32_t T = kBlock * R;
-  const uint32_t t0 = tile * T;
-  const uint32_t tl = min(T, g.t.len - t0);
-  const Rec* recs = c.rec[task_par(g.t)] + g.t.begin + t0;
-  uint16_t* bo = c.bucket_of + g.t.begin + t0;
-  const uint32_t mine = classify_count<LOGV>(recs, bo, tl, tree, x, hist, c.classifier, use_jump ? jump : nullptr);
-  __syncthreads();
-  uint32_t* cnt = counters + cnt_base(g) + tile;
-  for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) cnt[(uint64_t)b * g.tiles] = hist[b];
-  // per record: cache 8 read + bucket index 2 written; per tile: K counters written
-  unsigned long long bytes = 10ull * mine;
-  if (threadIdx.x == 0) bytes += 4ull * Gm::K;
-  if (spl[s_g].pj_on) {  // prefix jump: every string's agreement with the reference
-    const SetDesc sd = c.sets[task_set(g.t)];
-    __shared__ uint64_t ref[kPjWindows];
-    if (threadIdx.x == 0) {
-      uint64_t w[kPjWindows];
-      load_pj_windows(sd.chars, spl[s_g].pj_ref, g.t.depth, sd.cap, w);
-      for (int j = 0; j < kPjWindows; ++j) ref[j] = w[j];
-    }
+  unsigned long long bytes = 0;
+  uint32_t loaded = 0xFFFFFFFFu;  // subset whose splitters are in shared memory
+  for (uint32_t tg = next_item(work); tg < tiles; tg = next_item(work)) {
+    if (threadIdx.x == 0) s_g = find_gen_task(gt, G, tg);
+    for (uint32_t b = threadIdx.x; b < Gm::KP; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    const uint32_t bmin = block_min_agreement(c, recs, sd, c.wide[task_set(g.t)], g.t.depth, tl,
-                                              [](uint32_t i) { return i; }, ref, bytes);
-    if (threadIdx.x == 0 && bmin != 0xFFFFFFFFu)
-      atomicMin(&const_cast<BigSplitters<LOGV>*>(spl)[s_g].pj_lcp, bmin);
+    const uint32_t gi = s_g;
+    const GenTask g = gt[gi];
+    if (gi != loaded) {  // uniform over the block
+      const Splitters<LOGV, u128>& sp = spl[gi].sp;
+      for (uint32_t i = threadIdx.x; i <= Gm::V; i += blockDim.x) { tree[i] = sp.tree[i]; x[i] = sp.x[i]; }
+      if (use_jump) {
+        const uint4* js = reinterpret_cast<const uint4*>(spl[gi].jump);
+        uint4* jd = reinterpret_cast<uint4*>(jump);
+        for (uint32_t i = threadIdx.x; i < kJumpSize * 2 / 16; i += blockDim.x) jd[i] = js[i];
+      }
+      loaded = gi;
+      __syncthreads();
+    }
+    const uint32_t tile = tg - g.tile_start;
+    const uint32_t T = kBlock * R;
+    const uint32_t t0 = tile * T;
+    const uint32_t tl = min(T, g.t.len - t0);
+    const uint32_t par = task_par(g.t);
+    const Rec* recs = c.rec[par] + g.t.begin + t0;
+    uint16_t* bo = c.bucket_of + g.t.begin + t0;
+    const uint32_t mine = classify_count_k<LOGV, u128>([&](uint32_t p) { return load_wkey(recs + p); }, bo, tl,
+                                                       tree, x, hist, c.classifier, use_jump ? jump : nullptr);
+    __syncthreads();
+    uint32_t* cnt = ctl->counters + cnt_base(g) + tile;
+    for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) cnt[(uint64_t)b * g.tiles] = hist[b];
+    // per record: wide key 16 read + bucket index 2 written; per tile: K counters written
+    bytes += 18ull * mine;
+    if (threadIdx.x == 0) bytes += 4ull * Gm::K;
+    if (spl[gi].pj_on) {  // prefix jump: every string's agreement with the reference
+      const SetDesc sd = c.sets[task_set(g.t)];
+      if (threadIdx.x == 0) {
+        uint64_t w[kPjWindows];
+        load_pj_windows(sd.chars, spl[gi].pj_ref, g.t.depth, sd.cap, w);
+        for (int j = 0; j < kPjWindows; ++j) ref[j] = w[j];
+      }
+      __syncthreads();
+      const uint2* wids = c.wid[par] + g.t.begin + t0;
+      const uint32_t wide = c.wide[task_set(g.t)];
+      const uint32_t bmin = block_min_agreement(
+          sd, g.t.depth, tl, [&](uint32_t i) { const uint2 w = wids[i]; return rec_offset(sd, wide, w.x, w.y); },
+          ref, bytes);
+      if (threadIdx.x == 0 && bmin != 0xFFFFFFFFu) atomicMin(&spl[gi].pj_lcp, bmin);
+    }
   }
   account(c, kKBigClassify, bytes);
 }
 
 template <int LOGV>
-__global__ void __launch_bounds__(kBlock) k_big_emit(SortCtx c, const GenTask* __restrict__ gt,
-                                                     const BigSplitters<LOGV>* __restrict__ spl,
-                                                     const uint32_t* __restrict__ scanned,
-                                                     uint32_t* __restrict__ gstart, uint32_t* __restrict__ gdesc,
-                                                     uint32_t next_big) {
+__global__ void __launch_bounds__(kBlock) k_big_emit(const BigCtl* __restrict__ ctl, uint32_t* __restrict__ work) {
   using Gm = Geo<LOGV>;
-  const GenTask g = gt[blockIdx.x];
-  const Splitters<LOGV>& sp = spl[blockIdx.x].sp;
-  const SetDesc sd = c.sets[task_set(g.t)];
-  const uint32_t* sc = scanned + cnt_base(g);
+  const uint32_t G = ctl->G;
+  const SortCtx& c = ctl->c;
+  const BigSplitters<LOGV>* spl = reinterpret_cast<const BigSplitters<LOGV>*>(ctl->splitters);
+  const uint32_t next_big = ctl->next_big;
   unsigned long long bytes = 0;
-  for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) {
-    bytes += 16;  // two bucket offsets read, start and descriptor written
-    const uint32_t s = sc[(uint64_t)b * g.tiles] - g.rec_base;
-    const uint32_t e = (b + 1 < Gm::K) ? sc[(uint64_t)(b + 1) * g.tiles] - g.rec_base : g.t.len;
-    const uint32_t size = e - s;
-    gstart[(uint64_t)blockIdx.x * Gm::KP + b] = s;
-    uint32_t desc = kFin;
-    if (size) {
-      desc = bucket_desc<LOGV>(b, size, g.t.depth, sp, sd.dna);
-      // prefix jump: the whole subset is the key's equality bucket, and every
-      // string agrees with the reference for pj_lcp characters from the depth
-      if (spl[blockIdx.x].pj_on && (b & 1u) && size == g.t.len && !(desc & kFin)) {
-        const uint32_t J = spl[blockIdx.x].pj_lcp;
-        if (J > 8u && J != 0xFFFFFFFFu) desc = g.t.depth + J;
+  for (uint32_t gi = next_item(work); gi < G; gi = next_item(work)) {
+    const GenTask g = ctl->gt[gi];
+    const Splitters<LOGV, u128>& sp = spl[gi].sp;
+    const SetDesc sd = c.sets[task_set(g.t)];
+    const uint32_t* sc = ctl->counters + cnt_base(g);
+    for (uint32_t b = threadIdx.x; b < Gm::K; b += blockDim.x) {
+      bytes += 16;  // two bucket offsets read, start and descriptor written
+      const uint32_t s = sc[(uint64_t)b * g.tiles] - g.rec_base;
+      const uint32_t e = (b + 1 < Gm::K) ? sc[(uint64_t)(b + 1) * g.tiles] - g.rec_base : g.t.len;
+      const uint32_t size = e - s;
+      ctl->gstart[(uint64_t)gi * Gm::KP + b] = s;
+      uint32_t desc = kFin;
+      if (size) {
+        desc = bucket_desc<LOGV, u128>(b, size, g.t.depth, sp, sd.dna);
+        // prefix jump: the whole subset is the key's equality bucket, and every
+        // string agrees with the reference for pj_lcp characters from the depth
+        if (spl[gi].pj_on && (b & 1u) && size == g.t.len && !(desc & kFin)) {
+          const uint32_t J = spl[gi].pj_lcp;
+          if (J > KeyOps<u128>::width(0) && J != 0xFFFFFFFFu) desc = g.t.depth + J;
+        }
+        emit_bucket(c, sd, g.t, s, size, desc, next_big, kLcpMark | kLcpWide);
       }
-      emit_bucket(c, sd, g.t, s, size, desc, next_big);
+      ctl->gdesc[(uint64_t)gi * Gm::KP + b] = desc;
     }
-    gdesc[(uint64_t)blockIdx.x * Gm::KP + b] = desc;
   }
   account(c, kKBigEmit, bytes);
 }
 
 template <int LOGV>
-__global__ void __launch_bounds__(kBlock, 4) k_big_scatter(SortCtx c, const GenTask* __restrict__ gt, uint32_t G,
-                                                        const uint32_t* __restrict__ scanned,
-                                                        const uint32_t* __restrict__ gstart,
-                                                        const uint32_t* __restrict__ gdesc, uint32_t R) {
+__global__ void __launch_bounds__(kBlock, 4) k_big_scatter(const BigCtl* __restrict__ ctl, uint32_t* __restrict__ work) {
   using Gm = Geo<LOGV>;
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t* cntw = reinterpret_cast<uint32_t*>(smem);
@@ -251,33 +407,43 @@ __global__ void __launch_bounds__(kBlock, 4) k_big_scatter(SortCtx c, const GenT
   uint32_t* bfirst = desc + Gm::KP;
   uint16_t* tb = reinterpret_cast<uint16_t*>(bfirst + Gm::KP);
   __shared__ uint32_t s_g;
-  if (threadIdx.x == 0) s_g = find_gen_task(gt, G, blockIdx.x);
-  __syncthreads();
-  const uint32_t gi = s_g;
-  const GenTask g = gt[gi];
-  const SetDesc sd = c.sets[task_set(g.t)];
-  const uint32_t tile = blockIdx.x - g.tile_start;
-  const uint32_t T = kBlock * R;
-  const uint32_t t0 = tile * T;
-  const uint32_t tl = min(T, g.t.len - t0);
-  const uint32_t par = task_par(g.t);
-  const uint16_t* bo = c.bucket_of + g.t.begin + t0;
-  for (uint32_t p = threadIdx.x; p < tl; p += kBlock) tb[p] = bo[p];
-  const uint32_t* sc = scanned + cnt_base(g) + tile;
-  for (uint32_t b = threadIdx.x; b < Gm::K; b += kBlock) {
-    base[b] = g.t.begin + sc[(uint64_t)b * g.tiles] - g.rec_base;
-    desc[b] = gdesc[(uint64_t)gi * Gm::KP + b];
-    bfirst[b] = g.t.begin + gstart[(uint64_t)gi * Gm::KP + b];
+  const uint32_t G = ctl->G, tiles = ctl->tiles, R = ctl->R;
+  const SortCtx& c = ctl->c;
+  const GenTask* __restrict__ gt = ctl->gt;
+  unsigned long long bytes = 0;
+  for (uint32_t tg = next_item(work); tg < tiles; tg = next_item(work)) {
+    if (threadIdx.x == 0) s_g = find_gen_task(gt, G, tg);
+    __syncthreads();
+    const uint32_t gi = s_g;
+    const GenTask g = gt[gi];
+    const SetDesc sd = c.sets[task_set(g.t)];
+    const uint32_t tile = tg - g.tile_start;
+    const uint32_t T = kBlock * R;
+    const uint32_t t0 = tile * T;
+    const uint32_t tl = min(T, g.t.len - t0);
+    const uint32_t par = task_par(g.t);
+    const uint16_t* bo = c.bucket_of + g.t.begin + t0;
+    for (uint32_t p = threadIdx.x; p < tl; p += kBlock) tb[p] = bo[p];
+    const uint32_t* sc = ctl->counters + cnt_base(g) + tile;
+    for (uint32_t b = threadIdx.x; b < Gm::K; b += kBlock) {
+      base[b] = g.t.begin + sc[(uint64_t)b * g.tiles] - g.rec_base;
+      desc[b] = ctl->gdesc[(uint64_t)gi * Gm::KP + b];
+      bfirst[b] = g.t.begin + ctl->gstart[(uint64_t)gi * Gm::KP + b];
+    }
+    if (threadIdx.x == 0) bfirst[Gm::K] = g.t.begin + g.t.len;  // bucket sizes from neighbouring starts
+    __syncthreads();
+    const uint32_t src0 = g.t.begin + t0;
+    const uint32_t depth = g.t.depth;
+    const uint32_t wide = c.wide[task_set(g.t)];
+    if (threadIdx.x == 0) bytes += 12ull * Gm::K;  // per-bucket tile offsets, descriptors and starts
+    tile_scatter<LOGV, kWideMoveBatch>(
+        tb, tl, R, base, cntw,
+        [&](const uint32_t(&pp)[kWideMoveBatch], const uint32_t(&bb)[kWideMoveBatch],
+            const uint32_t(&dd)[kWideMoveBatch]) {
+          bytes += move_batch_wide<kWideMoveBatch>(c, sd, wide, par, src0, depth, desc,
+                                                   [&](uint32_t b) { return bfirst[b]; }, pp, bb, dd);
+        });
   }
-  __syncthreads();
-  const uint32_t src0 = g.t.begin + t0;
-  const uint32_t depth = g.t.depth;
-  const uint32_t wide = c.wide[task_set(g.t)];
-  unsigned long long bytes = threadIdx.x == 0 ? 12ull * Gm::K : 0ull;  // per-bucket tile offsets
-  tile_scatter<LOGV>(tb, tl, R, base, cntw, [&](const uint32_t(&pp)[kMoveBatch], const uint32_t(&bb)[kMoveBatch],
-                                                const uint32_t(&dd)[kMoveBatch]) {
-    bytes += move_batch(c, sd, wide, par, src0, depth, desc, [&](uint32_t b) { return bfirst[b]; }, pp, bb, dd);
-  });
   account(c, kKBigScatter, bytes);
 }
 
@@ -314,22 +480,35 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& excl) 
   return total;
 }
 
-__global__ void __launch_bounds__(kBlock) k_scan_reduce(const uint32_t* __restrict__ a, uint64_t n,
-                                                        uint32_t* __restrict__ part, SortCtx c) {
-  const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk;
-  uint32_t s = 0;
-  for (uint32_t i = threadIdx.x; i < kScanChunk; i += kBlock) {
-    const uint64_t k = b0 + i;
-    if (k < n) s += a[k];
+// The counters of the round: ctl->ncounters values, in chunks of kScanChunk.
+__global__ void __launch_bounds__(kBlock) k_scan_reduce(const BigCtl* __restrict__ ctl) {
+  const uint64_t n = ctl->ncounters;
+  const uint32_t* __restrict__ a = ctl->counters;
+  uint32_t* __restrict__ part = ctl->partials;
+  const uint64_t nb = (n + kScanChunk - 1) / kScanChunk;
+  unsigned long long bytes = 0;
+  for (uint64_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+    const uint64_t b0 = blk * kScanChunk;
+    uint32_t s = 0;
+    for (uint32_t i = threadIdx.x; i < kScanChunk; i += kBlock) {
+      const uint64_t k = b0 + i;
+      if (k < n) s += a[k];
+    }
+    uint32_t ex;
+    const uint32_t total = block_excl_scan(s, ex);
+    if (threadIdx.x == 0) {
+      part[blk] = total;
+      const uint64_t left = n - b0;
+      bytes += 4ull * (left < kScanChunk ? left : kScanChunk);
+    }
   }
-  uint32_t ex;
-  const uint32_t total = block_excl_scan(s, ex);
-  if (threadIdx.x == 0) part[blockIdx.x] = total;
-  const uint64_t left = n > b0 ? n - b0 : 0;
-  account(c, kKScan, threadIdx.x == 0 ? 4ull * (left < kScanChunk ? left : kScanChunk) : 0ull);
+  account(ctl->c, kKScan, bytes);
 }
 
-__global__ void __launch_bounds__(kBlock) k_scan_partials(uint32_t* __restrict__ part, uint32_t m) {
+__global__ void __launch_bounds__(kBlock) k_scan_partials(const BigCtl* __restrict__ ctl) {
+  const uint64_t n = ctl->ncounters;
+  uint32_t* __restrict__ part = ctl->partials;
+  const uint32_t m = (uint32_t)((n + kScanChunk - 1) / kScanChunk);
   uint32_t carry = 0;
   for (uint32_t i0 = 0; i0 < m; i0 += kBlock) {
     const uint32_t i = i0 + threadIdx.x;
@@ -341,28 +520,35 @@ __global__ void __launch_bounds__(kBlock) k_scan_partials(uint32_t* __restrict__
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_scan_down(uint32_t* __restrict__ a, uint64_t n,
-                                                      const uint32_t* __restrict__ part, SortCtx c) {
-  const uint64_t b0 = (uint64_t)blockIdx.x * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
-  uint32_t v[kScanItems];
-  uint32_t s = 0;
+__global__ void __launch_bounds__(kBlock) k_scan_down(const BigCtl* __restrict__ ctl) {
+  const uint64_t n = ctl->ncounters;
+  uint32_t* __restrict__ a = ctl->counters;
+  const uint32_t* __restrict__ part = ctl->partials;
+  const uint64_t nb = (n + kScanChunk - 1) / kScanChunk;
+  unsigned long long bytes = 0;
+  for (uint64_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
+    const uint64_t b0 = blk * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
 #pragma unroll
-  for (uint32_t j = 0; j < kScanItems; ++j) {
-    const uint64_t k = b0 + j;
-    v[j] = k < n ? a[k] : 0;
-    s += v[j];
-  }
-  uint32_t ex;
-  block_excl_scan(s, ex);
-  uint32_t run = part[blockIdx.x] + ex;
+    for (uint32_t j = 0; j < kScanItems; ++j) {
+      const uint64_t k = b0 + j;
+      v[j] = k < n ? a[k] : 0;
+      s += v[j];
+    }
+    uint32_t ex;
+    block_excl_scan(s, ex);
+    uint32_t run = part[blk] + ex;
 #pragma unroll
-  for (uint32_t j = 0; j < kScanItems; ++j) {
-    const uint64_t k = b0 + j;
-    if (k < n) a[k] = run;
-    run += v[j];
+    for (uint32_t j = 0; j < kScanItems; ++j) {
+      const uint64_t k = b0 + j;
+      if (k < n) a[k] = run;
+      run += v[j];
+    }
+    const uint64_t left = n > b0 ? n - b0 : 0;
+    bytes += 8ull * (left < kScanItems ? left : kScanItems);
   }
-  const uint64_t left = n > b0 ? n - b0 : 0;
-  account(c, kKScan, 8ull * (left < kScanItems ? left : kScanItems));
+  account(ctl->c, kKScan, bytes);
 }
 
 }  // namespace
@@ -380,9 +566,18 @@ size_t big_scatter_smem(int logv, uint32_t R) {
   return (size_t)(kWarps * KP + 3 * KP) * 4 + (size_t)kBlock * R * 2;
 }
 
+cudaError_t launch_big_plan(BigCtl* ctl, uint64_t cond_handle, bool use_cond, cudaStream_t st,
+                            const LaunchHook& hook) {
+  hook.run("big_sample", [&] {
+    k_big_plan<<<1, kPlanThreads, 0, st>>>(ctl, (cudaGraphConditionalHandle)cond_handle, use_cond ? 1u : 0u);
+  });
+  return cudaGetLastError();
+}
+
 template <int LOGV>
-static cudaError_t launch_big_step_t(const BigStepArgs& a, cudaStream_t st, const LaunchHook& hook) {
-  const size_t smem = big_scatter_smem(LOGV, a.R);
+static cudaError_t launch_big_round_t(BigCtl* ctl, uint32_t R_max, uint32_t sms, cudaStream_t st,
+                                      const LaunchHook& hook) {
+  const size_t smem = big_scatter_smem(LOGV, R_max);
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_big_scatter<LOGV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -390,30 +585,34 @@ static cudaError_t launch_big_step_t(const BigStepArgs& a, cudaStream_t st, cons
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  auto* spl = reinterpret_cast<BigSplitters<LOGV>*>(a.splitters);
-  hook.run("big_sample", [&] { k_big_sample<LOGV><<<a.G, kBlock, 0, st>>>(a.c, a.gt, spl); });
-  hook.run("big_classify", [&] {
-    k_big_classify<LOGV><<<a.tiles, kBlock, 0, st>>>(a.c, a.gt, a.G, spl, a.counters, a.R);
-  });
-  const uint32_t nb = (uint32_t)((a.ncounters + kScanChunk - 1) / kScanChunk);
-  hook.run("scan", [&] { k_scan_reduce<<<nb, kBlock, 0, st>>>(a.counters, a.ncounters, a.partials, a.c); });
-  hook.run("scan", [&] { k_scan_partials<<<1, kBlock, 0, st>>>(a.partials, nb); });
-  hook.run("scan", [&] { k_scan_down<<<nb, kBlock, 0, st>>>(a.counters, a.ncounters, a.partials, a.c); });
-  hook.run("big_emit", [&] {
-    k_big_emit<LOGV><<<a.G, kBlock, 0, st>>>(a.c, a.gt, spl, a.counters, a.gstart, a.gdesc, a.next_big);
-  });
-  hook.run("big_scatter", [&] {
-    k_big_scatter<LOGV><<<a.tiles, kBlock, smem, st>>>(a.c, a.gt, a.G, a.counters, a.gstart, a.gdesc, a.R);
-  });
+  // fixed grids (the work of a round is only known on the device): blocks
+  // loop over subsets, tiles or counter chunks and return when there are none
+  hook.run("big_sample", [&] { k_big_sample<LOGV><<<sms * 8, kBlock, 0, st>>>(ctl, &ctl->next_item[0]); });
+  hook.run("big_classify", [&] { k_big_classify<LOGV><<<sms * 8, kBlock, 0, st>>>(ctl, &ctl->next_item[1]); });
+  hook.run("scan", [&] { k_scan_reduce<<<sms * 8, kBlock, 0, st>>>(ctl); });
+  hook.run("scan", [&] { k_scan_partials<<<1, kBlock, 0, st>>>(ctl); });
+  hook.run("scan", [&] { k_scan_down<<<sms * 8, kBlock, 0, st>>>(ctl); });
+  hook.run("big_emit", [&] { k_big_emit<LOGV><<<sms * 8, kBlock, 0, st>>>(ctl, &ctl->next_item[2]); });
+  hook.run("big_scatter", [&] { k_big_scatter<LOGV><<<sms * 4, kBlock, smem, st>>>(ctl, &ctl->next_item[3]); });
   return cudaGetLastError();
 }
 
-cudaError_t launch_big_step(int logv, const BigStepArgs& a, cudaStream_t st, const LaunchHook& hook) {
+cudaError_t launch_big_round(int logv, BigCtl* ctl, uint32_t R_max, uint32_t sms, cudaStream_t st,
+                             const LaunchHook& hook) {
   switch (logv) {
-    case 8: return launch_big_step_t<8>(a, st, hook);
-    case 9: return launch_big_step_t<9>(a, st, hook);
-    default: return launch_big_step_t<10>(a, st, hook);
+    case 8: return launch_big_round_t<8>(ctl, R_max, sms, st, hook);
+    case 9: return launch_big_round_t<9>(ctl, R_max, sms, st, hook);
+    default: return launch_big_round_t<10>(ctl, R_max, sms, st, hook);
   }
+}
+
+uint64_t graph_launch_count() {
+  unsigned long long v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_graph_launches, sizeof(v)) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return v;
 }
 
 }  // namespace ss

@@ -20,6 +20,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/ss_sort.h"
@@ -62,8 +63,10 @@ static cudaEvent_t pooled_event(int dev) {
   return e;
 }
 
+static thread_local bool t_no_count = false;  // set while our own loop graphs are captured
+
 void LaunchHook::run(const char* name, const std::function<void()>& launch) const {
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  if (!t_no_count) g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (!g_profiling.load() || cudaStreamIsCapturing(stream, &cs) != cudaSuccess ||
       cs != cudaStreamCaptureStatusNone) {
@@ -205,8 +208,8 @@ enum Ctrl : uint32_t { kCStatus = 0, kCBig0 = 1, kCBig1 = 2, kCHead = 3, kCTail 
                        kCSmallW = 6, kCSmallC = 7, kCSmallD = 8 };
 
 struct Layout {
-  size_t ctrl, sets, wide, rec0, rec1, bucket_of, big0, big1, gen, spl, counters, partials, gstart, gdesc,
-      mq_items, mq_ready, sw_items, sc_items, total;
+  size_t ctrl, sets, wide, rec0, rec1, wid0, wid1, bucket_of, big0, big1, gen, spl, counters, partials, gstart,
+      gdesc, bigctl, mq_items, mq_ready, sw_items, sc_items, total;
   uint32_t cap_big, cap_mq, cap_sw, cap_sc;
   uint64_t ncounters_max;
 };
@@ -231,6 +234,8 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   L.wide = take((size_t)num_sets * 4);
   L.rec0 = take(M * sizeof(Rec));
   L.rec1 = take(M * sizeof(Rec));
+  L.wid0 = take(big ? M * sizeof(uint2) : 0);  // (idx, off) of the wide records of multi-block subsets
+  L.wid1 = take(big ? M * sizeof(uint2) : 0);
   L.bucket_of = take(M * 2);
   L.big0 = take((size_t)L.cap_big * sizeof(Task));
   L.big1 = take((size_t)L.cap_big * sizeof(Task));
@@ -240,6 +245,7 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   L.partials = take((L.ncounters_max / 4096 + 2) * 4);
   L.gstart = take((size_t)L.cap_big * KP * 4);
   L.gdesc = take((size_t)L.cap_big * KP * 4);
+  L.bigctl = take(big ? sizeof(BigCtl) : 0);  // a batch's loop control block (plain sorts use the stream's)
   L.mq_items = take((size_t)L.cap_mq * sizeof(Task));
   L.mq_ready = take((size_t)L.cap_mq * 4);
   L.sw_items = take(2 * (size_t)L.cap_sw * sizeof(Task));
@@ -257,6 +263,8 @@ static SortCtx make_ctx(uint8_t* ws, const Layout& L, uint32_t num_sets, uint32_
   c.wide = reinterpret_cast<uint32_t*>(ws + L.wide);
   c.rec[0] = reinterpret_cast<Rec*>(ws + L.rec0);
   c.rec[1] = reinterpret_cast<Rec*>(ws + L.rec1);
+  c.wid[0] = reinterpret_cast<uint2*>(ws + L.wid0);
+  c.wid[1] = reinterpret_cast<uint2*>(ws + L.wid1);
   c.bucket_of = reinterpret_cast<uint16_t*>(ws + L.bucket_of);
   c.status = ctrl + kCStatus;
   c.abytes = reinterpret_cast<unsigned long long*>(ctrl + kCtrlWords);
@@ -317,12 +325,6 @@ static thread_local Pinned t_down, t_up;
 // the copy engine when it is free.)
 static thread_local bool t_kernel_copies = false;
 
-static cudaError_t small_h2d(void* dst, const void* pinned_src, size_t bytes, cudaStream_t st,
-                             const LaunchHook& hook) {
-  if (t_kernel_copies) return launch_upload(pinned_src, dst, bytes, st, hook);
-  return cudaMemcpyAsync(dst, pinned_src, bytes, cudaMemcpyHostToDevice, st);
-}
-
 static cudaError_t zero_fill(void* dst, size_t bytes, cudaStream_t st, const LaunchHook& hook) {
   if (t_kernel_copies) return launch_upload(nullptr, dst, bytes, st, hook);
   return cudaMemsetAsync(dst, 0, bytes, st);
@@ -332,74 +334,225 @@ static cudaError_t zero_fill(void* dst, size_t bytes, cudaStream_t st, const Lau
 // neither stages it nor waits for a copy before enqueuing the sort.
 __global__ void k_set_desc(SetDesc* dst, SetDesc v) { *dst = v; }
 
-// Enqueues everything after the set descriptors are in place.
+// Writes the control block of the multi-block loop (same reason).
+__global__ void k_set_ctl(BigCtl* dst, BigCtl v) { *dst = v; }
+
+// ---- the multi-block loop as a CUDA graph -------------------------------------------------
+//
+// One round of multi-block steps is a plan kernel plus the round's kernels, all
+// reading the control block in device memory.  The rounds run in a graph with
+// a conditional WHILE node: the plan before the loop and the plan at the end
+// of each round set the condition to 1 while big subsets remain, so the host
+// enqueues the whole loop with one graph launch and never waits for it.  The
+// graph depends only on the control block's address and the step geometry;
+// it is built once per control block (a stream's, or a batch's) and reused.
+
+struct LoopKey {
+  int dev;
+  const void* ctl;
+  int logv;
+  uint32_t R_max;
+  bool operator<(const LoopKey& o) const {
+    return std::tie(dev, ctl, logv, R_max) < std::tie(o.dev, o.ctl, o.logv, o.R_max);
+  }
+};
+struct LoopGraph {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+static std::mutex g_loop_mu;
+static std::map<LoopKey, LoopGraph> g_loops;
+
+// Streams of this thread (per device) that the loop is captured on when a
+// graph is built.
+struct CaptureStreams {
+  cudaStream_t main = nullptr, body = nullptr;
+};
+static thread_local std::map<int, CaptureStreams> t_capture;
+
+static cudaError_t capture_streams(CaptureStreams*& out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  CaptureStreams& c = t_capture[dev];
+  if (!c.main && (e = cudaStreamCreateWithFlags(&c.main, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if (!c.body && (e = cudaStreamCreateWithFlags(&c.body, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  out = &c;
+  return cudaSuccess;
+}
+
+// Adds the loop to the graph being captured on `st`: the first plan, then a
+// WHILE node whose body is one round and the next plan.  Work captured on st
+// afterwards depends on the loop.
+static cudaError_t add_loop(cudaStream_t st, BigCtl* ctl, int logv, uint32_t R_max, uint32_t sms) {
+  CaptureStreams* cs = nullptr;
+  cudaError_t e = capture_streams(cs);
+  if (e != cudaSuccess) return e;
+  const LaunchHook hook{st};
+  cudaStreamCaptureStatus status;
+  cudaGraph_t graph = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  if ((e = cudaStreamGetCaptureInfo(st, &status, nullptr, &graph, &deps, nullptr, &ndeps)) != cudaSuccess) return e;
+  if (status != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+  cudaGraphConditionalHandle h;
+  if ((e = cudaGraphConditionalHandleCreate(&h, graph, 0, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+  if ((e = launch_big_plan(ctl, (uint64_t)h, true, st, hook)) != cudaSuccess) return e;
+  if ((e = cudaStreamGetCaptureInfo(st, &status, nullptr, &graph, &deps, nullptr, &ndeps)) != cudaSuccess) return e;
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if ((e = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &p)) != cudaSuccess) return e;
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  if ((e = cudaStreamBeginCaptureToGraph(cs->body, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed)) !=
+      cudaSuccess)
+    return e;
+  const LaunchHook bhook{cs->body};
+  cudaError_t e1 = launch_big_round(logv, ctl, R_max, sms, cs->body, bhook);
+  cudaError_t e2 = launch_big_plan(ctl, (uint64_t)h, true, cs->body, bhook);
+  cudaGraph_t done = nullptr;
+  e = cudaStreamEndCapture(cs->body, &done);
+  if (e1 != cudaSuccess) return e1;
+  if (e2 != cudaSuccess) return e2;
+  if (e != cudaSuccess) return e;
+  return cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+}
+
+// The instantiated loop graph for a control block (built on first use).
+static cudaError_t loop_exec(BigCtl* ctl, int logv, uint32_t R_max, uint32_t sms, cudaGraphExec_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(g_loop_mu);
+  LoopGraph& lg = g_loops[LoopKey{dev, ctl, logv, R_max}];
+  if (!lg.exec) {
+    CaptureStreams* cs = nullptr;
+    if ((e = capture_streams(cs)) != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCapture(cs->main, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    t_no_count = true;  // these kernels run once per graph launch; the plan kernels count them
+    cudaError_t e1 = add_loop(cs->main, ctl, logv, R_max, sms);
+    t_no_count = false;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(cs->main, &g);
+    if (e1 != cudaSuccess || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return e1 != cudaSuccess ? e1 : e;
+    }
+    if ((e = cudaGraphInstantiate(&lg.exec, g, 0)) != cudaSuccess) {
+      cudaGraphDestroy(g);
+      lg.exec = nullptr;
+      return e;
+    }
+    lg.g = g;
+  }
+  *out = lg.exec;
+  return cudaSuccess;
+}
+
+// Forgets the loop graphs of a control block (its memory is being released).
+static void drop_loops(const void* ctl) {
+  std::lock_guard<std::mutex> lk(g_loop_mu);
+  for (auto it = g_loops.begin(); it != g_loops.end();) {
+    if (it->first.ctl == ctl) {
+      if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
+      if (it->second.g) cudaGraphDestroy(it->second.g);
+      it = g_loops.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+// ---- per-stream state of asynchronous sorts ---------------------------------------------
+
+// Device memory of one (device, stream): the status word the stream's sorts
+// fold their device status into, and the multi-block loop's control block.
+struct StreamSlot {
+  uint32_t status;
+  uint32_t pad[63];
+  BigCtl ctl;
+};
+
+static std::mutex g_slot_mu;
+static std::map<std::pair<int, void*>, StreamSlot*> g_slots;
+
+static ss_status stream_slot(cudaStream_t st, bool create, StreamSlot** out) {
+  *out = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SS_ERR_NO_DEVICE;
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  auto key = std::make_pair(dev, static_cast<void*>(st));
+  auto it = g_slots.find(key);
+  if (it != g_slots.end()) {
+    *out = it->second;
+    return SS_OK;
+  }
+  if (!create) return SS_OK;
+  StreamSlot* p = nullptr;
+  if (cudaMalloc(reinterpret_cast<void**>(&p), sizeof(StreamSlot)) != cudaSuccess) return SS_ERR_OOM;
+  if (cudaMemset(p, 0, sizeof(StreamSlot)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(p);
+    return SS_ERR_CUDA;
+  }
+  g_slots[key] = p;
+  *out = p;
+  return SS_OK;
+}
+
+// Enqueues everything after the set descriptors are in place.  ctl: where the
+// multi-block loop's control block lives (needed when big).
 static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o, const DevInfo& dev,
-                          bool big, cudaStream_t st) {
+                          bool big, cudaStream_t st, BigCtl* ctl = nullptr) {
   const LaunchHook hook{st};
   SS_CUDA(zero_fill(ws + L.ctrl, kCtrlBytes, st, hook));
   SS_CUDA(zero_fill(ws + L.mq_ready, (size_t)L.cap_mq * 4, st, hook));
   SS_CUDA(zero_fill(ws + L.wide, (size_t)c.num_sets * 4, st, hook));
   SS_CUDA(launch_init(c, st, hook));
   if (big) {
-    if (t_down.reserve(64 + (size_t)L.cap_big * sizeof(Task)) != SS_OK) return SS_ERR_OOM;
-    if (t_up.reserve((size_t)L.cap_big * sizeof(GenTask)) != SS_OK) return SS_ERR_OOM;
-    uint32_t cur = 0;
-    const uint32_t K = (2u << o.logv_big) - 1;
-    std::vector<GenTask> gts;
-    while (true) {
-      uint32_t* hcnt = static_cast<uint32_t*>(t_down.p);
-      Task* htasks = reinterpret_cast<Task*>(static_cast<uint8_t*>(t_down.p) + 64);
-      SS_CUDA(cudaMemcpyAsync(hcnt, ws + L.ctrl, 64, cudaMemcpyDeviceToHost, st));
-      SS_CUDA(cudaMemcpyAsync(htasks, ws + (cur ? L.big1 : L.big0), (size_t)L.cap_big * sizeof(Task),
-                              cudaMemcpyDeviceToHost, st));
-      SS_CUDA(cudaStreamSynchronize(st));
-      collect_profile();
-      if (hcnt[kCStatus]) break;
-      const uint32_t G = std::min(hcnt[cur ? kCBig1 : kCBig0], L.cap_big);
-      if (G == 0) break;
-      uint64_t total = 0;
-      for (uint32_t g = 0; g < G; ++g) total += htasks[g].len;
-      uint32_t R = o.R;
-      if (!R) {
-        const uint64_t per = total / ((uint64_t)dev.sms * 2 * kBlock) + 1;
-        R = (uint32_t)std::min<uint64_t>(kMaxRounds, std::max<uint64_t>(8, per));
+    if (!ctl) return SS_ERR_INVALID;
+    BigCtl v{};
+    v.c = c;
+    v.gt = reinterpret_cast<GenTask*>(ws + L.gen);
+    v.splitters = ws + L.spl;
+    v.counters = reinterpret_cast<uint32_t*>(ws + L.counters);
+    v.partials = reinterpret_cast<uint32_t*>(ws + L.partials);
+    v.gstart = reinterpret_cast<uint32_t*>(ws + L.gstart);
+    v.gdesc = reinterpret_cast<uint32_t*>(ws + L.gdesc);
+    v.ncounters_max = L.ncounters_max;
+    v.cap_big = L.cap_big;
+    v.R_fixed = o.R;
+    v.sms = (uint32_t)dev.sms;
+    v.K = (2u << o.logv_big) - 1;
+    v.cur = 0;
+    v.round = 0;
+    hook.run("init", [&] { k_set_ctl<<<1, 1, 0, st>>>(ctl, v); });
+    SS_CUDA(cudaGetLastError());
+    const uint32_t R_max = o.R ? o.R : kMaxRounds;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    SS_CUDA(cudaStreamIsCapturing(st, &cs));
+    if (cs == cudaStreamCaptureStatusActive) {
+      // the caller is capturing a graph: the loop becomes part of it
+      SS_CUDA(add_loop(st, ctl, o.logv_big, R_max, (uint32_t)dev.sms));
+    } else if (g_profiling.load()) {
+      // timed launch by launch: the host runs the rounds, reading each plan
+      if (t_down.reserve(64) != SS_OK) return SS_ERR_OOM;
+      uint32_t* hG = static_cast<uint32_t*>(t_down.p);
+      while (true) {
+        SS_CUDA(launch_big_plan(ctl, 0, false, st, hook));
+        SS_CUDA(cudaMemcpyAsync(hG, &ctl->G, 4, cudaMemcpyDeviceToHost, st));
+        SS_CUDA(cudaStreamSynchronize(st));
+        collect_profile();
+        if (*hG == 0) break;
+        SS_CUDA(launch_big_round(o.logv_big, ctl, R_max, (uint32_t)dev.sms, st, hook));
       }
-      const uint32_t T = kBlock * R;
-      gts.resize(G);
-      uint32_t tiles = 0, rec = 0;
-      uint64_t cnt = 0;
-      for (uint32_t g = 0; g < G; ++g) {
-        GenTask& x = gts[g];
-        x.t = htasks[g];
-        x.tile_start = tiles;
-        x.tiles = (x.t.len + T - 1) / T;
-        x.rec_base = rec;
-        x.cnt_base_lo = (uint32_t)cnt;
-        x.cnt_base_hi = (uint32_t)(cnt >> 32);
-        tiles += x.tiles;
-        rec += x.t.len;
-        cnt += (uint64_t)K * x.tiles;
-      }
-      if (cnt > L.ncounters_max) return SS_ERR_QUEUE_FULL;
-      std::memcpy(t_up.p, gts.data(), (size_t)G * sizeof(GenTask));
-      SS_CUDA(small_h2d(ws + L.gen, t_up.p, (size_t)G * sizeof(GenTask), st, hook));
-      SS_CUDA(zero_fill(ws + L.ctrl + 4 * (cur ? kCBig0 : kCBig1), 4, st, hook));
-      BigStepArgs a;
-      a.c = c;
-      a.c.big_cur = cur;
-      a.gt = reinterpret_cast<const GenTask*>(ws + L.gen);
-      a.G = G;
-      a.tiles = tiles;
-      a.R = R;
-      a.splitters = ws + L.spl;
-      a.counters = reinterpret_cast<uint32_t*>(ws + L.counters);
-      a.ncounters = cnt;
-      a.partials = reinterpret_cast<uint32_t*>(ws + L.partials);
-      a.gstart = reinterpret_cast<uint32_t*>(ws + L.gstart);
-      a.gdesc = reinterpret_cast<uint32_t*>(ws + L.gdesc);
-      a.next_big = cur ^ 1;
-      SS_CUDA(launch_big_step(o.logv_big, a, st, hook));
-      cur ^= 1;
+    } else {
+      cudaGraphExec_t exec = nullptr;
+      SS_CUDA(loop_exec(ctl, o.logv_big, R_max, (uint32_t)dev.sms, &exec));
+      SS_CUDA(cudaGraphLaunch(exec, st));
     }
   }
   const uint32_t qgrid = (uint32_t)(dev.sms * dev.queue_blocks[o.logv]);
@@ -446,20 +599,42 @@ static ss_status sort_device(const uint8_t* chars, const uint64_t* offsets, uint
     if (cudaMallocAsync(reinterpret_cast<void**>(&ws), L.total, st) != cudaSuccess) return SS_ERR_OOM;
     owned = true;
   }
+  StreamSlot* slot = nullptr;
+  if ((s = stream_slot(st, true, &slot)) != SS_OK) {
+    if (owned) cudaFreeAsync(ws, st);
+    return s;
+  }
   SetDesc sd{chars, offsets, perm, lcp, (uint32_t)n, o.cap, 0, dna};
   ss_status r = SS_OK;
   LaunchHook{st}.run("init", [&] { k_set_desc<<<1, 1, 0, st>>>(reinterpret_cast<SetDesc*>(ws + L.sets), sd); });
   if (cudaGetLastError() != cudaSuccess) r = SS_ERR_CUDA;
   SortCtx ctx = make_ctx(ws, L, 1, (uint32_t)n, o, big);
   ctx.dna = dna;
-  if (r == SS_OK) r = run_sort(ws, L, ctx, o, dev, big, st);
-  ss_status r2 = read_status(ws, L, st);
-  if (r == SS_OK) r = r2;
-  if (owned) {
-    cudaFreeAsync(ws, st);
-    cudaStreamSynchronize(st);
-  }
+  ctx.fold_status = &slot->status;  // the device status goes to the stream's status word
+  if (r == SS_OK) r = run_sort(ws, L, ctx, o, dev, big, st, &slot->ctl);
+  if (g_profiling.load()) read_status(ws, L, st);  // waits: per-kernel times and bytes
+  if (owned) cudaFreeAsync(ws, st);
   return r;
+}
+
+// Waits for the stream and returns the device status its sorts have left in
+// its status word since it was last read (clearing it).
+static ss_status take_stream_status(cudaStream_t st) {
+  StreamSlot* slot = nullptr;
+  stream_slot(st, false, &slot);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SS_ERR_CUDA;
+  collect_profile();
+  if (!slot) return SS_OK;
+  if (t_down.reserve(64) != SS_OK) return SS_ERR_OOM;
+  uint32_t* h = static_cast<uint32_t*>(t_down.p);
+  SS_CUDA(cudaMemcpyAsync(h, &slot->status, 4, cudaMemcpyDeviceToHost, st));
+  SS_CUDA(cudaStreamSynchronize(st));
+  const uint32_t v = *h;
+  if (v) {
+    SS_CUDA(cudaMemsetAsync(&slot->status, 0, 4, st));
+    SS_CUDA(cudaStreamSynchronize(st));
+  }
+  return map_status(v);
 }
 
 }  // namespace ss
@@ -472,6 +647,7 @@ struct ss_batch {
   ss::DevInfo dev;
   uint8_t* ws = nullptr;
   bool owned = false;
+  bool big = false;  // some set is larger than the multi-block threshold
   uint32_t num_sets = 0;
   uint32_t total = 0;
 };
@@ -498,7 +674,17 @@ const char* ss_status_string(ss_status s) {
   return "unknown status";
 }
 
-uint64_t ss_launch_count(void) { return g_launches.load(); }
+uint64_t ss_launch_count(void) {
+  // host launches, plus the kernels the loop graphs launched (counted on the
+  // device by their plan kernels; reading that count waits for the device)
+  uint64_t graph = 0;
+  int dev = 0;
+  {
+    std::lock_guard<std::mutex> lk(g_loop_mu);
+    if (!g_loops.empty() && cudaGetDevice(&dev) == cudaSuccess) graph = graph_launch_count();
+  }
+  return g_launches.load() + graph;
+}
 
 void ss_set_profiling(int enabled) { g_profiling.store(enabled ? 1 : 0); }
 
@@ -802,6 +988,8 @@ ss_status ss_suffix_array(const uint8_t* text, uint64_t n, uint32_t* out_sa, uin
   if (cudaStreamSynchronize(st) != cudaSuccess && ok) ok = false;
   collect_profile();
   if (s != SS_OK) return s;
+  const ss_status ds = take_stream_status(st);  // device status of the rounds' sorts
+  if (ds != SS_OK) return ds;
   return ok ? SS_OK : SS_ERR_CUDA;
 }
 
@@ -854,6 +1042,8 @@ ss_status ss_sort_dna(const uint8_t* chars, uint64_t chars_len, const uint64_t* 
     if (r == SS_OK) r = SS_ERR_CUDA;
   cudaFreeAsync(d, st);
   if (r == SS_OK && hbad) r = SS_ERR_INVALID;
+  const ss_status ds = take_stream_status(st);
+  if (r == SS_OK) r = ds;
   return r;
 }
 
@@ -1076,27 +1266,34 @@ ss_status ss_sort_host(const uint8_t* chars, uint64_t chars_len, const uint64_t*
   }
   cudaFreeAsync(d, st);
   if (cudaStreamSynchronize(st) != cudaSuccess && r == SS_OK) r = SS_ERR_CUDA;
+  const ss_status ds = take_stream_status(st);
+  if (r == SS_OK) r = ds;
   return r;
 }
 
-static ss_status batch_geometry(const ss_set* sets, uint32_t num_sets, uint64_t* total) {
+// Total strings of a batch, and whether some set takes multi-block steps.
+static ss_status batch_geometry(const ss_set* sets, uint32_t num_sets, const Opts& o, uint64_t* total, bool* big) {
   if (num_sets && !sets) return SS_ERR_INVALID;
   uint64_t t = 0;
+  bool b = false;
   for (uint32_t i = 0; i < num_sets; ++i) {
     const ss_set& s = sets[i];
     if (s.n && (!s.chars || !s.offsets || !s.out_perm)) return SS_ERR_INVALID;
     t += s.n;
+    b = b || s.n > o.big_thr;
   }
   if (t >= 0xFFFFFFFFull) return SS_ERR_TOO_LARGE;
   *total = t;
+  *big = b;
   return SS_OK;
 }
 
 size_t ss_batch_workspace_size(const ss_set* sets, uint32_t num_sets, const ss_options* opt) {
   Opts o;
   uint64_t total = 0;
-  if (resolve_opts(opt, o) != SS_OK || batch_geometry(sets, num_sets, &total) != SS_OK) return 0;
-  return make_layout(total, num_sets, o, false).total;
+  bool big = false;
+  if (resolve_opts(opt, o) != SS_OK || batch_geometry(sets, num_sets, o, &total, &big) != SS_OK) return 0;
+  return make_layout(total, num_sets, o, big).total;
 }
 
 ss_status ss_batch_create(const ss_set* sets, uint32_t num_sets, const ss_options* opt, ss_batch** out) {
@@ -1106,9 +1303,9 @@ ss_status ss_batch_create(const ss_set* sets, uint32_t num_sets, const ss_option
   ss_status s = resolve_opts(opt, b.o);
   if (s != SS_OK) return s;
   uint64_t total = 0;
-  if ((s = batch_geometry(sets, num_sets, &total)) != SS_OK) return s;
+  if ((s = batch_geometry(sets, num_sets, b.o, &total, &b.big)) != SS_OK) return s;
   if ((s = device_info(b.dev)) != SS_OK) return s;
-  b.L = make_layout(total, num_sets, b.o, false);
+  b.L = make_layout(total, num_sets, b.o, b.big);
   if (opt && opt->workspace) {
     if (opt->workspace_bytes < b.L.total) return SS_ERR_INVALID;
     b.ws = static_cast<uint8_t*>(opt->workspace);
@@ -1142,8 +1339,8 @@ ss_status ss_batch_run(ss_batch* b, void* stream) {
     g_stream_last[stream] = b;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  SortCtx c = make_ctx(b->ws, b->L, b->num_sets, b->total, b->o, false);
-  return run_sort(b->ws, b->L, c, b->o, b->dev, false, st);
+  SortCtx c = make_ctx(b->ws, b->L, b->num_sets, b->total, b->o, b->big);
+  return run_sort(b->ws, b->L, c, b->o, b->dev, b->big, st, reinterpret_cast<BigCtl*>(b->ws + b->L.bigctl));
 }
 
 ss_status ss_batch_status(ss_batch* b, void* stream) {
@@ -1159,6 +1356,7 @@ ss_status ss_batch_destroy(ss_batch* b) {
     for (auto it = g_stream_last.begin(); it != g_stream_last.end();)
       it = (it->second == b) ? g_stream_last.erase(it) : std::next(it);
   }
+  if (b->big) drop_loops(b->ws + b->L.bigctl);
   if (b->owned) cudaFree(b->ws);
   delete b;
   return SS_OK;
@@ -1171,8 +1369,10 @@ ss_status ss_stream_status(void* stream) {
     auto it = g_stream_last.find(stream);
     if (it != g_stream_last.end()) b = it->second;
   }
-  if (b) return ss_batch_status(b, stream);
-  return cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) == cudaSuccess ? SS_OK : SS_ERR_CUDA;
+  // the sorts' status word of the stream, then the last batch run on it
+  const ss_status s = take_stream_status(static_cast<cudaStream_t>(stream));
+  if (s != SS_OK || !b) return s;
+  return ss_batch_status(b, stream);
 }
 
 ss_status ss_sort_batch(const ss_set* sets, uint32_t num_sets, const ss_options* opt, void* stream) {

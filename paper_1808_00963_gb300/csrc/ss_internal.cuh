@@ -20,6 +20,7 @@ namespace ss {
 constexpr uint32_t kNoCap = 0xFFFFFFFFu;
 constexpr uint32_t kMaxDepth = (1u << 30) - 16;  // deeper strings: SS_ERR_TOO_LARGE
 constexpr uint32_t kLcpMark = 0x80000000u;        // out_lcp[j] = mark | depth: fix up later
+constexpr uint32_t kLcpWide = 0x40000000u;        // ... the two strings differ within 2 keys (a wide step)
 
 // Device status bits (latched with atomicOr; the host maps them to ss_status).
 constexpr uint32_t kStQueueFull = 1u << 0;
@@ -111,6 +112,7 @@ struct SortCtx {
   uint32_t num_sets;
   uint32_t total;          // records over all sets
   Rec* rec[2];
+  uint2* wid[2];           // (idx, off) of a record held in the wide form (multi-block subsets)
   uint32_t* wide;          // per set: 1 if some offset is 2^32 or more (then off is not enough)
   uint16_t* bucket_of;     // bucket index of each record (array o of Algorithm 4.1)
   uint32_t* status;
@@ -128,6 +130,7 @@ struct SortCtx {
   uint32_t big_cur;        // which big[] list the current step reads
   uint32_t dna;            // every set holds 3-bit character codes (SetDesc::dna)
   uint64_t wait_ns;        // bound on every device-side wait (then kStTimeout)
+  uint32_t* fold_status;   // if set: the last kernel ORs *status into it (the stream's status word)
 };
 
 // ---------------------------------------------------------------------------
@@ -360,6 +363,91 @@ __device__ __forceinline__ uint32_t load_key_windows(const uint8_t* chars, uint6
     ended = ended || key_end(w[j], 1);
   }
   return KW;
+}
+
+// ---------------------------------------------------------------------------
+// Wide keys of the multi-block steps: 16 characters (two bytes-caches) or 42
+// packed DNA characters (two code words) per key, so that a step takes twice
+// the characters of a narrow one (chars_h of Algorithm 4.1 with w = 16; the
+// super-alphabet view of Section 4.4).  A key is compared as one 128-bit
+// integer (first character most significant).  A record of a multi-block
+// subset is held in the wide form: its key fills the 16-byte record slot
+// (high word first), and (idx, off) sit at the same position of wid[].
+
+typedef unsigned __int128 u128;
+
+__device__ __forceinline__ uint64_t k_hi(u128 k) { return (uint64_t)(k >> 64); }
+__device__ __forceinline__ uint64_t k_lo(u128 k) { return (uint64_t)k; }
+__device__ __forceinline__ u128 make_k(uint64_t hi, uint64_t lo) { return ((u128)hi << 64) | lo; }
+
+__device__ __forceinline__ u128 load_wkey(const Rec* p) {
+  const uint4 v = *reinterpret_cast<const uint4*>(p);
+  return make_k(((uint64_t)v.y << 32) | v.x, ((uint64_t)v.w << 32) | v.z);
+}
+
+__device__ __forceinline__ void store_wkey(Rec* p, u128 k) {
+  const uint64_t hi = k_hi(k), lo = k_lo(k);
+  *reinterpret_cast<uint4*>(p) = make_uint4((uint32_t)hi, (uint32_t)(hi >> 32), (uint32_t)lo, (uint32_t)(lo >> 32));
+}
+
+// Key operations by key type (narrow: uint64_t, wide: u128) and encoding.
+template <typename K>
+struct KeyOps;
+
+template <>
+struct KeyOps<uint64_t> {
+  static __device__ __forceinline__ uint32_t width(uint32_t dna) { return key_width(dna); }
+  static __device__ __forceinline__ uint32_t lcp(uint64_t a, uint64_t b, uint32_t dna) { return key_lcp(a, b, dna); }
+  static __device__ __forceinline__ bool end(uint64_t c, uint32_t dna) { return key_end(c, dna); }
+  static __device__ __forceinline__ uint32_t nnz(uint64_t c, uint32_t dna) { return key_nnz(c, dna); }
+  static __device__ __forceinline__ uint32_t top(uint64_t c, int bits) { return (uint32_t)(c >> (64 - bits)); }
+  static __device__ __forceinline__ uint64_t shfl_xor(uint64_t v, int m) { return __shfl_xor_sync(0xFFFFFFFFu, v, m); }
+  static __device__ __forceinline__ uint64_t ones() { return ~0ull; }
+};
+
+template <>
+struct KeyOps<u128> {
+  static __device__ __forceinline__ uint32_t width(uint32_t dna) { return 2 * key_width(dna); }
+  static __device__ __forceinline__ uint32_t lcp(u128 a, u128 b, uint32_t dna) {
+    return k_hi(a) != k_hi(b) ? key_lcp(k_hi(a), k_hi(b), dna) : key_width(dna) + key_lcp(k_lo(a), k_lo(b), dna);
+  }
+  // the low word ends in the end code iff the string ends inside the key
+  // (every position after the end is zero)
+  static __device__ __forceinline__ bool end(u128 c, uint32_t dna) { return key_end(k_lo(c), dna); }
+  static __device__ __forceinline__ uint32_t nnz(u128 c, uint32_t dna) {
+    return key_end(k_hi(c), dna) ? key_nnz(k_hi(c), dna) : key_width(dna) + key_nnz(k_lo(c), dna);
+  }
+  static __device__ __forceinline__ uint32_t top(u128 c, int bits) { return (uint32_t)(k_hi(c) >> (64 - bits)); }
+  static __device__ __forceinline__ u128 shfl_xor(u128 v, int m) {
+    return make_k(__shfl_xor_sync(0xFFFFFFFFu, k_hi(v), m), __shfl_xor_sync(0xFFFFFFFFu, k_lo(v), m));
+  }
+  static __device__ __forceinline__ u128 ones() { return ~(u128)0; }
+};
+
+// The wide key of the string at `off` from depth h (precondition as
+// load_cache).  Bytes: the 16 characters are fetched with the three aligned
+// words that cover them in one round trip when they lie in the 4 KiB block of
+// byte h (load_windows); otherwise word by word while the string continues.
+__device__ __forceinline__ u128 load_key128(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
+                                            uint32_t dna) {
+  if (dna) {
+    const uint64_t hi = dna_key(chars, off, h, cap);
+    const uint64_t lo = key_end(hi, 1) ? 0ull : dna_key(chars, off, h + kDnaWidth, cap);
+    return make_k(hi, lo);
+  }
+  uint64_t w[2];
+  const uint32_t nw = load_windows<2>(chars, off, h, cap, w);
+  if (nw == 0) w[0] = load_cache(chars, off, h, cap);
+  if (nw < 2) w[1] = has_nul(w[0]) ? 0ull : load_cache(chars, off, h + 8, cap);
+  return make_k(w[0], w[1]);
+}
+
+// The narrow key (8 characters) d characters into a byte-encoded wide key,
+// for d <= 8 (no memory access).
+__device__ __forceinline__ uint64_t narrow_at(u128 k, uint32_t d) {
+  if (d == 0) return k_hi(k);
+  if (d >= 8) return k_lo(k);
+  return (k_hi(k) << (8 * d)) | (k_lo(k) >> (64 - 8 * d));
 }
 
 // Counter-based hash for sample positions (SplitMix64 finaliser).

@@ -19,24 +19,58 @@ struct LaunchHook {
   void run(const char* name, const std::function<void()>& launch) const;
 };
 
-struct BigStepArgs {
+// Control block of the multi-block steps in device memory.  The host fills
+// the first part once per sort; k_big_plan writes the plan of each round from
+// the list of big subsets the previous round left, and every kernel of the
+// round reads it there, so rounds follow one another with no host in the loop
+// (Section 4.2.8: the fully parallel levels need no sequential coordinator).
+struct BigCtl {
   SortCtx c;
-  const GenTask* gt;      // G tasks (device)
-  uint32_t G;
-  uint32_t tiles;         // total tiles over the G tasks
+  GenTask* gt;            // cap_big tasks of the current round
+  void* splitters;        // cap_big * big_splitters_bytes(logv)
+  uint32_t* counters;     // [task][bucket][tile] counters of the round
+  uint32_t* partials;     // ncounters_max / 4096 + 2
+  uint32_t* gstart;       // cap_big * KP bucket starts
+  uint32_t* gdesc;        // cap_big * KP bucket descriptors
+  uint64_t ncounters_max;
+  uint32_t cap_big;
+  uint32_t R_fixed;       // tile rounds; 0: chosen per round from the strings in big subsets
+  uint32_t sms;
+  uint32_t K;             // buckets per step, 2^(logv + 1) - 1
+  // the plan of the current round (k_big_plan)
+  uint32_t cur;           // big list the next plan reads
+  uint32_t next_big;      // big list the current round's new big subsets go to
+  uint32_t round;
+  uint32_t G;             // big subsets of the round (0: the loop ends)
+  uint32_t tiles;         // tiles over them
   uint32_t R;             // tile = 256 * R records
-  void* splitters;        // G * big_splitters_bytes(logv)
-  uint32_t* counters;     // ncounters, [task][bucket][tile]
   uint64_t ncounters;
-  uint32_t* partials;     // ceil(ncounters / 4096)
-  uint32_t* gstart;       // G * KP
-  uint32_t* gdesc;        // G * KP
-  uint32_t next_big;      // big list that receives the next round's tasks
+  // work counters of the round's kernels (zeroed by the plan): blocks take
+  // the next subset or tile from them, so that uneven tiles balance out
+  uint32_t next_item[4];  // sample, classify, emit, scatter
 };
+
+// Most rounds of multi-block steps one sort may take (each advances every big
+// subset by at least one character; a subset sharing more than about 2^20
+// characters is reported as SS_ERR_TOO_LARGE).
+constexpr uint32_t kMaxBigRounds = 1u << 20;
+
+// Kernel launches of one multi-block round after its plan: sample, classify,
+// the three prefix-sum kernels, emit and scatter.
+constexpr uint32_t kBigRoundKernels = 7;
 
 size_t big_splitters_bytes(int logv);
 size_t big_scatter_smem(int logv, uint32_t R);
-cudaError_t launch_big_step(int logv, const BigStepArgs& a, cudaStream_t st, const LaunchHook& hook);
+// The plan of the next round; with use_cond it also sets the loop graph's
+// condition (1 while big subsets remain).
+cudaError_t launch_big_plan(BigCtl* ctl, uint64_t cond_handle, bool use_cond, cudaStream_t st,
+                            const LaunchHook& hook);
+// The kernels of one round (they do nothing when the plan found no subset).
+cudaError_t launch_big_round(int logv, BigCtl* ctl, uint32_t R_max, uint32_t sms, cudaStream_t st,
+                             const LaunchHook& hook);
+// Kernels the loop graphs of this device have launched so far (their plan
+// kernels count them on the device; reading the count waits for the device).
+uint64_t graph_launch_count();
 
 // Persistent work-queue kernel (single-block S^5 steps).
 size_t queue_smem(int logv);

@@ -37,8 +37,14 @@ __global__ void __launch_bounds__(kBlock) k_init(SortCtx c) {
     const uint32_t i = r - sd.base;
     const uint64_t off = sd.offsets[i];
     if ((off >> 32) && !c.wide[s]) atomicOr(c.wide + s, 1u);
-    store_rec(c.rec[0] + r, load_key(sd.chars, off, 0, sd.cap, sd.dna), i, (uint32_t)off);
-    bytes += 32;  // offset 8 + 8 characters read, record 16 written
+    if (c.big_enabled && sd.n > c.big_threshold) {  // a multi-block root: wide records
+      store_wkey(c.rec[0] + r, load_key128(sd.chars, off, 0, sd.cap, sd.dna));
+      c.wid[0][r] = make_uint2(i, (uint32_t)off);
+      bytes += 48;  // offset 8 + 16 characters read, wide record 24 written
+    } else {
+      store_rec(c.rec[0] + r, load_key(sd.chars, off, 0, sd.cap, sd.dna), i, (uint32_t)off);
+      bytes += 32;  // offset 8 + 8 characters read, record 16 written
+    }
   }
   account(c, kKInit, bytes);
 }
@@ -572,6 +578,22 @@ __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint
 __global__ void __launch_bounds__(kBlock) k_lcp_fix(SortCtx c) {
   const uint32_t stride = gridDim.x * blockDim.x;
   unsigned long long bytes = 0;
+  // the last kernel of a sort: every other one has finished, so the sort's
+  // status is final and goes into the stream's status word
+  const uint32_t status = *c.status;
+  if (c.fold_status && blockIdx.x == 0 && threadIdx.x == 0 && status) atomicOr(c.fold_status, status);
+  if (status) {
+    // a device-side error stopped the sort part way: positions it did not
+    // reach hold whatever the output buffers held.  Give every set the
+    // identity permutation and zero LCPs instead, so that no later kernel
+    // (this one, or a caller's) follows an index that is out of range.
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < c.total; r += stride) {
+      const SetDesc sd = c.sets[c.num_sets == 1 ? 0 : find_set(c, r)];
+      sd.perm[r - sd.base] = r - sd.base;
+      if (sd.lcp) sd.lcp[r - sd.base] = 0;
+    }
+    return;
+  }
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < c.total; r += stride) {
     const uint32_t s = c.num_sets == 1 ? 0 : find_set(c, r);
     const SetDesc sd = c.sets[s];
@@ -580,11 +602,20 @@ __global__ void __launch_bounds__(kBlock) k_lcp_fix(SortCtx c) {
     const uint32_t v = sd.lcp[j];
     bytes += 4;
     if (j == 0 || !(v & kLcpMark)) continue;
-    const uint32_t h = v & ~kLcpMark;
-    const uint64_t a = load_key(sd.chars, sd.offsets[sd.perm[j - 1]], h, sd.cap, sd.dna);
-    const uint64_t b = load_key(sd.chars, sd.offsets[sd.perm[j]], h, sd.cap, sd.dna);
-    sd.lcp[j] = h + key_lcp(a, b, sd.dna);
-    bytes += 44;  // lcp 4 written; per string: perm 4 + offset 8 + 8 characters read
+    const uint32_t h = v & ~(kLcpMark | kLcpWide);
+    const uint32_t pa = sd.perm[j - 1], pb = sd.perm[j];
+    if (pa >= sd.n || pb >= sd.n) continue;  // cannot happen after a sort without errors
+    if (v & kLcpWide) {  // a boundary of a multi-block step: the strings differ within its wide key
+      const u128 a = load_key128(sd.chars, sd.offsets[pa], h, sd.cap, sd.dna);
+      const u128 b = load_key128(sd.chars, sd.offsets[pb], h, sd.cap, sd.dna);
+      sd.lcp[j] = h + KeyOps<u128>::lcp(a, b, sd.dna);
+      bytes += 60;  // lcp 4 written; per string: perm 4 + offset 8 + 16 characters read
+    } else {
+      const uint64_t a = load_key(sd.chars, sd.offsets[pa], h, sd.cap, sd.dna);
+      const uint64_t b = load_key(sd.chars, sd.offsets[pb], h, sd.cap, sd.dna);
+      sd.lcp[j] = h + key_lcp(a, b, sd.dna);
+      bytes += 44;  // lcp 4 written; per string: perm 4 + offset 8 + 8 characters read
+    }
   }
   account(c, kKLcpFix, bytes);
 }

@@ -24,18 +24,18 @@ struct Geo {
   static constexpr uint32_t S = 2u << LOGV;         // sample size alpha * (v + 1), alpha = 2
 };
 
-// Splitters of one step.
-template <int LOGV>
+// Splitters of one step (K: uint64_t for narrow keys, u128 for wide ones).
+template <int LOGV, typename K = uint64_t>
 struct Splitters {
-  uint64_t tree[Geo<LOGV>::V + 1];  // t[1..v], level order (t[0] unused)
-  uint64_t x[Geo<LOGV>::V + 1];     // x_0..x_{v-1} sorted; x[v] unused
+  K tree[Geo<LOGV>::V + 1];  // t[1..v], level order (t[0] unused)
+  K x[Geo<LOGV>::V + 1];     // x_0..x_{v-1} sorted; x[v] unused
   uint8_t hp[Geo<LOGV>::V + 1];     // h'_0..h'_v: lcp of neighbouring splitters
 };
 
 // Scratch of the splitter construction (may alias other shared memory).
-template <int LOGV>
+template <int LOGV, typename K = uint64_t>
 struct BuildScratch {
-  uint64_t sample[Geo<LOGV>::S];
+  K sample[Geo<LOGV>::S];
   uint16_t lo[Geo<LOGV>::S];   // first sample position with a key >= sample[i]
   uint16_t hi[Geo<LOGV>::S];   // first sample position with a key >  sample[i]
 };
@@ -43,8 +43,8 @@ struct BuildScratch {
 // Ascending bitonic sort of the 32 * E keys a warp holds, E per lane in
 // index order lane * E + e: partners closer than E sit in the same lane,
 // farther ones are exchanged with shuffles.
-template <int E>
-__device__ __forceinline__ void warp_bitonic_u64(uint64_t (&v)[E]) {
+template <int E, typename K>
+__device__ __forceinline__ void warp_bitonic(K (&v)[E]) {
   constexpr uint32_t N = 32 * E;
   const uint32_t lane = threadIdx.x & 31;
 #pragma unroll
@@ -56,7 +56,7 @@ __device__ __forceinline__ void warp_bitonic_u64(uint64_t (&v)[E]) {
         const bool lower = (lane & lj) == 0;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, v[e], lj);
+          const K o = KeyOps<K>::shfl_xor(v[e], (int)lj);
           const bool up = ((lane * E + e) & k) == 0;
           const bool take_min = lower == up;
           v[e] = take_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
@@ -68,7 +68,7 @@ __device__ __forceinline__ void warp_bitonic_u64(uint64_t (&v)[E]) {
             const int f = e | (int)j;
             const bool up = ((lane * E + e) & k) == 0;
             if ((v[e] > v[f]) == up) {
-              const uint64_t t = v[e];
+              const K t = v[e];
               v[e] = v[f];
               v[f] = t;
             }
@@ -94,24 +94,25 @@ __device__ __forceinline__ void warp_bitonic_u64(uint64_t (&v)[E]) {
 // keys around every sample position known, each tree node finds its range by
 // walking from the root along its level-order index, so the recursion needs
 // no step-by-step synchronisation.  Ends with __syncthreads().
-template <int LOGV>
-__device__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint64_t hseed,
-                                Splitters<LOGV>& sp, BuildScratch<LOGV>& bs, uint32_t dna) {
+// key_at(pos) gives the key of the subset's record pos.
+template <int LOGV, typename K, typename KeyAt>
+__device__ void build_splitters_k(KeyAt&& key_at, uint32_t len, uint64_t hseed, Splitters<LOGV, K>& sp,
+                                  BuildScratch<LOGV, K>& bs, uint32_t dna) {
   using G = Geo<LOGV>;
   constexpr uint32_t C = G::S / kWarps;  // keys per warp
   constexpr int E = (int)(C / 32);       // keys per lane
   static_assert(E >= 1 && C % 32 == 0, "sample does not split into whole warps");
   const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint64_t v[E];
+  K v[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) {
     const uint32_t i = w * C + lane * E + e;
     const uint64_t h = mix64(hseed + i);
     const uint32_t pos = (uint32_t)(((h >> 32) * (uint64_t)len) >> 32);
-    v[e] = recs[pos].key;
+    v[e] = key_at(pos);
   }
-  warp_bitonic_u64<E>(v);
-  uint64_t* s = bs.sample;
+  warp_bitonic<E, K>(v);
+  K* s = bs.sample;
 #pragma unroll
   for (int e = 0; e < E; ++e) s[w * C + lane * E + e] = v[e];
   __syncthreads();
@@ -122,7 +123,7 @@ __device__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint
 #pragma unroll
     for (uint32_t ww = 0; ww < kWarps; ++ww) {
       if (ww == w) continue;
-      const uint64_t* ch = s + ww * C;
+      const K* ch = s + ww * C;
       uint32_t a = 0, b = C;
       if (ww < w) {
         while (a < b) { const uint32_t m = (a + b) >> 1; if (ch[m] <= v[e]) a = m + 1; else b = m; }
@@ -138,7 +139,7 @@ __device__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint
   for (int e = 0; e < E; ++e) s[rank[e]] = v[e];
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < G::S; i += blockDim.x) {
-    const uint64_t val = s[i];
+    const K val = s[i];
     uint32_t a = 0, b = i;
     while (a < b) { const uint32_t m = (a + b) >> 1; if (s[m] < val) a = m + 1; else b = m; }
     bs.lo[i] = (uint16_t)a;
@@ -166,15 +167,22 @@ __device__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint
         a = b;
       }
     }
-    const uint64_t val = a < b ? s[(a + b) >> 1] : (b < G::S ? s[b] : ~0ull);
+    const K val = a < b ? s[(a + b) >> 1] : (b < G::S ? s[b] : KeyOps<K>::ones());
     sp.tree[i] = val;
     sp.x[(2 * (i - (1u << l)) + 1) * (1u << (LOGV - 1 - l)) - 1] = val;
   }
   __syncthreads();
   for (uint32_t r = threadIdx.x; r <= G::V; r += blockDim.x)
-    sp.hp[r] = (r == 0 || r == G::V) ? 0 : (uint8_t)key_lcp(sp.x[r - 1], sp.x[r], dna);
+    sp.hp[r] = (r == 0 || r == G::V) ? 0 : (uint8_t)KeyOps<K>::lcp(sp.x[r - 1], sp.x[r], dna);
   if (threadIdx.x == 0) sp.tree[0] = 0;
   __syncthreads();
+}
+
+// The sampling steps for a subset of narrow records.
+template <int LOGV>
+__device__ __forceinline__ void build_splitters(const Rec* __restrict__ recs, uint32_t len, uint64_t hseed,
+                                                Splitters<LOGV>& sp, BuildScratch<LOGV>& bs, uint32_t dna) {
+  build_splitters_k<LOGV, uint64_t>([&](uint32_t pos) { return recs[pos].key; }, len, hseed, sp, bs, dna);
 }
 
 // Lemma 4.1: one-based level-order index l <-> one-based pre-order index p
@@ -208,11 +216,11 @@ constexpr uint32_t kClassifyUIJ = 3;  // UI entered through a jump table over th
 constexpr int kJumpBits = 12;
 constexpr uint32_t kJumpSize = 1u << kJumpBits;
 
-template <int LOGV>
-__device__ __forceinline__ uint32_t jump_entry(uint32_t p, const uint64_t* tree) {
+template <int LOGV, typename K>
+__device__ __forceinline__ uint32_t jump_entry(uint32_t p, const K* tree) {
   uint32_t i = 1;
   while (i < (1u << LOGV)) {
-    const uint32_t tp = (uint32_t)(tree[i] >> (64 - kJumpBits));
+    const uint32_t tp = KeyOps<K>::top(tree[i], kJumpBits);
     if (p == tp) break;
     i = 2 * i + (p > tp ? 1u : 0u);
   }
@@ -221,10 +229,9 @@ __device__ __forceinline__ uint32_t jump_entry(uint32_t p, const uint64_t* tree)
 
 // The UI classification entered at the jump table's node: the remaining
 // levels are predicated off for keys already at a leaf.
-template <int LOGV>
-__device__ __forceinline__ uint32_t classify_jump(uint64_t c, const uint64_t* tree, const uint64_t* x,
-                                                  const uint16_t* jump) {
-  uint32_t i = jump[c >> (64 - kJumpBits)];
+template <int LOGV, typename K>
+__device__ __forceinline__ uint32_t classify_jump(K c, const K* tree, const K* x, const uint16_t* jump) {
+  uint32_t i = jump[KeyOps<K>::top(c, kJumpBits)];
 #pragma unroll
   for (int l = 0; l < LOGV; ++l)
     if (i < (1u << LOGV)) i = 2 * i + (c > tree[i] ? 1u : 0u);
@@ -236,15 +243,14 @@ __device__ __forceinline__ uint32_t classify_jump(uint64_t c, const uint64_t* tr
 // The classification of one key in Algorithm 4.1: branch-free descent of the level-order tree,
 // i := 2i + [c > t_i] (the reading of its descent step under which bucket b_{2r} holds
 // x_{r-1} < c < x_r), then the single equality test with x_r.
-template <int LOGV>
-__device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, const uint64_t* x,
-                                             uint32_t variant = kClassifyUI) {
+template <int LOGV, typename K>
+__device__ __forceinline__ uint32_t classify(K c, const K* tree, const K* x, uint32_t variant = kClassifyUI) {
   uint32_t i = 1;
   if (variant == kClassifyE) {
     uint32_t eq = 0;
 #pragma unroll
     for (int l = 0; l < LOGV; ++l) {
-      const uint64_t t = tree[i];
+      const K t = tree[i];
       if (!eq && c == t) eq = i;
       i = 2 * i + (c > t ? 1u : 0u);
     }
@@ -262,9 +268,9 @@ __device__ __forceinline__ uint32_t classify(uint64_t c, const uint64_t* tree, c
 // Buckets of U keys.  For S5-UI the U descents advance one tree level at a
 // time together, so that U independent shared-memory loads are in flight per
 // level rather than one (20 M URL strings: the classification 0.64 -> 0.55 ms).
-template <int LOGV, int U>
-__device__ __forceinline__ void classify_batch(const uint64_t (&k)[U], uint32_t (&b)[U], const uint64_t* tree,
-                                               const uint64_t* x, uint32_t variant, const uint16_t* jump) {
+template <int LOGV, int U, typename K>
+__device__ __forceinline__ void classify_batch(const K (&k)[U], uint32_t (&b)[U], const K* tree, const K* x,
+                                               uint32_t variant, const uint16_t* jump) {
   if (variant == kClassifyUI) {
     uint32_t i[U];
 #pragma unroll
@@ -283,31 +289,30 @@ __device__ __forceinline__ void classify_batch(const uint64_t (&k)[U], uint32_t 
   }
 #pragma unroll
   for (int u = 0; u < U; ++u)
-    b[u] = (variant == kClassifyUIJ && jump) ? classify_jump<LOGV>(k[u], tree, x, jump)
-                                             : classify<LOGV>(k[u], tree, x, variant);
+    b[u] = (variant == kClassifyUIJ && jump) ? classify_jump<LOGV, K>(k[u], tree, x, jump)
+                                             : classify<LOGV, K>(k[u], tree, x, variant);
 }
 
 // Classifies n keys (the classification loop of Algorithm 4.1): writes the bucket of
 // keys[p] to bo[p] and counts it in hist (shared memory, warp-aggregated
 // atomics).  Each thread loads 8 keys before descending the tree for them,
 // so that the loads of a batch overlap.  Returns this thread's records.
-template <int LOGV>
-__device__ __forceinline__ uint32_t classify_count(const Rec* __restrict__ recs, uint16_t* __restrict__ bo,
-                                                   uint32_t n, const uint64_t* tree, const uint64_t* x,
-                                                   uint32_t* hist, uint32_t variant,
-                                                   const uint16_t* jump = nullptr) {
+template <int LOGV, typename K, typename KeyAt>
+__device__ __forceinline__ uint32_t classify_count_k(KeyAt&& key_at, uint16_t* __restrict__ bo, uint32_t n,
+                                                     const K* tree, const K* x, uint32_t* hist, uint32_t variant,
+                                                     const uint16_t* jump) {
   constexpr int U = 8;
   uint32_t mine = 0;
   const uint32_t lim = (n + kBlock - 1) / kBlock * kBlock;
   for (uint32_t p0 = threadIdx.x; p0 < lim; p0 += U * kBlock) {
-    uint64_t k[U];
+    K k[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t p = p0 + u * kBlock;
-      k[u] = p < n ? recs[p].key : 0ull;
+      k[u] = p < n ? key_at(p) : (K)0;
     }
     uint32_t bb[U];
-    classify_batch<LOGV, U>(k, bb, tree, x, variant, jump);
+    classify_batch<LOGV, U, K>(k, bb, tree, x, variant, jump);
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const uint32_t p = p0 + u * kBlock;
@@ -325,20 +330,29 @@ __device__ __forceinline__ uint32_t classify_count(const Rec* __restrict__ recs,
   return mine;
 }
 
+template <int LOGV>
+__device__ __forceinline__ uint32_t classify_count(const Rec* __restrict__ recs, uint16_t* __restrict__ bo,
+                                                   uint32_t n, const uint64_t* tree, const uint64_t* x,
+                                                   uint32_t* hist, uint32_t variant,
+                                                   const uint16_t* jump = nullptr) {
+  return classify_count_k<LOGV, uint64_t>([&](uint32_t p) { return recs[p].key; }, bo, n, tree, x, hist, variant,
+                                          jump);
+}
+
 // What happens to bucket b of a step at depth h (Output of Algorithm 4.1 and
 // Section 4.2.3): an even bucket b_{2r} continues at depth h + h'_r, an
 // equality bucket at h + 8, unless its splitter holds the terminator (then all
 // members are equal strings and the bucket is finished; their LCP is their
 // length); a single string is finished.
-template <int LOGV>
+template <int LOGV, typename K>
 __device__ __forceinline__ uint32_t bucket_desc(uint32_t b, uint32_t size, uint32_t depth,
-                                                const Splitters<LOGV>& sp, uint32_t dna) {
+                                                const Splitters<LOGV, K>& sp, uint32_t dna) {
   const uint32_t r = b >> 1;
   if (b & 1) {
-    const uint64_t xr = sp.x[r];
-    if (key_end(xr, dna)) return kFin | kNulEq | (depth + key_nnz(xr, dna));
+    const K xr = sp.x[r];
+    if (KeyOps<K>::end(xr, dna)) return kFin | kNulEq | (depth + KeyOps<K>::nnz(xr, dna));
     if (size == 1) return kFin;
-    return depth + key_width(dna);
+    return depth + KeyOps<K>::width(dna);
   }
   if (size == 1) return kFin;
   return depth + sp.hp[r];
@@ -361,7 +375,7 @@ constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 // ranks come from __match_any_sync, so equal buckets keep input order.
 // move(p[], b[], dest[]) is called with kMoveBatch rounds of one warp at a time
 // (p = kInvalid for lanes without a record).  Ends with __syncthreads().
-template <int LOGV, typename Move>
+template <int LOGV, int MB = kMoveBatch, typename Move>
 __device__ void tile_scatter(const uint16_t* tb, uint32_t tl, uint32_t R, uint32_t* base,
                              uint32_t* cntw, Move&& move) {
   using G = Geo<LOGV>;
@@ -391,10 +405,10 @@ __device__ void tile_scatter(const uint16_t* tb, uint32_t tl, uint32_t R, uint32
   }
   __syncthreads();
   const uint32_t lt = lanemask_lt();
-  for (uint32_t r0 = 0; r0 < R; r0 += kMoveBatch) {
-    uint32_t pp[kMoveBatch], bb[kMoveBatch], dd[kMoveBatch];
+  for (uint32_t r0 = 0; r0 < R; r0 += MB) {
+    uint32_t pp[MB], bb[MB], dd[MB];
 #pragma unroll
-    for (int u = 0; u < kMoveBatch; ++u) {
+    for (int u = 0; u < MB; ++u) {
       const uint32_t r = r0 + u;
       const uint32_t p = p0 + r * 32 + lane;
       const bool valid = r < R && p < tl;
@@ -477,14 +491,88 @@ __device__ __forceinline__ uint32_t move_batch(const SortCtx& c, const SetDesc& 
   return bytes;
 }
 
+// move_batch for records of a multi-block subset, held in the wide form (wide
+// key in the record slot, (idx, off) in wid[]).  A record whose new bucket is
+// itself a multi-block subset stays wide (key reloaded at the new depth unless
+// the depth is unchanged); otherwise it becomes a narrow record, whose key is
+// cut out of the wide one when the new depth is at most 8 characters deeper
+// (bytes), or is the first or second half of it (DNA codes, 0 or 21 deeper),
+// and gathered from the string otherwise.  bucket_first(b) is the position of
+// bucket b's first record (bucket_first(b + 1) - bucket_first(b) its size).
+// Returns the algorithmic bytes: bucket index 2 + wide record 24 read;
+// finished: perm 4 (+ lcp 4) written; open: 24 (wide) or 16 (narrow) written,
+// plus 16 (wide) or 8 (narrow) characters read when gathered.
+template <int MB, typename First>
+__device__ __forceinline__ uint32_t move_batch_wide(const SortCtx& c, const SetDesc& sd, uint32_t wide,
+                                                    uint32_t par, uint32_t src0, uint32_t depth, const uint32_t* desc,
+                                                    First&& bucket_first, const uint32_t (&pp)[MB],
+                                                    const uint32_t (&bb)[MB], const uint32_t (&dd)[MB]) {
+  uint32_t ds[MB];
+  uint2 wi[MB];
+  u128 key[MB];
+  uint32_t bytes = 0;
+#pragma unroll
+  for (int u = 0; u < MB; ++u) {
+    ds[u] = kFin;
+    wi[u] = make_uint2(0, 0);
+    key[u] = 0;
+    if (pp[u] != kInvalid) {
+      ds[u] = desc[bb[u]];
+      key[u] = load_wkey(c.rec[par] + src0 + pp[u]);
+      wi[u] = c.wid[par][src0 + pp[u]];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < MB; ++u) {
+    if (pp[u] == kInvalid) continue;
+    const uint32_t d = ds[u];
+    const uint32_t dest = dd[u];
+    if (d & kFin) {
+      sd.perm[dest - sd.base] = wi[u].x;
+      bytes += 30;
+      if (sd.lcp && (d & kNulEq) && dest != bucket_first(bb[u])) {
+        sd.lcp[dest - sd.base] = d & kLow30;
+        bytes += 4;
+      }
+      continue;
+    }
+    const uint32_t nd = d & kLow30;
+    const uint32_t adv = nd - depth;
+    const uint32_t size = bucket_first(bb[u] + 1) - bucket_first(bb[u]);
+    if (c.big_enabled && size > c.big_threshold) {
+      u128 k = key[u];
+      bytes += 50;
+      if (adv) {
+        k = load_key128(sd.chars, rec_offset(sd, wide, wi[u].x, wi[u].y), nd, sd.cap, sd.dna);
+        bytes += 16;
+      }
+      store_wkey(c.rec[par ^ 1] + dest, k);
+      c.wid[par ^ 1][dest] = wi[u];
+    } else {
+      uint64_t k;
+      bytes += 42;
+      if (!sd.dna && adv <= 8) {
+        k = narrow_at(key[u], adv);
+      } else if (sd.dna && (adv == 0 || adv == kDnaWidth)) {
+        k = adv ? k_lo(key[u]) : k_hi(key[u]);
+      } else {
+        k = load_key(sd.chars, rec_offset(sd, wide, wi[u].x, wi[u].y), nd, sd.cap, sd.dna);
+        bytes += 8;
+      }
+      store_rec(c.rec[par ^ 1] + dest, k, wi[u].x, wi[u].y);
+    }
+  }
+  return bytes;
+}
+
 // Emits the outcome of one non-empty bucket: its boundary LCP mark (resolved at
 // the end, Section 4.2.8 "LCP Calculation": the LCP with the previous bucket is
 // depth + lcp of the two strings' caches at this depth) and, if it is not
 // finished, a new task.
 __device__ __forceinline__ void emit_bucket(const SortCtx& c, const SetDesc& sd, const Task& t,
                                             uint32_t start, uint32_t size, uint32_t desc,
-                                            uint32_t next_big) {
-  if (start > 0 && sd.lcp) sd.lcp[t.begin + start - sd.base] = kLcpMark | t.depth;
+                                            uint32_t next_big, uint32_t mark = kLcpMark) {
+  if (start > 0 && sd.lcp) sd.lcp[t.begin + start - sd.base] = mark | t.depth;
   if (!(desc & kFin)) {
     Task ch{t.begin + start, size, desc & kLow30, make_meta(task_set(t), task_par(t) ^ 1)};
     route_task(c, ch, next_big);

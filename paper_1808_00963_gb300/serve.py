@@ -26,7 +26,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Batch, sort, workspace_size
+from . import Batch, sort, stream_status, workspace_size
 
 
 @dataclass
@@ -117,7 +117,7 @@ class Server:
                 dev.append((ch, of, r.max_len, p, l))
             if len(group) == 1 and (self.mode == "plain" or group[0].n > self.big):
                 ch, of, ml, p, l = dev[0]
-                sort(ch, of, max_len=ml, out=(p, l), stream=stream)
+                sort(ch, of, max_len=ml, out=(p, l), stream=stream, sync=False)
             else:
                 b = Batch(dev, own_workspace=True)
                 b.run(stream)
@@ -126,7 +126,7 @@ class Server:
             for r, (_, _, _, p, l) in zip(group, dev):
                 r.perm.copy_(p, non_blocking=True)
                 r.lcp.copy_(l, non_blocking=True)
-            stream.synchronize()
+            stream_status(stream)  # waits for the stream; raises on a device-side error
             now = time.perf_counter() - t0
             for r in group:
                 r.done = now

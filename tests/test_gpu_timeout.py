@@ -32,3 +32,20 @@ def test_generous_wait_limit_changes_nothing():
     s = gen.url_set(50_000, 79)
     p, l = gpu_sort(s, wait_limit_us=2_000_000)
     assert_parity(s, p, l)
+
+
+def test_expired_wait_leaves_in_range_outputs():
+    """After a device-side error the sort writes the identity permutation and
+    zero LCPs (outputs first filled with out-of-range values)."""
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    s = gen.url_set(6000, 80)
+    chars, offsets = to_device(s)
+    perm = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
+    lcp = torch.full((s.n,), -1, dtype=torch.int32, device="cuda")
+    with pytest.raises(ss.SortError) as e:
+        ss.sort(chars, offsets, out=(perm, lcp), wait_limit_us=1)
+    assert e.value.code == 5
+    assert np.array_equal(perm.cpu().numpy(), np.arange(s.n, dtype=np.int32))
+    assert not lcp.cpu().numpy().any()
