@@ -1047,7 +1047,13 @@ def main():
                     help="leave out the batched (configuration 4) and served (configuration 5) parts of the "
                          "default line")
     ap.add_argument("--n", type=int, default=None, help="reduced string count (c2 and m2; profiler captures)")
+    ap.add_argument("--no-graph-loop", action="store_true",
+                    help="run the multi-block rounds launch by launch (for kernel profilers, which do not see "
+                         "kernels inside graphs with conditional nodes)")
     args = ap.parse_args()
+    if args.no_graph_loop and args.impl == "ours":
+        import paper_1808_00963_gb300 as ss
+        ss.set_graph_loop(False)
     if args.impl == "reference":
         rank = int(os.environ.get("RANK", "0"))
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), rank)

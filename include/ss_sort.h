@@ -373,6 +373,14 @@ uint64_t ss_launch_count(void);
  * up to `cap` entries (name, launches, total ms, algorithmic bytes; any output
  * array may be NULL) and returns the number of kernel classes. */
 void ss_set_profiling(int enabled);
+
+/* With 0, ss_sort / ss_sort_ex / ss_batch_run run the rounds of multi-block
+ * steps from the host instead of the loop graph: the same kernels, each its
+ * own launch, with the host waiting for each round's plan (the calls then
+ * wait for the multi-block part of the sort).  For tools that cannot see
+ * kernels inside a graph with conditional nodes (kernel profilers).  Default
+ * 1.  Has no effect on a call made while its stream is being captured. */
+void ss_set_graph_loop(int enabled);
 uint32_t ss_kernel_stats(const char** names, uint64_t* launches, double* total_ms,
                          uint64_t* alg_bytes, uint32_t cap);
 void ss_reset_kernel_stats(void);

@@ -163,6 +163,8 @@ def load(path: str | None = None):
     lib.ss_launch_count.restype = u64
     lib.ss_set_profiling.argtypes = [i32]
     lib.ss_set_profiling.restype = None
+    lib.ss_set_graph_loop.argtypes = [i32]
+    lib.ss_set_graph_loop.restype = None
     lib.ss_kernel_stats.argtypes = [ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(u64),
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(u64), u32]
     lib.ss_kernel_stats.restype = u32
@@ -451,6 +453,12 @@ def launch_count() -> int:
 
 def set_profiling(on: bool):
     load().ss_set_profiling(1 if on else 0)
+
+
+def set_graph_loop(on: bool):
+    """ss_set_graph_loop: run the multi-block rounds as one graph launch
+    (default) or launch by launch from the host (for kernel profilers)."""
+    load().ss_set_graph_loop(1 if on else 0)
 
 
 def reset_kernel_stats():

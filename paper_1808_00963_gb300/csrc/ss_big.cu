@@ -222,15 +222,26 @@ __global__ void __launch_bounds__(kPlanThreads) k_big_plan(BigCtl* __restrict__ 
 // record and its loads take twice the registers of a narrow one).
 constexpr int kWideMoveBatch = 2;
 
-// The next item (subset or tile) of a round's kernel for this block: taken
-// from the kernel's work counter by one thread and shared with the block.
-__device__ __forceinline__ uint32_t next_item(uint32_t* counter) {
-  __shared__ uint32_t s_item;
-  __syncthreads();  // every thread has read the previous item
-  if (threadIdx.x == 0) s_item = atomicAdd(counter, 1u);
-  __syncthreads();
-  return s_item;
-}
+// The items (subsets or tiles) of a round's kernel for this block, taken from
+// the kernel's work counter one ahead: thread 0 claims the block's next item
+// when the current one starts, so the atomic's round trip overlaps the work.
+//   for (uint32_t i = items.first(); i < n; i = items.next()) { items.claim(); ... }
+struct ItemStream {
+  uint32_t* counter;
+  uint32_t ahead;  // thread 0: the item claimed for after the current one
+  __device__ __forceinline__ uint32_t share(uint32_t v) {
+    __shared__ uint32_t s_item;
+    __syncthreads();  // every thread is done with the previous item
+    if (threadIdx.x == 0) s_item = v;
+    __syncthreads();
+    return s_item;
+  }
+  __device__ __forceinline__ uint32_t first() { return share(threadIdx.x == 0 ? atomicAdd(counter, 1u) : 0u); }
+  __device__ __forceinline__ void claim() {
+    if (threadIdx.x == 0) ahead = atomicAdd(counter, 1u);
+  }
+  __device__ __forceinline__ uint32_t next() { return share(ahead); }
+};
 
 template <int LOGV>
 __global__ void __launch_bounds__(kBlock) k_big_sample(const BigCtl* __restrict__ ctl, uint32_t* __restrict__ work) {
@@ -241,7 +252,9 @@ __global__ void __launch_bounds__(kBlock) k_big_sample(const BigCtl* __restrict_
   const SortCtx& c = ctl->c;
   BigSplitters<LOGV>* out = reinterpret_cast<BigSplitters<LOGV>*>(ctl->splitters);
   unsigned long long bytes = 0;
-  for (uint32_t gi = next_item(work); gi < G; gi = next_item(work)) {
+  ItemStream items{work, 0u};
+  for (uint32_t gi = items.first(); gi < G; gi = items.next()) {
+    items.claim();
     const GenTask g = ctl->gt[gi];
     const uint32_t par = task_par(g.t);
     const Rec* recs = c.rec[par] + g.t.begin;
@@ -310,7 +323,9 @@ __global__ void __launch_bounds__(kBlock) k_big_classify(const BigCtl* __restric
   const bool use_jump = c.classifier == kClassifyUIJ;
   unsigned long long bytes = 0;
   uint32_t loaded = 0xFFFFFFFFu;  // subset whose splitters are in shared memory
-  for (uint32_t tg = next_item(work); tg < tiles; tg = next_item(work)) {
+  ItemStream items{work, 0u};
+  for (uint32_t tg = items.first(); tg < tiles; tg = items.next()) {
+    items.claim();
     if (threadIdx.x == 0) s_g = find_gen_task(gt, G, tg);
     for (uint32_t b = threadIdx.x; b < Gm::KP; b += blockDim.x) hist[b] = 0;
     __syncthreads();
@@ -369,7 +384,9 @@ __global__ void __launch_bounds__(kBlock) k_big_emit(const BigCtl* __restrict__ 
   const BigSplitters<LOGV>* spl = reinterpret_cast<const BigSplitters<LOGV>*>(ctl->splitters);
   const uint32_t next_big = ctl->next_big;
   unsigned long long bytes = 0;
-  for (uint32_t gi = next_item(work); gi < G; gi = next_item(work)) {
+  ItemStream items{work, 0u};
+  for (uint32_t gi = items.first(); gi < G; gi = items.next()) {
+    items.claim();
     const GenTask g = ctl->gt[gi];
     const Splitters<LOGV, u128>& sp = spl[gi].sp;
     const SetDesc sd = c.sets[task_set(g.t)];
@@ -390,6 +407,11 @@ __global__ void __launch_bounds__(kBlock) k_big_emit(const BigCtl* __restrict__ 
           if (J > KeyOps<u128>::width(0) && J != 0xFFFFFFFFu) desc = g.t.depth + J;
         }
         emit_bucket(c, sd, g.t, s, size, desc, next_big, kLcpMark | kLcpWide);
+        if (s > 0 && sd.lcp) {  // the fix-up at the end visits the listed marks only
+          const uint32_t k = atomicAdd(c.marks_count, 1u);
+          if (k < c.marks_cap) c.marks[k] = g.t.begin + s;
+          else latch_status(c.status, kStQueueFull);
+        }
       }
       ctl->gdesc[(uint64_t)gi * Gm::KP + b] = desc;
     }
@@ -411,7 +433,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_big_scatter(const BigCtl* __restr
   const SortCtx& c = ctl->c;
   const GenTask* __restrict__ gt = ctl->gt;
   unsigned long long bytes = 0;
-  for (uint32_t tg = next_item(work); tg < tiles; tg = next_item(work)) {
+  ItemStream items{work, 0u};
+  for (uint32_t tg = items.first(); tg < tiles; tg = items.next()) {
+    items.claim();
     if (threadIdx.x == 0) s_g = find_gen_task(gt, G, tg);
     __syncthreads();
     const uint32_t gi = s_g;

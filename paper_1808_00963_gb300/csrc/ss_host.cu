@@ -34,6 +34,7 @@ namespace ss {
 
 static std::atomic<uint64_t> g_launches{0};
 static std::atomic<int> g_profiling{0};
+static std::atomic<int> g_graph_loop{1};  // 0: the host runs the multi-block rounds (see ss_set_graph_loop)
 static std::mutex g_stats_mu;
 static std::map<std::string, std::pair<uint64_t, double>> g_stats;
 static std::map<std::string, unsigned long long> g_bytes;
@@ -205,11 +206,11 @@ static uint32_t pmax_of(uint32_t cutoff) {
 constexpr uint32_t kCtrlWords = 64;                          // status and list counters
 constexpr size_t kCtrlBytes = kCtrlWords * 4 + kKClasses * 8;  // + algorithmic byte counters
 enum Ctrl : uint32_t { kCStatus = 0, kCBig0 = 1, kCBig1 = 2, kCHead = 3, kCTail = 4, kCPending = 5,
-                       kCSmallW = 6, kCSmallC = 7, kCSmallD = 8 };
+                       kCSmallW = 6, kCSmallC = 7, kCSmallD = 8, kCMarks = 9 };
 
 struct Layout {
   size_t ctrl, sets, wide, rec0, rec1, wid0, wid1, bucket_of, big0, big1, gen, spl, counters, partials, gstart,
-      gdesc, bigctl, mq_items, mq_ready, sw_items, sc_items, total;
+      gdesc, bigctl, marks, mq_items, mq_ready, sw_items, sc_items, total;
   uint32_t cap_big, cap_mq, cap_sw, cap_sc;
   uint64_t ncounters_max;
 };
@@ -246,6 +247,7 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   L.gstart = take((size_t)L.cap_big * KP * 4);
   L.gdesc = take((size_t)L.cap_big * KP * 4);
   L.bigctl = take(big ? sizeof(BigCtl) : 0);  // a batch's loop control block (plain sorts use the stream's)
+  L.marks = take(big ? M * 4 : 0);             // LCP marks of multi-block steps (distinct positions: < M)
   L.mq_items = take((size_t)L.cap_mq * sizeof(Task));
   L.mq_ready = take((size_t)L.cap_mq * 4);
   L.sw_items = take(2 * (size_t)L.cap_sw * sizeof(Task));
@@ -275,6 +277,9 @@ static SortCtx make_ctx(uint8_t* ws, const Layout& L, uint32_t num_sets, uint32_
   c.small_warp = TaskList{reinterpret_cast<Task*>(ws + L.sw_items), ctrl + kCSmallW, L.cap_sw};
   c.small_deep = TaskList{reinterpret_cast<Task*>(ws + L.sw_items) + L.cap_sw, ctrl + kCSmallD, L.cap_sw};
   c.small_cta = TaskList{reinterpret_cast<Task*>(ws + L.sc_items), ctrl + kCSmallC, L.cap_sc};
+  c.marks = reinterpret_cast<uint32_t*>(ws + L.marks);
+  c.marks_count = ctrl + kCMarks;
+  c.marks_cap = big ? total : 0u;
   c.small_cutoff = o.cutoff;
   c.big_threshold = o.big_thr;
   c.big_enabled = big ? 1u : 0u;
@@ -537,8 +542,8 @@ static ss_status run_sort(uint8_t* ws, const Layout& L, SortCtx c, const Opts& o
     if (cs == cudaStreamCaptureStatusActive) {
       // the caller is capturing a graph: the loop becomes part of it
       SS_CUDA(add_loop(st, ctl, o.logv_big, R_max, (uint32_t)dev.sms));
-    } else if (g_profiling.load()) {
-      // timed launch by launch: the host runs the rounds, reading each plan
+    } else if (g_profiling.load() || !g_graph_loop.load()) {
+      // launch by launch (timed, or for a profiler): the host runs the rounds, reading each plan
       if (t_down.reserve(64) != SS_OK) return SS_ERR_OOM;
       uint32_t* hG = static_cast<uint32_t*>(t_down.p);
       while (true) {
@@ -687,6 +692,8 @@ uint64_t ss_launch_count(void) {
 }
 
 void ss_set_profiling(int enabled) { g_profiling.store(enabled ? 1 : 0); }
+
+void ss_set_graph_loop(int enabled) { g_graph_loop.store(enabled ? 1 : 0); }
 
 void ss_reset_kernel_stats(void) {
   std::lock_guard<std::mutex> lk(g_stats_mu);

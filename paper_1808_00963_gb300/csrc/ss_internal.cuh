@@ -122,6 +122,9 @@ struct SortCtx {
   TaskList small_warp;     // 2..32 records
   TaskList small_deep;     // runs the first warp pass deferred (long common prefixes)
   TaskList small_cta;      // 33..small_cutoff records
+  uint32_t* marks;         // record positions whose LCP entry holds a mark (multi-block step boundaries)
+  uint32_t* marks_count;
+  uint32_t marks_cap;
   uint32_t small_cutoff;
   uint32_t big_threshold;  // tasks longer than this go to big[] (if big_enabled)
   uint32_t big_enabled;

@@ -26,6 +26,11 @@ struct QueueSmem {
   union U {
     BuildScratch<LOGV> bs;
     struct {
+      unsigned long long bmin[Geo<LOGV>::KP];  // smallest / largest key of each even bucket
+      unsigned long long bmax[Geo<LOGV>::KP];
+      uint32_t prev[Geo<LOGV>::KP];            // last non-empty bucket before each bucket, + 1 (0: none)
+    } mm;
+    struct {
       uint32_t cntw[kWarps * Geo<LOGV>::KP];
       uint16_t tb[kMaxTile];
     } sc;
@@ -97,6 +102,42 @@ __device__ void block_excl_scan_smem(const uint32_t* in, uint32_t* out, uint32_t
   __syncthreads();
 }
 
+// Inclusive max-scan of n (a multiple of the block size) values in shared memory.
+__device__ void block_max_scan_smem(uint32_t* a, uint32_t n) {
+  __shared__ uint32_t wmax[kWarps];
+  const uint32_t per = n / kBlock;
+  const uint32_t b0 = threadIdx.x * per;
+  uint32_t m = 0;
+  for (uint32_t j = 0; j < per; ++j) m = max(m, a[b0 + j]);
+  uint32_t inc = m;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane_id() >= (uint32_t)o) inc = max(inc, t);
+  }
+  const uint32_t w = threadIdx.x >> 5;
+  if (lane_id() == 31) wmax[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t v = lane_id() < kWarps ? wmax[lane_id()] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xFFFFFFFFu, v, o);
+      if (lane_id() >= (uint32_t)o) v = max(v, t);
+    }
+    if (lane_id() < kWarps) wmax[lane_id()] = v;
+  }
+  __syncthreads();
+  uint32_t run = __shfl_up_sync(0xFFFFFFFFu, inc, 1);
+  if (lane_id() == 0) run = 0;
+  run = max(run, w ? wmax[w - 1] : 0u);
+  for (uint32_t j = 0; j < per; ++j) {
+    run = max(run, a[b0 + j]);
+    a[b0 + j] = run;
+  }
+  __syncthreads();
+}
+
 // One S^5 step on task t by this block.
 // Returns this thread's share of the step's algorithmic bytes: the sample,
 // cache 8 read + bucket index 2 written per record while classifying, and the
@@ -111,15 +152,42 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
   build_splitters<LOGV>(recs, t.len, mix64(c.seed ^ ((uint64_t)t.begin << 20) ^ t.depth), s.sp, s.u.bs, sd.dna);
   unsigned long long bytes = threadIdx.x == 0 ? Gm::S * 8ull : 0ull;
 
-  // classification (Algorithm 4.1): classify into the array o and count
-  for (uint32_t b = threadIdx.x; b < Gm::KP; b += kBlock) s.hist[b] = 0;
+  // classification (Algorithm 4.1): classify into the array o and count; with
+  // an LCP output also the smallest and largest key of each even bucket
+  const bool with_lcp = sd.lcp != nullptr;
+  for (uint32_t b = threadIdx.x; b < Gm::KP; b += kBlock) {
+    s.hist[b] = 0;
+    s.u.mm.bmin[b] = ~0ull;
+    s.u.mm.bmax[b] = 0ull;
+  }
   __syncthreads();
   uint16_t* bo = c.bucket_of + t.begin;
-  bytes += 10ull * classify_count<LOGV>(recs, bo, t.len, s.sp.tree, s.sp.x, s.hist, c.classifier);
+  bytes += 10ull * classify_count_k<LOGV, uint64_t>([&](uint32_t p) { return recs[p].key; }, bo, t.len, s.sp.tree,
+                                                    s.sp.x, s.hist, c.classifier, nullptr,
+                                                    with_lcp ? s.u.mm.bmin : nullptr,
+                                                    with_lcp ? s.u.mm.bmax : nullptr);
   __syncthreads();
 
   // prefix sum over the bucket sizes; bucket outcomes
   block_excl_scan_smem(s.hist, s.bstart, Gm::KP);  // bstart[K] = len (hist[K] is 0)
+  if (with_lcp) {
+    // LCP at each bucket boundary (Section 4.2.3 "LCP via XOR", Section 4.2.8
+    // "LCP Calculation"): the last string of the previous non-empty bucket
+    // and the first string of this one are the largest key of the one and
+    // the smallest of the other, which differ within the step's 8 characters
+    for (uint32_t b = threadIdx.x; b < Gm::KP; b += kBlock) s.u.mm.prev[b] = (b < Gm::K && s.hist[b]) ? b + 1 : 0u;
+    __syncthreads();
+    block_max_scan_smem(s.u.mm.prev, Gm::KP);  // prev[b] - 1: last non-empty bucket <= b
+    for (uint32_t b = threadIdx.x + 1; b < Gm::K; b += kBlock) {
+      const uint32_t q = s.u.mm.prev[b - 1];
+      if (!s.hist[b] || q == 0) continue;
+      const uint32_t pb = q - 1;
+      const uint64_t hi = (pb & 1u) ? s.sp.x[pb >> 1] : s.u.mm.bmax[pb];
+      const uint64_t lo = (b & 1u) ? s.sp.x[b >> 1] : s.u.mm.bmin[b];
+      sd.lcp[t.begin + s.bstart[b] - sd.base] = t.depth + key_lcp(hi, lo, sd.dna);
+    }
+    __syncthreads();  // hist is overwritten below
+  }
   for (uint32_t b = threadIdx.x; b < Gm::K; b += kBlock) {
     const uint32_t size = s.hist[b];
     s.desc[b] = size ? bucket_desc<LOGV>(b, size, t.depth, s.sp, sd.dna) : kFin;
@@ -151,7 +219,7 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
   for (uint32_t b = threadIdx.x; b < Gm::K; b += kBlock) {
     const uint32_t start = s.bstart[b];
     const uint32_t size = s.bstart[b + 1] - start;
-    if (size) emit_bucket(c, sd, t, start, size, s.desc[b], 0);
+    if (size) emit_bucket(c, sd, t, start, size, s.desc[b], 0, 0u);  // boundary LCPs are written already
   }
   return bytes;
 }

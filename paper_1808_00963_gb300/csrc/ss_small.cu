@@ -572,9 +572,10 @@ __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint
   account(c, kKSmallCta, bytes);
 }
 
-// Resolves the boundary marks left by the distribution steps: out_lcp[j] =
-// mark | h means the strings at j-1 and j share exactly their first h
-// characters plus the common prefix of their caches at depth h.
+// Resolves the boundary marks left by the multi-block steps (listed in
+// c.marks): out_lcp[j] = mark | h means the strings at j-1 and j share exactly
+// their first h characters plus the common prefix of their keys at depth h.
+// (The single-block steps write their boundary LCPs themselves.)
 __global__ void __launch_bounds__(kBlock) k_lcp_fix(SortCtx c) {
   const uint32_t stride = gridDim.x * blockDim.x;
   unsigned long long bytes = 0;
@@ -594,13 +595,14 @@ __global__ void __launch_bounds__(kBlock) k_lcp_fix(SortCtx c) {
     }
     return;
   }
-  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < c.total; r += stride) {
+  const uint32_t nm = min(*c.marks_count, c.marks_cap);
+  for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += stride) {
+    const uint32_t r = c.marks[m];
     const uint32_t s = c.num_sets == 1 ? 0 : find_set(c, r);
     const SetDesc sd = c.sets[s];
-    if (!sd.lcp) continue;
     const uint32_t j = r - sd.base;
     const uint32_t v = sd.lcp[j];
-    bytes += 4;
+    bytes += 8;  // list entry and LCP entry read
     if (j == 0 || !(v & kLcpMark)) continue;
     const uint32_t h = v & ~(kLcpMark | kLcpWide);
     const uint32_t pa = sd.perm[j - 1], pb = sd.perm[j];

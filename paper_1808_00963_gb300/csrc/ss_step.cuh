@@ -300,7 +300,8 @@ __device__ __forceinline__ void classify_batch(const K (&k)[U], uint32_t (&b)[U]
 template <int LOGV, typename K, typename KeyAt>
 __device__ __forceinline__ uint32_t classify_count_k(KeyAt&& key_at, uint16_t* __restrict__ bo, uint32_t n,
                                                      const K* tree, const K* x, uint32_t* hist, uint32_t variant,
-                                                     const uint16_t* jump) {
+                                                     const uint16_t* jump, unsigned long long* bmin = nullptr,
+                                                     unsigned long long* bmax = nullptr) {
   constexpr int U = 8;
   uint32_t mine = 0;
   const uint32_t lim = (n + kBlock - 1) / kBlock * kBlock;
@@ -325,6 +326,14 @@ __device__ __forceinline__ uint32_t classify_count_k(KeyAt&& key_at, uint16_t* _
       }
       const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
       if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
+      if constexpr (sizeof(K) == 8) {
+        // smallest and largest key of each even bucket (an equality bucket's
+        // keys all equal its splitter), for the LCPs at bucket boundaries
+        if (bmin && valid && !(b & 1u)) {
+          atomicMin(&bmin[b], (unsigned long long)k[u]);
+          atomicMax(&bmax[b], (unsigned long long)k[u]);
+        }
+      }
     }
   }
   return mine;
@@ -572,7 +581,7 @@ __device__ __forceinline__ uint32_t move_batch_wide(const SortCtx& c, const SetD
 __device__ __forceinline__ void emit_bucket(const SortCtx& c, const SetDesc& sd, const Task& t,
                                             uint32_t start, uint32_t size, uint32_t desc,
                                             uint32_t next_big, uint32_t mark = kLcpMark) {
-  if (start > 0 && sd.lcp) sd.lcp[t.begin + start - sd.base] = mark | t.depth;
+  if (mark && start > 0 && sd.lcp) sd.lcp[t.begin + start - sd.base] = mark | t.depth;
   if (!(desc & kFin)) {
     Task ch{t.begin + start, size, desc & kLow30, make_meta(task_set(t), task_par(t) ^ 1)};
     route_task(c, ch, next_big);
