@@ -70,7 +70,8 @@ typedef struct ss_options {
                                   >= max_len reads as the terminator.           */
     uint32_t splitters_log2;   /* d with v = 2^d - 1 splitters per step in the
                                   single-block steps; 8..10 (default 8).        */
-    uint32_t big_splitters_log2; /* d for the multi-block steps; 8..10 (default 9). */
+    uint32_t big_splitters_log2; /* d for the multi-block steps (16-character keys);
+                                  8..9 (default 9).                              */
     uint32_t tile_rounds;      /* multi-block tile = 256 * tile_rounds strings;
                                   8..32 (default: chosen per step from the
                                   number of strings in big subsets).            */
@@ -297,11 +298,12 @@ ss_status ss_batch_create(const ss_set* sets, uint32_t num_sets, const ss_option
 size_t ss_batch_workspace_size(const ss_set* sets, uint32_t num_sets, const ss_options* opt);
 
 /* Enqueue the sort of every set of the batch on `stream`.  Asynchronous: no
- * host synchronisation and no allocation.  Sets above the big threshold take
- * multi-block steps, run by the loop of ss_sort (a graph with a conditional
- * WHILE node over the batch's own control block: launched as a graph, or,
- * when `stream` is being captured, added to the caller's graph); the rest is
- * a fixed sequence of launches (one persistent work-queue launch does the
+ * host synchronisation.  Sets above the big threshold take multi-block
+ * steps, run by the loop of ss_sort: the stream's loop graph over the
+ * stream's control block (allocated by the first such call on the stream),
+ * or, when `stream` is being captured, the same loop over the batch's own
+ * control block, added to the caller's graph (no allocation then).  The rest
+ * is a fixed sequence of launches (one persistent work-queue launch does the
  * single-block splitting).  So the call can be captured into a CUDA graph and
  * replayed.  Device-side errors are latched and read by ss_batch_status(). */
 ss_status ss_batch_run(ss_batch* b, void* stream);

@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(kBlock) k_big_sample(const BigCtl* __restrict_
 }
 
 template <int LOGV>
-__global__ void __launch_bounds__(kBlock) k_big_classify(const BigCtl* __restrict__ ctl, uint32_t* __restrict__ work) {
+__global__ void __launch_bounds__(kBlock, 4) k_big_classify(const BigCtl* __restrict__ ctl, uint32_t* __restrict__ work) {
   using Gm = Geo<LOGV>;
   __shared__ __align__(16) u128 tree[Gm::V + 1];
   __shared__ __align__(16) u128 x[Gm::V + 1];
@@ -578,11 +578,7 @@ __global__ void __launch_bounds__(kBlock) k_scan_down(const BigCtl* __restrict__
 }  // namespace
 
 size_t big_splitters_bytes(int logv) {
-  switch (logv) {
-    case 8: return sizeof(BigSplitters<8>);
-    case 9: return sizeof(BigSplitters<9>);
-    default: return sizeof(BigSplitters<10>);
-  }
+  return logv == 8 ? sizeof(BigSplitters<8>) : sizeof(BigSplitters<9>);
 }
 
 size_t big_scatter_smem(int logv, uint32_t R) {
@@ -626,7 +622,7 @@ cudaError_t launch_big_round(int logv, BigCtl* ctl, uint32_t R_max, uint32_t sms
   switch (logv) {
     case 8: return launch_big_round_t<8>(ctl, R_max, sms, st, hook);
     case 9: return launch_big_round_t<9>(ctl, R_max, sms, st, hook);
-    default: return launch_big_round_t<10>(ctl, R_max, sms, st, hook);
+    default: return cudaErrorInvalidValue;  // 2^10 wide splitters exceed static shared memory
   }
 }
 

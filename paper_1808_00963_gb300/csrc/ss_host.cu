@@ -173,8 +173,8 @@ static ss_status resolve_opts(const ss_options* o, Opts& r) {
     if (o->splitters_log2 < 8 || o->splitters_log2 > 10) return SS_ERR_INVALID;
     r.logv = (int)o->splitters_log2;
   }
-  if (o->big_splitters_log2) {
-    if (o->big_splitters_log2 < 8 || o->big_splitters_log2 > 10) return SS_ERR_INVALID;
+  if (o->big_splitters_log2) {  // wide keys: 2^10 splitters would not fit a block's static shared memory
+    if (o->big_splitters_log2 < 8 || o->big_splitters_log2 > 9) return SS_ERR_INVALID;
     r.logv_big = (int)o->big_splitters_log2;
   }
   if (o->tile_rounds) {
@@ -342,6 +342,15 @@ __global__ void k_set_desc(SetDesc* dst, SetDesc v) { *dst = v; }
 // Writes the control block of the multi-block loop (same reason).
 __global__ void k_set_ctl(BigCtl* dst, BigCtl v) { *dst = v; }
 
+// A batch's set descriptors, up to kDescChunk per launch (kernel parameters).
+constexpr uint32_t kDescChunk = 128;
+struct SetDescChunk {
+  SetDesc d[kDescChunk];
+};
+__global__ void k_set_descs(SetDesc* dst, uint32_t count, SetDescChunk v) {
+  for (uint32_t i = threadIdx.x; i < count; i += blockDim.x) dst[i] = v.d[i];
+}
+
 // ---- the multi-block loop as a CUDA graph -------------------------------------------------
 //
 // One round of multi-block steps is a plan kernel plus the round's kernels, all
@@ -350,7 +359,10 @@ __global__ void k_set_ctl(BigCtl* dst, BigCtl v) { *dst = v; }
 // of each round set the condition to 1 while big subsets remain, so the host
 // enqueues the whole loop with one graph launch and never waits for it.  The
 // graph depends only on the control block's address and the step geometry;
-// it is built once per control block (a stream's, or a batch's) and reused.
+// it is built once per stream (whose control block every sort and batch run
+// on that stream uses) and reused.  A run inside a caller's stream capture
+// adds the same loop, over the batch's own control block, to the caller's
+// graph instead.
 
 struct LoopKey {
   int dev;
@@ -458,20 +470,6 @@ static cudaError_t loop_exec(BigCtl* ctl, int logv, uint32_t R_max, uint32_t sms
   return cudaSuccess;
 }
 
-// Forgets the loop graphs of a control block (its memory is being released).
-static void drop_loops(const void* ctl) {
-  std::lock_guard<std::mutex> lk(g_loop_mu);
-  for (auto it = g_loops.begin(); it != g_loops.end();) {
-    if (it->first.ctl == ctl) {
-      if (it->second.exec) cudaGraphExecDestroy(it->second.exec);
-      if (it->second.g) cudaGraphDestroy(it->second.g);
-      it = g_loops.erase(it);
-    } else {
-      ++it;
-    }
-  }
-}
-
 // ---- per-stream state of asynchronous sorts ---------------------------------------------
 
 // Device memory of one (device, stream): the status word the stream's sorts
@@ -499,7 +497,7 @@ static ss_status stream_slot(cudaStream_t st, bool create, StreamSlot** out) {
   if (!create) return SS_OK;
   StreamSlot* p = nullptr;
   if (cudaMalloc(reinterpret_cast<void**>(&p), sizeof(StreamSlot)) != cudaSuccess) return SS_ERR_OOM;
-  if (cudaMemset(p, 0, sizeof(StreamSlot)) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) {
+  if (cudaMemsetAsync(p, 0, sizeof(StreamSlot), st) != cudaSuccess) {  // ordered before the stream's first use
     cudaFree(p);
     return SS_ERR_CUDA;
   }
@@ -655,6 +653,7 @@ struct ss_batch {
   bool big = false;  // some set is larger than the multi-block threshold
   uint32_t num_sets = 0;
   uint32_t total = 0;
+  std::vector<ss::SetDesc> sd;  // the set descriptors, written into the workspace by each run
 };
 
 using namespace ss;
@@ -1320,17 +1319,15 @@ ss_status ss_batch_create(const ss_set* sets, uint32_t num_sets, const ss_option
     if (cudaMalloc(reinterpret_cast<void**>(&b.ws), b.L.total) != cudaSuccess) return SS_ERR_OOM;
     b.owned = true;
   }
-  std::vector<SetDesc> sd(num_sets);
+  // The descriptors go into the workspace with each run, on its stream: a
+  // caller's workspace is stream-ordered memory that earlier work on that
+  // stream may still be using when the batch is created.
+  b.sd.resize(num_sets);
   uint32_t base = 0;
   for (uint32_t i = 0; i < num_sets; ++i) {
     const ss_set& x = sets[i];
-    sd[i] = SetDesc{x.chars, x.offsets, x.out_perm, x.out_lcp, x.n, x.max_len ? x.max_len : kNoCap, base, 0};
+    b.sd[i] = SetDesc{x.chars, x.offsets, x.out_perm, x.out_lcp, x.n, x.max_len ? x.max_len : kNoCap, base, 0};
     base += x.n;
-  }
-  if (num_sets && cudaMemcpy(b.ws + b.L.sets, sd.data(), sd.size() * sizeof(SetDesc), cudaMemcpyHostToDevice) !=
-                      cudaSuccess) {
-    if (b.owned) cudaFree(b.ws);
-    return SS_ERR_CUDA;
   }
   b.num_sets = num_sets;
   b.total = (uint32_t)total;
@@ -1346,8 +1343,34 @@ ss_status ss_batch_run(ss_batch* b, void* stream) {
     g_stream_last[stream] = b;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the set descriptors, as kernel parameters (no staging copy to wait for,
+  // and capturable)
+  SetDesc* dsets = reinterpret_cast<SetDesc*>(b->ws + b->L.sets);
+  for (uint32_t i0 = 0; i0 < b->num_sets; i0 += kDescChunk) {
+    SetDescChunk ch;
+    const uint32_t cnt = std::min(kDescChunk, b->num_sets - i0);
+    std::copy(b->sd.begin() + i0, b->sd.begin() + i0 + cnt, ch.d);
+    LaunchHook{st}.run("init", [&] { k_set_descs<<<1, kBlock, 0, st>>>(dsets + i0, cnt, ch); });
+    if (cudaGetLastError() != cudaSuccess) return SS_ERR_CUDA;
+  }
   SortCtx c = make_ctx(b->ws, b->L, b->num_sets, b->total, b->o, b->big);
-  return run_sort(b->ws, b->L, c, b->o, b->dev, b->big, st, reinterpret_cast<BigCtl*>(b->ws + b->L.bigctl));
+  // the multi-block loop's control block: inside a caller's capture the
+  // batch's own (its address goes into the caller's graph); otherwise the
+  // stream's, whose loop graph is built once per stream
+  BigCtl* ctl = nullptr;
+  if (b->big) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return SS_ERR_CUDA;
+    if (cs == cudaStreamCaptureStatusActive) {
+      ctl = reinterpret_cast<BigCtl*>(b->ws + b->L.bigctl);
+    } else {
+      StreamSlot* slot = nullptr;
+      ss_status s = stream_slot(st, true, &slot);
+      if (s != SS_OK) return s;
+      ctl = &slot->ctl;
+    }
+  }
+  return run_sort(b->ws, b->L, c, b->o, b->dev, b->big, st, ctl);
 }
 
 ss_status ss_batch_status(ss_batch* b, void* stream) {
@@ -1363,7 +1386,6 @@ ss_status ss_batch_destroy(ss_batch* b) {
     for (auto it = g_stream_last.begin(); it != g_stream_last.end();)
       it = (it->second == b) ? g_stream_last.erase(it) : std::next(it);
   }
-  if (b->big) drop_loops(b->ws + b->L.bigctl);
   if (b->owned) cudaFree(b->ws);
   delete b;
   return SS_OK;

@@ -302,7 +302,7 @@ __device__ __forceinline__ uint32_t classify_count_k(KeyAt&& key_at, uint16_t* _
                                                      const K* tree, const K* x, uint32_t* hist, uint32_t variant,
                                                      const uint16_t* jump, unsigned long long* bmin = nullptr,
                                                      unsigned long long* bmax = nullptr) {
-  constexpr int U = 8;
+  constexpr int U = sizeof(K) == 8 ? 8 : 4;  // keys per thread in flight (wide keys take 4 registers)
   uint32_t mine = 0;
   const uint32_t lim = (n + kBlock - 1) / kBlock * kBlock;
   for (uint32_t p0 = threadIdx.x; p0 < lim; p0 += U * kBlock) {

@@ -83,3 +83,44 @@ def test_served_requests_up_to_millions_of_strings():
         p, l = ss.sort(ch, of, max_len=s.max_len)
         assert np.array_equal(p.cpu().numpy().view(np.uint32), gp)
         assert np.array_equal(l.cpu().numpy().view(np.uint32), gl)
+
+
+@pytest.mark.slow
+def test_served_trickle_of_requests_keeps_every_result():
+    """Requests arriving one by one (mostly single-request groups, sorted
+    asynchronously, two groups in flight per worker stream, some small
+    batches between them): every result of 400 requests, replaying a pool of
+    40 sets of 1k..3M strings, equals its set sorted alone, and the pool sets
+    pass the oracle's O(n + D) checker.  (This pattern once exposed batch
+    descriptors read before their upload had landed.)"""
+    import dataclasses
+
+    import torch
+
+    import paper_1808_00963_gb300 as ss
+    from paper_1808_00963_gb300.serve import Server, make_request
+    spec = gen.trace(400, 23, 900.0, smin=1000, smax=3_000_000)
+    pool = [gen.make_set(k, n, sd) for (_, k, n, sd) in spec[:40]]
+    expected = []
+    for st in pool:
+        ch = torch.from_numpy(st.chars).cuda()
+        of = torch.from_numpy(st.offsets.view(np.int64)).cuda()
+        p, l = ss.sort(ch, of, max_len=st.max_len)
+        hp, hl = p.cpu().numpy().view(np.uint32), l.cpu().numpy().view(np.uint32)
+        assert oracle.check(st.chars, st.offsets, hp, hl, st.max_len) == -1, st.name
+        expected.append((hp.copy(), hl.copy()))
+    base = [make_request(i, 0.0, st.chars, st.offsets, st.max_len) for i, st in enumerate(pool)]
+    reqs = [dataclasses.replace(base[j % len(pool)], rid=j, arrival=t, meta={"pool": j % len(pool)})
+            for j, (t, _, _, _) in enumerate(spec)]
+    bad = []
+
+    def verify(r):
+        hp, hl = expected[r.meta["pool"]]
+        if not (np.array_equal(r.perm.numpy().view(np.uint32), hp)
+                and np.array_equal(r.lcp.numpy().view(np.uint32), hl)):
+            bad.append(r.rid)
+
+    stats = Server(budget_bytes=16 << 30, streams=4, mode="served", on_done=verify).run(reqs)
+    assert not stats["errors"]
+    assert not bad, bad[:10]
+    assert stats["mean_batch"] < 4.0  # mostly small groups
