@@ -64,30 +64,27 @@ __global__ void k_roots(SortCtx c) {
 
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
-__device__ __forceinline__ bool less3(uint32_t sa, uint64_t ka, uint32_t ia, uint32_t sb, uint64_t kb,
-                                      uint32_t ib) {
-  return sa < sb || (sa == sb && (ka < kb || (ka == kb && ia < ib)));
+// Order of the warp sort: (segment, key, source lane); tag = segment << 5 |
+// source lane, segment 32 for idle lanes.  Evaluated without branches.
+__device__ __forceinline__ bool wtag_less(uint64_t ka, uint32_t ta, uint64_t kb, uint32_t tb) {
+  const uint32_t sa = ta >> 5, sb = tb >> 5;
+  return (sa < sb) | ((sa == sb) & ((ka < kb) | ((ka == kb) & (ta < tb))));
 }
 
-// Bitonic sort of one element per lane by (seg, key, idx), ascending in lane
-// order; off, depth and open travel with the element.
-__device__ __forceinline__ void warp_sort(uint32_t& seg, uint64_t& key, uint32_t& idx, uint64_t& off,
-                                          uint32_t& depth, uint32_t& open) {
+// Bitonic sort of one (key, tag) per lane, ascending in lane order.
+__device__ __forceinline__ void warp_sort(uint32_t& tag, uint64_t& key) {
   const uint32_t lane = lane_id();
 #pragma unroll
   for (uint32_t k = 2; k <= 32; k <<= 1) {
 #pragma unroll
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      const uint32_t os = __shfl_xor_sync(kFull, seg, j);
+      const uint32_t ot = __shfl_xor_sync(kFull, tag, j);
       const uint64_t ok = __shfl_xor_sync(kFull, key, j);
-      const uint32_t oi = __shfl_xor_sync(kFull, idx, j);
-      const uint64_t oo = __shfl_xor_sync(kFull, off, j);
-      const uint32_t od = __shfl_xor_sync(kFull, depth, j);
-      const uint32_t op = __shfl_xor_sync(kFull, open, j);
       const bool up = (lane & k) == 0;
       const bool lower = (lane & j) == 0;
-      const bool take = (lower == up) ? less3(os, ok, oi, seg, key, idx) : less3(seg, key, idx, os, ok, oi);
-      if (take) { seg = os; key = ok; idx = oi; off = oo; depth = od; open = op; }
+      const bool take = (lower == up) ? wtag_less(ok, ot, key, tag) : wtag_less(key, tag, ok, ot);
+      tag = take ? ot : tag;
+      key = take ? ok : key;
     }
   }
 }
@@ -126,7 +123,17 @@ __device__ uint32_t warp_refine(bool active, uint32_t g0, uint32_t nact, uint64_
       const uint64_t pk0 = __shfl_up_sync(kFull, key, 1);
       const uint32_t pi0 = __shfl_up_sync(kFull, idx, 1);
       const bool disorder = active && lane > 0 && seg == ps0 && (key < pk0 || (key == pk0 && idx < pi0));
-      if (__any_sync(kFull, disorder)) warp_sort(seg, key, idx, off, depth, open);
+      if (__any_sync(kFull, disorder)) {
+        // Segments occupy fixed lanes, and depth and open are the same for
+        // every member of a segment, so only the key and the source lane
+        // move; ties go by source lane, which within a segment is index
+        // order.  Index and offset follow from the source lane.
+        uint32_t tag = ((active ? seg : 32u) << 5) | lane;
+        warp_sort(tag, key);
+        const uint32_t src = tag & 31u;
+        idx = __shfl_sync(kFull, idx, src);
+        off = __shfl_sync(kFull, off, src);
+      }
     }
     const uint32_t ps = __shfl_up_sync(kFull, seg, 1);
     const uint64_t pk = __shfl_up_sync(kFull, key, 1);
@@ -301,10 +308,10 @@ struct CtaSmem {  // carved from dynamic shared memory, pmax elements
   uint16_t* nseg;   // segment start of each position
 };
 
-// Order of the block sort: (segment, cache, tag).
+// Order of the block sort: (segment, cache, tag), evaluated without branches.
 __device__ __forceinline__ bool elem_less(uint64_t ka, uint32_t ta, uint64_t kb, uint32_t tb) {
   const uint32_t sa = tag_seg(ta), sb = tag_seg(tb);
-  return sa < sb || (sa == sb && (ka < kb || (ka == kb && ta < tb)));
+  return (sa < sb) | ((sa == sb) & ((ka < kb) | ((ka == kb) & (ta < tb))));
 }
 
 // Stable block merge sort of (key, tag) at positions [0, n), n <= pmax.

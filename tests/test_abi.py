@@ -53,7 +53,8 @@ def test_host_side_argument_checks(lib):
     # option ranges
     for bad in (dict(splitters_log2=7), dict(splitters_log2=11), dict(small_cutoff=32),
                 dict(small_cutoff=8192), dict(tile_rounds=64), dict(host_parts=3), dict(host_parts=32), dict(classifier=4),
-                dict(small_cutoff=1024, big_threshold=512)):
+                dict(small_cutoff=1024, big_threshold=512),
+                dict(big_splitters_log2=7), dict(big_splitters_log2=10)):
         ob = ss.make_options(**bad)
         assert lib.ss_sort_ex(dummy, dummy, 5, dummy, None, ctypes.byref(ob), None) == 1, bad
         assert lib.ss_workspace_size(1000, ctypes.byref(ob)) == 0
