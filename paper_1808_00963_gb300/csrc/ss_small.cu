@@ -314,30 +314,46 @@ __device__ __forceinline__ bool elem_less(uint64_t ka, uint32_t ta, uint64_t kb,
   return (sa < sb) | ((sa == sb) & ((ka < kb) | ((ka == kb) & (ta < tb))));
 }
 
+// Slots past the end of a subset: after every real element in elem_less order.
+constexpr uint32_t kPadTag = 0xFFFFFFFFu;
+
+// Bitonic sort of one (key, tag) per lane by elem_less, ascending in lane order.
+__device__ __forceinline__ void warp_sort_elems(uint64_t& key, uint32_t& tag) {
+  const uint32_t lane = lane_id();
+#pragma unroll
+  for (uint32_t k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      const uint32_t ot = __shfl_xor_sync(kFull, tag, j);
+      const uint64_t ok = __shfl_xor_sync(kFull, key, j);
+      const bool up = (lane & k) == 0;
+      const bool lower = (lane & j) == 0;
+      const bool take = (lower == up) ? elem_less(ok, ot, key, tag) : elem_less(key, tag, ok, ot);
+      tag = take ? ot : tag;
+      key = take ? ok : key;
+    }
+  }
+}
+
 // Stable block merge sort of (key, tag) at positions [0, n), n <= pmax.
-// Each thread first sorts its own chunk of ipt positions (insertion sort);
-// then every merge pass doubles the run length, each thread producing ipt
-// outputs of one merged pair of runs: it finds where its outputs start with a
-// binary search along the merge path and merges sequentially.  Uses
-// (key2, tag2) as the second buffer; the result ends in (m.key, m.tag).
+// Each warp first sorts runs of 32 positions with a bitonic network in
+// registers; then every merge pass doubles the run length, each thread
+// producing ipt (<= 32) outputs of one merged pair of runs: it finds where its
+// outputs start with a binary search along the merge path and merges
+// sequentially.  Uses (key2, tag2) as the second buffer; the result ends in
+// (m.key, m.tag).
 template <uint32_t NT>
 __device__ void block_sort(CtaSmem& m, uint32_t n) {
   uint32_t ipt = 1;
   while (ipt * NT < n) ipt <<= 1;
-  {
-    const uint32_t a = threadIdx.x * ipt;
-    const uint32_t e = min(n, a + ipt);
-    for (uint32_t i = a + 1; i < e; ++i) {
-      const uint64_t k = m.key[i];
-      const uint32_t t = m.tag[i];
-      uint32_t j = i;
-      while (j > a && elem_less(k, t, m.key[j - 1], m.tag[j - 1])) {
-        m.key[j] = m.key[j - 1];
-        m.tag[j] = m.tag[j - 1];
-        --j;
-      }
-      m.key[j] = k;
-      m.tag[j] = t;
+  for (uint32_t c0 = threadIdx.x & ~31u; c0 < n; c0 += NT) {
+    const uint32_t p = c0 + lane_id();
+    uint64_t k = p < n ? m.key[p] : ~0ull;
+    uint32_t t = p < n ? m.tag[p] : kPadTag;
+    warp_sort_elems(k, t);
+    if (p < n) {
+      m.key[p] = k;
+      m.tag[p] = t;
     }
   }
   __syncthreads();
@@ -345,7 +361,7 @@ __device__ void block_sort(CtaSmem& m, uint32_t n) {
   uint32_t* st = m.tag;
   uint64_t* dk = m.key2;
   uint32_t* dt = m.tag2;
-  for (uint32_t run = ipt; run < n; run <<= 1) {
+  for (uint32_t run = 32; run < n; run <<= 1) {
     const uint32_t out = threadIdx.x * ipt;
     if (out < n) {
       const uint32_t base = (out / (2 * run)) * (2 * run);
