@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(kBlock) k_big_emit(const BigCtl* __restrict__ 
 }
 
 template <int LOGV>
-__global__ void __launch_bounds__(kBlock, 4) k_big_scatter(const BigCtl* __restrict__ ctl, uint32_t* __restrict__ work) {
+__global__ void __launch_bounds__(kBlock, 3) k_big_scatter(const BigCtl* __restrict__ ctl, uint32_t* __restrict__ work) {
   using Gm = Geo<LOGV>;
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t* cntw = reinterpret_cast<uint32_t*>(smem);
@@ -613,7 +613,7 @@ static cudaError_t launch_big_round_t(BigCtl* ctl, uint32_t R_max, uint32_t sms,
   hook.run("scan", [&] { k_scan_partials<<<1, kBlock, 0, st>>>(ctl); });
   hook.run("scan", [&] { k_scan_down<<<sms * 8, kBlock, 0, st>>>(ctl); });
   hook.run("big_emit", [&] { k_big_emit<LOGV><<<sms * 8, kBlock, 0, st>>>(ctl, &ctl->next_item[2]); });
-  hook.run("big_scatter", [&] { k_big_scatter<LOGV><<<sms * 4, kBlock, smem, st>>>(ctl, &ctl->next_item[3]); });
+  hook.run("big_scatter", [&] { k_big_scatter<LOGV><<<sms * 3, kBlock, smem, st>>>(ctl, &ctl->next_item[3]); });
   return cudaGetLastError();
 }
 

@@ -228,22 +228,38 @@ constexpr int kLookWindows = 8;  // look-ahead: 8 windows = 64 characters per ro
 // past the terminator are discarded.  Returns how many leading windows are
 // fully determined (windows past the block, before a terminator was seen, are
 // not).
+//
+// Two phases, so that a thread can have the reads of several strings in
+// flight before it uses any of them: issue_windows loads the words,
+// finish_windows turns them into the windows.
 template <int KW>
-__device__ __forceinline__ uint32_t load_windows(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
-                                                 uint64_t (&w)[KW]) {
+struct WindowWords {
+  uint64_t word[KW + 1];
+};
+
+template <int KW>
+__device__ __forceinline__ void issue_windows(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
+                                              WindowWords<KW>& ww) {
+  const uintptr_t a = (uintptr_t)(chars + off + h);
+  const uintptr_t blk_end = (a & ~(uintptr_t)4095) + 4096;
+  const uintptr_t p0 = a & ~(uintptr_t)7;
+#pragma unroll
+  for (int i = 0; i <= KW; ++i) {
+    const uintptr_t q = p0 + 8 * (uintptr_t)i;
+    ww.word[i] = (h < cap && q < blk_end) ? __ldg(reinterpret_cast<const uint64_t*>(q)) : 0ull;
+  }
+}
+
+// The same string and depth as the issue_windows call that filled ww.
+template <int KW>
+__device__ __forceinline__ uint32_t finish_windows(const WindowWords<KW>& ww, const uint8_t* chars, uint64_t off,
+                                                   uint32_t h, uint32_t cap, uint64_t (&w)[KW]) {
 #pragma unroll
   for (int j = 0; j < KW; ++j) w[j] = 0;
   if (h >= cap) return KW;
   const uintptr_t a = (uintptr_t)(chars + off + h);
   const uintptr_t blk_end = (a & ~(uintptr_t)4095) + 4096;
-  const uintptr_t p0 = a & ~(uintptr_t)7;
   const uint32_t sh = (uint32_t)(a & 7);
-  uint64_t word[KW + 1];
-#pragma unroll
-  for (int i = 0; i <= KW; ++i) {
-    const uintptr_t q = p0 + 8 * (uintptr_t)i;
-    word[i] = q < blk_end ? __ldg(reinterpret_cast<const uint64_t*>(q)) : 0ull;
-  }
   const uint64_t known_total = (uint64_t)(blk_end - a);  // bytes from h that may be read (>= 1)
   const uint64_t room_total = (uint64_t)cap - h;         // bytes from h before the cap (>= 1)
   uint32_t nwin = KW;
@@ -251,7 +267,7 @@ __device__ __forceinline__ uint32_t load_windows(const uint8_t* chars, uint64_t 
 #pragma unroll
   for (int j = 0; j < KW; ++j) {
     if (ended || (uint32_t)j >= nwin) continue;
-    uint64_t v = sh ? ((word[j] >> (8 * sh)) | (word[j + 1] << (64 - 8 * sh))) : word[j];
+    uint64_t v = sh ? ((ww.word[j] >> (8 * sh)) | (ww.word[j + 1] << (64 - 8 * sh))) : ww.word[j];
     const uint64_t ws = 8ull * j;
     const uint32_t known = known_total > ws ? (known_total - ws >= 8 ? 8u : (uint32_t)(known_total - ws)) : 0u;
     const uint32_t room = room_total > ws ? (room_total - ws >= 8 ? 8u : (uint32_t)(room_total - ws)) : 0u;
@@ -268,6 +284,14 @@ __device__ __forceinline__ uint32_t load_windows(const uint8_t* chars, uint64_t 
     }
   }
   return nwin;
+}
+
+template <int KW>
+__device__ __forceinline__ uint32_t load_windows(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
+                                                 uint64_t (&w)[KW]) {
+  WindowWords<KW> ww;
+  issue_windows<KW>(chars, off, h, cap, ww);
+  return finish_windows<KW>(ww, chars, off, h, cap, w);
 }
 
 // Offset of a record's string.

@@ -516,7 +516,9 @@ __device__ __forceinline__ uint32_t move_batch_wide(const SortCtx& c, const SetD
                                                     uint32_t par, uint32_t src0, uint32_t depth, const uint32_t* desc,
                                                     First&& bucket_first, const uint32_t (&pp)[MB],
                                                     const uint32_t (&bb)[MB], const uint32_t (&dd)[MB]) {
-  uint32_t ds[MB];
+  constexpr uint32_t kSkip = 0, kFinal = 1, kKeep = 2, kGather = 3;  // what a record needs
+  uint32_t ds[MB], how[MB];
+  bool to_wide[MB];
   uint2 wi[MB];
   u128 key[MB];
   uint32_t bytes = 0;
@@ -531,44 +533,67 @@ __device__ __forceinline__ uint32_t move_batch_wide(const SortCtx& c, const SetD
       wi[u] = c.wid[par][src0 + pp[u]];
     }
   }
+  // what each record needs; the characters of every byte-string gather are
+  // requested before any of them is used (one memory round trip for the batch)
+  WindowWords<2> ww[MB];
 #pragma unroll
   for (int u = 0; u < MB; ++u) {
+    how[u] = kSkip;
+    to_wide[u] = false;
     if (pp[u] == kInvalid) continue;
     const uint32_t d = ds[u];
-    const uint32_t dest = dd[u];
     if (d & kFin) {
+      how[u] = kFinal;
+      continue;
+    }
+    const uint32_t adv = (d & kLow30) - depth;
+    const uint32_t size = bucket_first(bb[u] + 1) - bucket_first(bb[u]);
+    to_wide[u] = c.big_enabled && size > c.big_threshold;
+    const bool derive = to_wide[u] ? adv == 0 : (sd.dna ? (adv == 0 || adv == kDnaWidth) : adv <= 8);
+    how[u] = derive ? kKeep : kGather;
+    if (!derive && !sd.dna)
+      issue_windows<2>(sd.chars, rec_offset(sd, wide, wi[u].x, wi[u].y), d & kLow30, sd.cap, ww[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < MB; ++u) {
+    if (how[u] == kSkip) continue;
+    const uint32_t dest = dd[u];
+    if (how[u] == kFinal) {
       sd.perm[dest - sd.base] = wi[u].x;
       bytes += 30;
-      if (sd.lcp && (d & kNulEq) && dest != bucket_first(bb[u])) {
-        sd.lcp[dest - sd.base] = d & kLow30;
+      if (sd.lcp && (ds[u] & kNulEq) && dest != bucket_first(bb[u])) {
+        sd.lcp[dest - sd.base] = ds[u] & kLow30;
         bytes += 4;
       }
       continue;
     }
-    const uint32_t nd = d & kLow30;
+    const uint32_t nd = ds[u] & kLow30;
     const uint32_t adv = nd - depth;
-    const uint32_t size = bucket_first(bb[u] + 1) - bucket_first(bb[u]);
-    if (c.big_enabled && size > c.big_threshold) {
-      u128 k = key[u];
-      bytes += 50;
-      if (adv) {
-        k = load_key128(sd.chars, rec_offset(sd, wide, wi[u].x, wi[u].y), nd, sd.cap, sd.dna);
-        bytes += 16;
+    u128 k = key[u];
+    if (how[u] == kGather) {
+      if (sd.dna) {
+        const uint64_t o = rec_offset(sd, wide, wi[u].x, wi[u].y);
+        k = to_wide[u] ? load_key128(sd.chars, o, nd, sd.cap, 1u) : make_k(dna_key(sd.chars, o, nd, sd.cap), 0);
+      } else {
+        uint64_t w[2];
+        const uint64_t o = rec_offset(sd, wide, wi[u].x, wi[u].y);
+        const uint32_t nw = finish_windows<2>(ww[u], sd.chars, o, nd, sd.cap, w);
+        // bytes past the 4 KiB block of the first character decide: word by word
+        if (nw == 0) w[0] = load_cache(sd.chars, o, nd, sd.cap);
+        if (to_wide[u] && nw < 2) w[1] = has_nul(w[0]) ? 0ull : load_cache(sd.chars, o, nd + 8, sd.cap);
+        k = make_k(w[0], w[1]);
       }
+      bytes += to_wide[u] ? 16 : 8;
+    }
+    if (to_wide[u]) {
+      bytes += 50;
       store_wkey(c.rec[par ^ 1] + dest, k);
       c.wid[par ^ 1][dest] = wi[u];
     } else {
-      uint64_t k;
       bytes += 42;
-      if (!sd.dna && adv <= 8) {
-        k = narrow_at(key[u], adv);
-      } else if (sd.dna && (adv == 0 || adv == kDnaWidth)) {
-        k = adv ? k_lo(key[u]) : k_hi(key[u]);
-      } else {
-        k = load_key(sd.chars, rec_offset(sd, wide, wi[u].x, wi[u].y), nd, sd.cap, sd.dna);
-        bytes += 8;
-      }
-      store_rec(c.rec[par ^ 1] + dest, k, wi[u].x, wi[u].y);
+      // a gathered narrow key is the first half; a kept one is cut out of the wide key
+      const uint64_t nk = how[u] == kGather ? k_hi(k) : (sd.dna ? (adv ? k_lo(k) : k_hi(k)) : narrow_at(k, adv));
+      store_rec(c.rec[par ^ 1] + dest, nk, wi[u].x, wi[u].y);
     }
   }
   return bytes;
