@@ -77,11 +77,24 @@ __device__ __forceinline__ void store_mrec(MergeRec* p, const MergeRec& r) {
   q[1] = make_uint4((uint32_t)r.off, (uint32_t)(r.off >> 32), r.idx, r.h);
 }
 
-// The 16 characters of a string from depth h (no terminator before h).
+// The 16 characters of a string from depth h (no terminator before h): the
+// three aligned words that cover them in one round trip when they lie in the
+// 4 KiB block of byte h, otherwise word by word while the string continues.
+__device__ __forceinline__ void finish_words(const WindowWords<2>& ww, const uint8_t* chars, uint32_t cap,
+                                             uint64_t off, uint32_t h, uint64_t& w0, uint64_t& w1) {
+  uint64_t w[2];
+  const uint32_t nw = finish_windows<2>(ww, chars, off, h, cap, w);
+  if (nw == 0) w[0] = cache_at(chars, cap, off, h);
+  if (nw < 2) w[1] = has_nul(w[0]) ? 0ull : cache_at(chars, cap, off, h + 8);
+  w0 = w[0];
+  w1 = w[1];
+}
+
 __device__ __forceinline__ void load_words(const uint8_t* chars, uint32_t cap, uint64_t off, uint32_t h,
                                            uint64_t& w0, uint64_t& w1) {
-  w0 = cache_at(chars, cap, off, h);
-  w1 = has_nul(w0) ? 0ull : cache_at(chars, cap, off, h + 8);
+  WindowWords<2> ww;
+  issue_windows<2>(chars, off, h, cap, ww);
+  finish_words(ww, chars, cap, off, h, w0, w1);
 }
 
 // Index of the last range whose start is <= i (starts non-decreasing).
@@ -96,16 +109,44 @@ __device__ __forceinline__ uint32_t find_range(const uint32_t* start, uint32_t c
 
 // ---- round 0: records of the input runs --------------------------------------------------
 
+// Records built per thread at once: the loads of all of them are issued
+// level by level (entries, offsets, characters), one round trip each.
+constexpr int kPrepBatch = 4;
+
 __global__ void __launch_bounds__(256) k_merge_prep(MergePrepArgs a) {
-  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += gridDim.x * blockDim.x) {
-    const uint32_t k = find_range(a.start, a.K, g);
-    const uint32_t j = g - a.start[k];
-    MergeRec r;
-    r.idx = a.perm[k][j] + a.ibase[k];
-    r.h = j ? a.lcp[k][j] : 0u;
-    r.off = a.offsets[r.idx];
-    load_words(a.chars, a.cap, r.off, r.h, r.w0, r.w1);
-    store_mrec(a.dst + g, r);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t g0 = blockIdx.x * blockDim.x + threadIdx.x; g0 < a.total; g0 += stride * kPrepBatch) {
+    uint32_t idx[kPrepBatch], h[kPrepBatch];
+    uint64_t off[kPrepBatch];
+    WindowWords<2> ww[kPrepBatch];
+#pragma unroll
+    for (int u = 0; u < kPrepBatch; ++u) {
+      const uint32_t g = g0 + u * stride;
+      idx[u] = 0;
+      h[u] = 0;
+      if (g < a.total) {
+        const uint32_t k = find_range(a.start, a.K, g);
+        const uint32_t j = g - a.start[k];
+        idx[u] = a.perm[k][j] + a.ibase[k];
+        h[u] = j ? a.lcp[k][j] : 0u;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPrepBatch; ++u) off[u] = g0 + u * stride < a.total ? a.offsets[idx[u]] : 0ull;
+#pragma unroll
+    for (int u = 0; u < kPrepBatch; ++u)
+      if (g0 + u * stride < a.total) issue_windows<2>(a.chars, off[u], h[u], a.cap, ww[u]);
+#pragma unroll
+    for (int u = 0; u < kPrepBatch; ++u) {
+      const uint32_t g = g0 + u * stride;
+      if (g >= a.total) continue;
+      MergeRec r;
+      r.idx = idx[u];
+      r.h = h[u];
+      r.off = off[u];
+      finish_words(ww[u], a.chars, a.cap, off[u], h[u], r.w0, r.w1);
+      store_mrec(a.dst + g, r);
+    }
   }
 }
 
