@@ -230,7 +230,7 @@ typedef struct ss_run {
  *   max_len    as ss_options.max_len; it must be the value the runs were
  *              sorted with.  Strings are compared up to 2^30 characters.
  *   sample_step  every sample_step-th string of a run bounds a piece
- *              (16..65536; 0 = 128).
+ *              (16..65536; 0 = 64).
  *   workspace  device memory of ss_merge_workspace_size() bytes, 256-byte
  *              aligned, or NULL (a stream-ordered allocation is made and
  *              freed on `stream`).

@@ -740,7 +740,7 @@ ss_status ss_distinguishing(const uint8_t* chars, const uint64_t* offsets, uint6
 
 // ---- K-way LCP merge ------------------------------------------------------------------
 
-static uint32_t merge_step(uint32_t sample_step) { return sample_step ? sample_step : 128; }
+static uint32_t merge_step(uint32_t sample_step) { return sample_step ? sample_step : 64; }
 
 static ss_status merge_geometry(const ss_run* runs, uint32_t num_runs, uint32_t sample_step, uint64_t* total,
                                 uint32_t* S) {
@@ -1061,8 +1061,8 @@ ss_status ss_sort_dna(const uint8_t* chars, uint64_t chars_len, const uint64_t* 
 // 16.0 / 20.4 ms in 2 / 4 / 8 parts).
 constexpr uint32_t kPipeAutoParts = 1;
 // Merges of the parts use a sample step between these two, the largest that
-// still gives about 1024 pieces per SM (a piece is merged by one thread).
-constexpr uint32_t kPipeMinStep = 16, kPipeMaxStep = 128;
+// still gives about 1024 pieces per SM (a piece is merged by one lane).
+constexpr uint32_t kPipeMinStep = 16, kPipeMaxStep = 64;
 static_assert(sizeof(SetDesc) % 4 == 0 && sizeof(GenTask) % 4 == 0, "uploads move whole words");
 
 // A copy stream and its events, per thread and device.

@@ -14,17 +14,22 @@
 // for each sample, the records of the partner run that go before it, with a
 // binary search that skips the prefix every record between the two bounds
 // shares with the sample.  The pieces of a pair of runs are the stretches of
-// its output between consecutive samples; each thread takes pieces from a
-// counter.  With two runs a piece holds at most 2S records.
+// its output between consecutive samples; each warp takes 32 pieces at a
+// time from a counter, one per lane.  With two runs a piece holds at most 2S
+// records.
 //
 // Merging a piece.  Both front records carry h = LCP with the last string
 // output (a piece starts after a sample, whose LCP with the other run's front
 // is computed directly).  LCP-Compare (Algorithm 4.2): unequal h decide
 // without reading characters (the larger h goes first, the loser keeps its
-// h); equal h compare the cached words, and read the strings only when 16
-// characters agree; the loser's h becomes its LCP with the winner and its
-// words are reloaded at that depth.  Ties of equal strings go by index, and an
-// index present in both runs takes the first run's record first.
+// h); equal h compare the cached characters, and read the strings only when
+// all the cached characters both records still hold agree; the loser's h
+// becomes its LCP with the winner.  The loser's cache then moves on to that
+// depth by a shift (the characters between the old and the new h are the
+// ones the two strings share), so a record holds from 1 to 16 valid cached
+// characters; only a comparison that runs past them reads the strings, and
+// the loser's cache is reloaded after it.  Ties of equal strings go by index,
+// and an index present in both runs takes the first run's record first.
 #include "../../include/ss_sort.h"
 #include "ss_kernels.h"
 
@@ -59,22 +64,45 @@ __device__ __forceinline__ int cmp_from(const uint8_t* chars, uint32_t cap, uint
   }
 }
 
-__device__ __forceinline__ MergeRec load_mrec(const MergeRec* p) {
+// A record in registers: the memory record plus how many of its 16 cached
+// characters are not valid (the cache was shifted after a comparison).  In
+// memory that count sits in the top byte of the offset (string offsets are
+// below 2^56).
+struct MRec {
+  uint64_t w0, w1, off;
+  uint32_t idx, h, miss;
+};
+constexpr uint64_t kOffMask = (1ull << 56) - 1;
+
+__device__ __forceinline__ MRec load_mrec(const MergeRec* p) {
   const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
   const uint4 b = __ldg(reinterpret_cast<const uint4*>(p) + 1);
-  MergeRec r;
+  MRec r;
   r.w0 = ((uint64_t)a.y << 32) | a.x;
   r.w1 = ((uint64_t)a.w << 32) | a.z;
-  r.off = ((uint64_t)b.y << 32) | b.x;
+  const uint64_t o = ((uint64_t)b.y << 32) | b.x;
+  r.off = o & kOffMask;
+  r.miss = (uint32_t)(o >> 56);
   r.idx = b.z;
   r.h = b.w;
   return r;
 }
 
-__device__ __forceinline__ void store_mrec(MergeRec* p, const MergeRec& r) {
+__device__ __forceinline__ void store_mrec(MergeRec* p, const MRec& r) {
   uint4* q = reinterpret_cast<uint4*>(p);
+  const uint64_t o = r.off | ((uint64_t)r.miss << 56);
   q[0] = make_uint4((uint32_t)r.w0, (uint32_t)(r.w0 >> 32), (uint32_t)r.w1, (uint32_t)(r.w1 >> 32));
-  q[1] = make_uint4((uint32_t)r.off, (uint32_t)(r.off >> 32), r.idx, r.h);
+  q[1] = make_uint4((uint32_t)o, (uint32_t)(o >> 32), r.idx, r.h);
+}
+
+// Position (0..15) of the first zero byte of a 16-character cache (first
+// character most significant), 16 if none.  Exact per byte: no borrow runs
+// between bytes.
+__device__ __forceinline__ uint32_t first_zero_char(uint64_t w0, uint64_t w1) {
+  constexpr uint64_t k7F = 0x7F7F7F7F7F7F7F7Full;
+  const uint64_t z0 = ~(((w0 & k7F) + k7F) | w0 | k7F);
+  const uint64_t z1 = ~(((w1 & k7F) + k7F) | w1 | k7F);
+  return z0 ? (uint32_t)__clzll((long long)z0) >> 3 : (z1 ? 8u + ((uint32_t)__clzll((long long)z1) >> 3) : 16u);
 }
 
 // The 16 characters of a string from depth h (no terminator before h): the
@@ -140,10 +168,11 @@ __global__ void __launch_bounds__(256) k_merge_prep(MergePrepArgs a) {
     for (int u = 0; u < kPrepBatch; ++u) {
       const uint32_t g = g0 + u * stride;
       if (g >= a.total) continue;
-      MergeRec r;
+      MRec r;
       r.idx = idx[u];
       r.h = h[u];
       r.off = off[u];
+      r.miss = 0;
       finish_words(ww[u], a.chars, a.cap, off[u], h[u], r.w0, r.w1);
       store_mrec(a.dst + g, r);
     }
@@ -159,7 +188,7 @@ __global__ void __launch_bounds__(256) k_merge_cut(MergeRoundArgs a) {
   for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < a.nsamples; s += gridDim.x * blockDim.x) {
     const uint32_t c = find_range(a.sbase, a.ncur, s);
     const uint32_t pos = (s - a.sbase[c] + 1) * a.S - 1;
-    const MergeRec x = load_mrec(a.src + a.start[c] + pos);
+    const MRec x = load_mrec(a.src + a.start[c] + pos);
     const uint32_t q = c ^ 1u;
     uint32_t lo = 0, hi = 0;
     if (q < a.ncur) {
@@ -170,7 +199,7 @@ __global__ void __launch_bounds__(256) k_merge_cut(MergeRoundArgs a) {
       while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
         const uint4 b = __ldg(reinterpret_cast<const uint4*>(prt + mid) + 1);
-        const uint64_t off = ((uint64_t)b.y << 32) | b.x;
+        const uint64_t off = (((uint64_t)b.y << 32) | b.x) & kOffMask;
         uint32_t l;
         const int cmp = cmp_from(a.chars, a.cap, b.z, off, x.idx, x.off, llo < lhi ? llo : lhi, &l);
         if (strict ? cmp < 0 : cmp <= 0) {
@@ -222,112 +251,150 @@ __device__ __forceinline__ uint32_t last_sample_below(const MergeRoundArgs& a, u
 
 // ---- merging ------------------------------------------------------------------------------
 
+// Pieces are taken 32 at a time by a warp, one per lane, and the lanes merge
+// them in lockstep: each iteration runs the same instructions on every lane
+// (the choice between the fronts, the reload of the loser's words and the
+// advance of the winner are selects and predicated loads), so lanes diverge
+// only where a comparison has to read past the 16 cached characters; a lane
+// whose piece is done idles until the longest piece of its warp is.
 __global__ void __launch_bounds__(kMergeBlock) k_merge_round(MergeRoundArgs a) {
   const uint32_t npairs = (a.ncur + 1) / 2;
   const uint32_t npieces = a.nsamples + npairs;
+  const uint32_t lane = lane_id();
+  const bool last = a.dst == nullptr;
   while (true) {
-    const uint32_t q = atomicAdd(a.counter, 1u);
-    if (q >= npieces) return;
-    // the pair and the end of this piece (records of each run up to it)
-    uint32_t p, ea, eb;
-    if (q < a.nsamples) {
-      const uint32_t c = find_range(a.sbase, a.ncur, q);
-      p = c >> 1;
-      sample_end(a, c, q - a.sbase[c], ea, eb);
-    } else {
-      p = q - a.nsamples;
-      ea = a.start[min(2 * p + 1, a.ncur)] - a.start[2 * p];
-      eb = a.start[min(2 * p + 2, a.ncur)] - a.start[min(2 * p + 1, a.ncur)];
-    }
-    const uint32_t cA = 2 * p, cB = 2 * p + 1;
-    const uint32_t base = a.start[cA];
-    const MergeRec* A = a.src + base;
-    const MergeRec* B = a.src + a.start[min(cB, a.ncur)];
-    // the piece starts after the latest sample of the pair that ends before it
-    uint32_t sa = 0, sb = 0, prev_run = 2;  // prev_run: 0 = A, 1 = B, 2 = none
-    {
-      uint32_t ra = 0, rb = 0;
-      const uint32_t ta = last_sample_below(a, cA, ea + eb, ra);
-      const uint32_t tb = last_sample_below(a, cB, ea + eb, rb);
-      if (ta != kNoSample && (tb == kNoSample || ra > rb)) {
-        sample_end(a, cA, ta, sa, sb);
-        prev_run = 0;
-      } else if (tb != kNoSample) {
-        sample_end(a, cB, tb, sa, sb);
-        prev_run = 1;
+    uint32_t q0 = 0;
+    if (lane == 0) q0 = atomicAdd(a.counter, 32u);
+    q0 = __shfl_sync(0xFFFFFFFFu, q0, 0);
+    if (q0 >= npieces) return;
+    const uint32_t q = q0 + lane;
+    uint32_t out = 0, out_end = 0, ia = 0, jb = 0, ea = 0, eb = 0, base = 0;
+    const MergeRec* A = a.src;
+    const MergeRec* B = a.src;
+    MRec fa{}, fb{};
+    if (q < npieces) {
+      // the pair and the end of this piece (records of each run up to it)
+      uint32_t p;
+      if (q < a.nsamples) {
+        const uint32_t c = find_range(a.sbase, a.ncur, q);
+        p = c >> 1;
+        sample_end(a, c, q - a.sbase[c], ea, eb);
+      } else {
+        p = q - a.nsamples;
+        ea = a.start[min(2 * p + 1, a.ncur)] - a.start[2 * p];
+        eb = a.start[min(2 * p + 2, a.ncur)] - a.start[min(2 * p + 1, a.ncur)];
+      }
+      const uint32_t cA = 2 * p, cB = 2 * p + 1;
+      base = a.start[cA];
+      A = a.src + base;
+      B = a.src + a.start[min(cB, a.ncur)];
+      // the piece starts after the latest sample of the pair that ends before it
+      uint32_t sa = 0, sb = 0, prev_run = 2;  // prev_run: 0 = A, 1 = B, 2 = none
+      {
+        uint32_t ra = 0, rb = 0;
+        const uint32_t ta = last_sample_below(a, cA, ea + eb, ra);
+        const uint32_t tb = last_sample_below(a, cB, ea + eb, rb);
+        if (ta != kNoSample && (tb == kNoSample || ra > rb)) {
+          sample_end(a, cA, ta, sa, sb);
+          prev_run = 0;
+        } else if (tb != kNoSample) {
+          sample_end(a, cB, tb, sa, sb);
+          prev_run = 1;
+        }
+      }
+      out = sa + sb;
+      out_end = ea + eb;
+      ia = sa;
+      jb = sb;
+      if (out < out_end) {
+        if (ia < ea) fa = load_mrec(A + ia);
+        if (jb < eb) fb = load_mrec(B + jb);
+        // LCP of the other run's front with the sample just before the piece
+        if (prev_run == 0 && jb < eb) {
+          const MRec P = load_mrec(A + sa - 1);
+          cmp_from(a.chars, a.cap, P.idx, P.off, fb.idx, fb.off, 0, &fb.h);
+          load_words(a.chars, a.cap, fb.off, fb.h, fb.w0, fb.w1);
+          fb.miss = 0;
+        } else if (prev_run == 1 && ia < ea) {
+          const MRec P = load_mrec(B + sb - 1);
+          cmp_from(a.chars, a.cap, P.idx, P.off, fa.idx, fa.off, 0, &fa.h);
+          load_words(a.chars, a.cap, fa.off, fa.h, fa.w0, fa.w1);
+          fa.miss = 0;
+        }
       }
     }
-    uint32_t out = sa + sb;
-    const uint32_t out_end = ea + eb;
-    if (out >= out_end) continue;
-    uint32_t ia = sa, jb = sb;
-    MergeRec fa{}, fb{};
-    if (ia < ea) fa = load_mrec(A + ia);
-    if (jb < eb) fb = load_mrec(B + jb);
-    // LCP of the other run's front with the sample just before the piece
-    if (prev_run == 0 && jb < eb) {
-      const MergeRec P = load_mrec(A + sa - 1);
-      cmp_from(a.chars, a.cap, P.idx, P.off, fb.idx, fb.off, 0, &fb.h);
-      load_words(a.chars, a.cap, fb.off, fb.h, fb.w0, fb.w1);
-    } else if (prev_run == 1 && ia < ea) {
-      const MergeRec P = load_mrec(B + sb - 1);
-      cmp_from(a.chars, a.cap, P.idx, P.off, fa.idx, fa.off, 0, &fa.h);
-      load_words(a.chars, a.cap, fa.off, fa.h, fa.w0, fa.w1);
-    }
-    const bool last = a.dst == nullptr;
-    while (out < out_end) {
-      bool take_a;
-      if (ia >= ea) {
-        take_a = false;
-      } else if (jb >= eb) {
-        take_a = true;
-      } else if (fa.h != fb.h) {
-        take_a = fa.h > fb.h;  // the larger LCP with the last output goes first; the loser keeps its h
-      } else {
-        const uint32_t h = fa.h;
-        uint32_t lw;
-        if (fa.w0 != fb.w0) {
-          take_a = fa.w0 < fb.w0;
-          lw = h + lcp8(fa.w0, fb.w0);
-        } else if (has_nul(fa.w0)) {
-          take_a = fa.idx <= fb.idx;
-          lw = h + nnz_prefix(fa.w0);
-        } else if (fa.w1 != fb.w1) {
-          take_a = fa.w1 < fb.w1;
-          lw = h + 8 + lcp8(fa.w1, fb.w1);
-        } else if (has_nul(fa.w1)) {
-          take_a = fa.idx <= fb.idx;
-          lw = h + 8 + nnz_prefix(fa.w1);
+    while (__any_sync(0xFFFFFFFFu, out < out_end)) {
+      const bool act = out < out_end;
+      const bool a_ok = act && ia < ea, b_ok = act && jb < eb;
+      const bool both = a_ok && b_ok;
+      const bool eqh = fa.h == fb.h;
+      // equal LCPs with the last output: the m characters both caches still
+      // hold decide unless they agree and neither string ends among them
+      const uint32_t m = 16u - max(fa.miss, fb.miss);  // >= 1
+      const u128 ka = make_k(fa.w0, fa.w1), kb = make_k(fb.w0, fb.w1);
+      const u128 x = (ka ^ kb) & (m >= 16 ? ~(u128)0 : ~(~(u128)0 >> (8 * m)));
+      const uint32_t za = first_zero_char(fa.w0, fa.w1);
+      const uint64_t xh = k_hi(x), xl = k_lo(x);
+      const uint32_t c = xh ? (uint32_t)__clzll((long long)xh) >> 3 : 8u + ((uint32_t)__clzll((long long)xl) >> 3);
+      bool wtake = x != 0 ? ka < kb : fa.idx <= fb.idx;
+      uint32_t lw = fa.h + (x != 0 ? c : za);
+      const bool slow = both && eqh && x == 0 && za >= m;
+      if (slow) wtake = cmp_from(a.chars, a.cap, fa.idx, fa.off, fb.idx, fb.off, fa.h + m, &lw) <= 0;
+      // unequal LCPs decide without characters: the larger goes first, the
+      // loser keeps its LCP
+      const bool take_a = a_ok && (!b_ok || (eqh ? wtake : fa.h > fb.h));
+      // after a comparison of equal LCPs the loser's LCP with the last output
+      // becomes lw: its cache shifts by lw - h, or, after reading the strings,
+      // is reloaded at lw
+      const bool moved = both && eqh;
+      const uint64_t loff = take_a ? fb.off : fa.off;
+      WindowWords<2> ww;
+      if (slow) issue_windows<2>(a.chars, loff, lw, a.cap, ww);
+      // the winner is output; its run moves on
+      const MRec w = take_a ? fa : fb;
+      if (act) {
+        if (last) {
+          a.out_perm[base + out] = w.idx;
+          if (a.out_lcp) a.out_lcp[base + out] = out == 0 ? 0u : w.h;
         } else {
-          take_a = cmp_from(a.chars, a.cap, fa.idx, fa.off, fb.idx, fb.off, h + 16, &lw) <= 0;
-        }
-        if (take_a) {
-          if (lw != fb.h) {
-            fb.h = lw;
-            load_words(a.chars, a.cap, fb.off, lw, fb.w0, fb.w1);
-          }
-        } else if (lw != fa.h) {
-          fa.h = lw;
-          load_words(a.chars, a.cap, fa.off, lw, fa.w0, fa.w1);
+          MRec o = w;
+          if (out == 0) o.h = 0;
+          store_mrec(a.dst + base + out, o);
         }
       }
-      const MergeRec w = take_a ? fa : fb;
-      if (last) {
-        a.out_perm[base + out] = w.idx;
-        if (a.out_lcp) a.out_lcp[base + out] = out == 0 ? 0u : w.h;
-      } else {
-        MergeRec o = w;
-        if (out == 0) o.h = 0;
-        store_mrec(a.dst + base + out, o);
+      const uint32_t nia = ia + ((act && take_a) ? 1u : 0u);
+      const uint32_t njb = jb + ((act && !take_a) ? 1u : 0u);
+      const bool more = act && (take_a ? nia < ea : njb < eb);
+      MRec nx{};
+      if (more) nx = load_mrec(take_a ? A + nia : B + njb);
+      // the loser's new cache
+      MRec& lo = take_a ? fb : fa;
+      uint64_t r0 = lo.w0, r1 = lo.w1;
+      uint32_t rmiss = lo.miss;
+      if (slow) {
+        finish_words(ww, a.chars, a.cap, loff, lw, r0, r1);
+        rmiss = 0;
+      } else if (moved) {
+        const uint32_t d = lw - lo.h;  // < m: the cache keeps at least one valid character
+        const u128 sk = d ? (make_k(r0, r1) << (8 * d)) : make_k(r0, r1);
+        r0 = k_hi(sk);
+        r1 = k_lo(sk);
+        rmiss += d;
       }
-      ++out;
-      // the winner's run moves on: one load for every lane, from the run it took
-      if (take_a) ++ia; else ++jb;
-      const bool more = take_a ? ia < ea : jb < eb;
-      if (more) {
-        const MergeRec nx = load_mrec(take_a ? A + ia : B + jb);
-        if (take_a) fa = nx; else fb = nx;
+      if (act) {
+        if (moved) {
+          lo.h = lw;
+          lo.w0 = r0;
+          lo.w1 = r1;
+          lo.miss = rmiss;
+        }
+        if (more) {
+          if (take_a) fa = nx; else fb = nx;
+        }
       }
+      ia = nia;
+      jb = njb;
+      out += act ? 1u : 0u;
     }
   }
 }
