@@ -226,9 +226,9 @@ def measured_peaks():
     try:
         with open(p) as f:
             m = json.load(f)
-        return float(m["hbm_gbs"]), "measured"
+        return float(m["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, "fallback (6.8 TB/s; MEASURED_PEAKS.json absent)"
 
 
 def ncu_traffic(kernel: str, config: str):
@@ -442,7 +442,7 @@ def run_ours(args, ws, rank, local):
         achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if kms > 0 else 0.0
         path_bytes = D + 16 * n
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": ncu_traffic(name, args.config),
                 "alg_bytes_per_launch": kbytes / nl, "launches": nl, "ms_per_launch": kms / nl,
                 "path_alg_bytes_per_step": path_bytes,
@@ -598,7 +598,7 @@ def run_merge(args, ws, rank, local):
         kbytes = merge_round_bytes(n, K)
         achieved = kbytes / (kms / nl / 1e3) / 1e9
         roof = {"bound": "hbm", "kernel": "merge_round", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": ncu_traffic("merge_round", "m2"), "alg_bytes_per_launch": kbytes,
                 "launches": nl, "ms_per_launch": kms / nl,
                 "kernel_share": {k: round(v[1] / sum(x[1] for x in stats.values()), 4) for k, v in stats.items()},
@@ -747,7 +747,7 @@ def run_sa(args, ws, rank, local):
         name, (nl, kms, kbytes) = max(counted.items(), key=lambda kv: kv[1][1])
         achieved = (kbytes / nl) / (kms / nl / 1e3) / 1e9 if kms > 0 else 0.0
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "frac": achieved / peak, "peak_source": peak_kind,
                 "traffic": None, "alg_bytes_per_launch": kbytes / nl, "launches": nl, "ms_per_launch": kms / nl,
                 "kernel_share": {k: round(v[1] / sum(x[1] for x in stats.values()), 4) for k, v in stats.items()},
                 "timing": "CUDA events around each launch in a profiled pass of the same steps after the timed region",
