@@ -221,6 +221,14 @@ def _prefix_sets():
     pre300 = bytes(rng.integers(97, 123, 300).astype(np.uint8))
     sets["prefix300"] = [pre300 + t for t in tails(20_000, 0, 6)]  # several jumps in a row
     sets["identical150"] = [pre300[:150]] * 12_000 + [pre300[:149]] * 50
+    # groups of 1500..6000 strings (subsets of the work queue) sharing 20..200
+    # more characters within the group
+    grp = []
+    for _ in range(16):
+        head = bytes(rng.integers(97, 123, 6).astype(np.uint8))
+        shared = bytes(rng.integers(97, 123, int(rng.integers(20, 200))).astype(np.uint8))
+        grp += [head + shared + t for t in tails(int(rng.integers(1500, 6000)), 0, 5)]
+    sets["queue_groups"] = grp
     return sets
 
 
@@ -228,15 +236,18 @@ PREFIX_SETS = _prefix_sets()
 
 
 @pytest.mark.parametrize("cap", [0, 20, 40])
-@pytest.mark.parametrize("opts", [dict(big_threshold=2048), dict(big_threshold=4096, classifier=2), dict()])
+@pytest.mark.parametrize("opts", [dict(big_threshold=2048), dict(big_threshold=4096, classifier=2), dict(),
+                                  dict(big_threshold=1 << 30)])
 @pytest.mark.parametrize("name", sorted(PREFIX_SETS))
 def test_subsets_with_long_common_prefixes(name, opts, cap):
-    """Multi-block subsets whose whole sample is one key, where the step
-    jumps over the subset's common prefix (up to 64 characters at a time)
-    instead of walking it 8 characters per step, against the oracle:
-    prefixes of 12, 45 and 300 characters, identical strings, strings ending
+    """Subsets whose strings share a long prefix, where a step jumps over the
+    subset's common prefix (up to 64 characters at a time) instead of walking
+    it 8 or 16 characters per step, against the oracle: multi-block subsets
+    whose whole sample is one key, and (big_threshold 2^30: every subset in
+    the work queue) subsets that fall whole into one equality bucket;
+    prefixes of 12 to 300 characters, identical strings, strings ending
     inside the prefix, caps inside it, a first member that differs (no jump),
-    several hosts."""
+    several hosts, groups of queue-sized subsets."""
     s = from_strings(PREFIX_SETS[name], max_len=cap)
     p, l = gpu_sort(s, **opts)
     assert_parity(s, p, l)
