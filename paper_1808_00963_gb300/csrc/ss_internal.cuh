@@ -237,16 +237,19 @@ struct WindowWords {
   uint64_t word[KW + 1];
 };
 
+// Loads the first `words` (<= KW + 1) of the words; a caller that uses only
+// the first window may ask for 2 (the rest read as 0, and their windows are
+// not to be used).
 template <int KW>
 __device__ __forceinline__ void issue_windows(const uint8_t* chars, uint64_t off, uint32_t h, uint32_t cap,
-                                              WindowWords<KW>& ww) {
+                                              WindowWords<KW>& ww, uint32_t words = KW + 1) {
   const uintptr_t a = (uintptr_t)(chars + off + h);
   const uintptr_t blk_end = (a & ~(uintptr_t)4095) + 4096;
   const uintptr_t p0 = a & ~(uintptr_t)7;
 #pragma unroll
   for (int i = 0; i <= KW; ++i) {
     const uintptr_t q = p0 + 8 * (uintptr_t)i;
-    ww.word[i] = (h < cap && q < blk_end) ? __ldg(reinterpret_cast<const uint64_t*>(q)) : 0ull;
+    ww.word[i] = ((uint32_t)i < words && h < cap && q < blk_end) ? __ldg(reinterpret_cast<const uint64_t*>(q)) : 0ull;
   }
 }
 

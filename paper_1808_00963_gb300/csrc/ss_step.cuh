@@ -551,8 +551,9 @@ __device__ __forceinline__ uint32_t move_batch_wide(const SortCtx& c, const SetD
     to_wide[u] = c.big_enabled && size > c.big_threshold;
     const bool derive = to_wide[u] ? adv == 0 : (sd.dna ? (adv == 0 || adv == kDnaWidth) : adv <= 8);
     how[u] = derive ? kKeep : kGather;
-    if (!derive && !sd.dna)
-      issue_windows<2>(sd.chars, rec_offset(sd, wide, wi[u].x, wi[u].y), d & kLow30, sd.cap, ww[u]);
+    if (!derive && !sd.dna)  // a narrow key needs the first window only: two words, not three
+      issue_windows<2>(sd.chars, rec_offset(sd, wide, wi[u].x, wi[u].y), d & kLow30, sd.cap, ww[u],
+                       to_wide[u] ? 3u : 2u);
   }
 #pragma unroll
   for (int u = 0; u < MB; ++u) {
