@@ -225,7 +225,7 @@ __device__ unsigned long long queue_step(const SortCtx& c, const Task& t, QueueS
 }
 
 template <int LOGV>
-__global__ void __launch_bounds__(kBlock, 4) k_queue(SortCtx c, uint32_t R) {
+__global__ void __launch_bounds__(kBlock, 3) k_queue(SortCtx c, uint32_t R) {
   extern __shared__ __align__(16) uint8_t smem[];
   QueueSmem<LOGV>& s = *reinterpret_cast<QueueSmem<LOGV>*>(smem);
   unsigned long long bytes = 0;

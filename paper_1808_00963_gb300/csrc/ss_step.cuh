@@ -468,11 +468,16 @@ __device__ __forceinline__ uint32_t move_batch(const SortCtx& c, const SetDesc& 
       o32[u] = r.off;
     }
   }
+  // the characters of every byte-string reload are requested before any of
+  // them is used (one memory round trip for the batch)
+  WindowWords<1> ww[kMoveBatch];
 #pragma unroll
   for (int u = 0; u < kMoveBatch; ++u) {
     off[u] = 0;
-    if (pp[u] != kInvalid && !(ds[u] & kFin) && (ds[u] & kLow30) != depth)
+    if (pp[u] != kInvalid && !(ds[u] & kFin) && (ds[u] & kLow30) != depth) {
       off[u] = rec_offset(sd, wide, id[u], o32[u]);
+      if (!sd.dna) issue_windows<1>(sd.chars, off[u], ds[u] & kLow30, sd.cap, ww[u]);
+    }
   }
 #pragma unroll
   for (int u = 0; u < kMoveBatch; ++u) {
@@ -492,7 +497,13 @@ __device__ __forceinline__ uint32_t move_batch(const SortCtx& c, const SetDesc& 
     uint64_t k = key[u];
     bytes += 34;
     if (nd != depth) {
-      k = load_key(sd.chars, off[u], nd, sd.cap, sd.dna);
+      if (sd.dna) {
+        k = load_key(sd.chars, off[u], nd, sd.cap, 1u);
+      } else {
+        uint64_t w[1];
+        // bytes past the 4 KiB block of the first character decide: word by word
+        k = finish_windows<1>(ww[u], sd.chars, off[u], nd, sd.cap, w) ? w[0] : load_cache(sd.chars, off[u], nd, sd.cap);
+      }
       bytes += 8;
     }
     store_rec(c.rec[par ^ 1] + dest, k, id[u], o32[u]);
