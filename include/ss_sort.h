@@ -222,6 +222,8 @@ typedef struct ss_run {
  *              read during the call only.  Every index must be < the number
  *              of strings behind offsets (not checked).  An index may appear
  *              in several runs: it is then output once per appearance.
+ *   offsets    as for ss_sort; every offset must be below 2^56 (not checked:
+ *              the merge's records keep a count in the offset's top byte).
  *   out_perm   uint32[total] (total = sum of the runs' n): the union of the
  *              runs in string order, equal strings by ascending index — the
  *              result of sorting the union with ss_sort.
