@@ -22,6 +22,29 @@ __device__ __forceinline__ uint32_t find_gen_task(const GenTask* gt, uint32_t G,
   return lo;
 }
 
+// The first tile of every subset of the round, for up to kTileStartsMax
+// subsets, copied into shared memory when a kernel starts: a block then finds
+// the subset of each tile it takes with a shared-memory search instead of a
+// chain of dependent global loads.
+constexpr uint32_t kTileStartsMax = 4096;
+
+__device__ __forceinline__ void load_tile_starts(const GenTask* gt, uint32_t G, uint32_t* ts) {
+  const uint32_t m = G < kTileStartsMax ? G : kTileStartsMax;
+  for (uint32_t i = threadIdx.x; i < m; i += blockDim.x) ts[i] = gt[i].tile_start;
+  __syncthreads();
+}
+
+__device__ __forceinline__ uint32_t find_gen_task_ts(const GenTask* gt, const uint32_t* ts, uint32_t G,
+                                                     uint32_t tile) {
+  if (G > kTileStartsMax) return find_gen_task(gt, G, tile);
+  uint32_t lo = 0, hi = G - 1;  // last task with tile_start <= tile
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (ts[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __device__ __forceinline__ uint64_t cnt_base(const GenTask& g) {
   return ((uint64_t)g.cnt_base_hi << 32) | g.cnt_base_lo;
 }
@@ -316,17 +339,19 @@ __global__ void __launch_bounds__(kBlock, 4) k_big_classify(const BigCtl* __rest
   __shared__ __align__(16) uint16_t jump[kJumpSize];
   __shared__ uint64_t ref[kPjWindows];
   __shared__ uint32_t s_g;
+  __shared__ uint32_t ts[kTileStartsMax];
   const uint32_t G = ctl->G, tiles = ctl->tiles, R = ctl->R;
   const SortCtx& c = ctl->c;
   const GenTask* __restrict__ gt = ctl->gt;
   BigSplitters<LOGV>* spl = reinterpret_cast<BigSplitters<LOGV>*>(ctl->splitters);
   const bool use_jump = c.classifier == kClassifyUIJ;
+  load_tile_starts(gt, G, ts);
   unsigned long long bytes = 0;
   uint32_t loaded = 0xFFFFFFFFu;  // subset whose splitters are in shared memory
   ItemStream items{work, 0u};
   for (uint32_t tg = items.first(); tg < tiles; tg = items.next()) {
     items.claim();
-    if (threadIdx.x == 0) s_g = find_gen_task(gt, G, tg);
+    if (threadIdx.x == 0) s_g = find_gen_task_ts(gt, ts, G, tg);
     for (uint32_t b = threadIdx.x; b < Gm::KP; b += blockDim.x) hist[b] = 0;
     __syncthreads();
     const uint32_t gi = s_g;
@@ -429,14 +454,16 @@ __global__ void __launch_bounds__(kBlock, 3) k_big_scatter(const BigCtl* __restr
   uint32_t* bfirst = desc + Gm::KP;
   uint16_t* tb = reinterpret_cast<uint16_t*>(bfirst + Gm::KP);
   __shared__ uint32_t s_g;
+  __shared__ uint32_t ts[kTileStartsMax];
   const uint32_t G = ctl->G, tiles = ctl->tiles, R = ctl->R;
   const SortCtx& c = ctl->c;
   const GenTask* __restrict__ gt = ctl->gt;
+  load_tile_starts(gt, G, ts);
   unsigned long long bytes = 0;
   ItemStream items{work, 0u};
   for (uint32_t tg = items.first(); tg < tiles; tg = items.next()) {
     items.claim();
-    if (threadIdx.x == 0) s_g = find_gen_task(gt, G, tg);
+    if (threadIdx.x == 0) s_g = find_gen_task_ts(gt, ts, G, tg);
     __syncthreads();
     const uint32_t gi = s_g;
     const GenTask g = gt[gi];
