@@ -181,17 +181,26 @@ def test_url_1m_exact():
     assert_parity(s, p, l, exact_limit=2_000_000)
 
 
+def _tuned(kind):
+    from paper_1808_00963_gb300 import tune
+    return {k: v for k, v in tune.options_for(kind).items() if v}
+
+
 @pytest.mark.slow
-def test_config3_full():
+@pytest.mark.parametrize("options", ["defaults", "tuned"])
+def test_config3_full(options):
+    """All 4M suffixes, with the compiled defaults and with the options the
+    autotuner table gives the bench for this workload class."""
     s = gen.config3()
-    p, l = gpu_sort(s)
+    p, l = gpu_sort(s, **(_tuned("dna") if options == "tuned" else {}))
     assert_parity(s, p, l)
 
 
 @pytest.mark.slow
-def test_config2_full():
+@pytest.mark.parametrize("options", ["defaults", "tuned"])
+def test_config2_full(options):
     s = gen.config2()
-    p, l = gpu_sort(s)
+    p, l = gpu_sort(s, **(_tuned("url") if options == "tuned" else {}))
     assert_parity(s, p, l)
     # sampled exact ranks: the oracle's order restricted to a random sample of
     # strings is the order of those strings in the GPU permutation
