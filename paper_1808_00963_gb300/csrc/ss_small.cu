@@ -309,7 +309,12 @@ struct CtaSmem {  // carved from dynamic shared memory, pmax elements
 };
 
 // Order of the block sort: (segment, cache, tag), evaluated without branches.
+// OneSeg: every element is in segment 0 and none is handed on (the first pass
+// over a subset, which does nearly all of the block sorts' work), so the tags
+// compare as original positions and the segment test drops out.
+template <bool OneSeg>
 __device__ __forceinline__ bool elem_less(uint64_t ka, uint32_t ta, uint64_t kb, uint32_t tb) {
+  if (OneSeg) return (ka < kb) | ((ka == kb) & (ta < tb));
   const uint32_t sa = tag_seg(ta), sb = tag_seg(tb);
   return (sa < sb) | ((sa == sb) & ((ka < kb) | ((ka == kb) & (ta < tb))));
 }
@@ -318,17 +323,20 @@ __device__ __forceinline__ bool elem_less(uint64_t ka, uint32_t ta, uint64_t kb,
 constexpr uint32_t kPadTag = 0xFFFFFFFFu;
 
 // Bitonic sort of one (key, tag) per lane by elem_less, ascending in lane order.
+// The stages of each merge level run as a loop: the smaller code was faster
+// than the fully unrolled network in the block sort kernels.
+template <bool OneSeg>
 __device__ __forceinline__ void warp_sort_elems(uint64_t& key, uint32_t& tag) {
   const uint32_t lane = lane_id();
 #pragma unroll
   for (uint32_t k = 2; k <= 32; k <<= 1) {
-#pragma unroll
+#pragma unroll 1
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
       const uint32_t ot = __shfl_xor_sync(kFull, tag, j);
       const uint64_t ok = __shfl_xor_sync(kFull, key, j);
       const bool up = (lane & k) == 0;
       const bool lower = (lane & j) == 0;
-      const bool take = (lower == up) ? elem_less(ok, ot, key, tag) : elem_less(key, tag, ok, ot);
+      const bool take = (lower == up) ? elem_less<OneSeg>(ok, ot, key, tag) : elem_less<OneSeg>(key, tag, ok, ot);
       tag = take ? ot : tag;
       key = take ? ok : key;
     }
@@ -342,7 +350,7 @@ __device__ __forceinline__ void warp_sort_elems(uint64_t& key, uint32_t& tag) {
 // outputs start with a binary search along the merge path and merges
 // sequentially.  Uses (key2, tag2) as the second buffer; the result ends in
 // (m.key, m.tag).
-template <uint32_t NT>
+template <uint32_t NT, bool OneSeg>
 __device__ void block_sort(CtaSmem& m, uint32_t n) {
   uint32_t ipt = 1;
   while (ipt * NT < n) ipt <<= 1;
@@ -350,7 +358,7 @@ __device__ void block_sort(CtaSmem& m, uint32_t n) {
     const uint32_t p = c0 + lane_id();
     uint64_t k = p < n ? m.key[p] : ~0ull;
     uint32_t t = p < n ? m.tag[p] : kPadTag;
-    warp_sort_elems(k, t);
+    warp_sort_elems<OneSeg>(k, t);
     if (p < n) {
       m.key[p] = k;
       m.tag[p] = t;
@@ -375,13 +383,13 @@ __device__ void block_sort(CtaSmem& m, uint32_t n) {
       uint32_t lo = d > lb ? d - lb : 0u, hi = min(d, la);
       while (lo < hi) {  // number of A elements among the first d outputs
         const uint32_t mid = (lo + hi) >> 1;
-        if (!elem_less(bk[d - mid - 1], bt[d - mid - 1], ak[mid], at[mid])) lo = mid + 1;
+        if (!elem_less<OneSeg>(bk[d - mid - 1], bt[d - mid - 1], ak[mid], at[mid])) lo = mid + 1;
         else hi = mid;
       }
       uint32_t i = lo, j = d - lo;
       const uint32_t cnt = min(ipt, n - out);
       for (uint32_t q = 0; q < cnt; ++q) {
-        const bool take_a = i < la && (j >= lb || !elem_less(bk[j], bt[j], ak[i], at[i]));
+        const bool take_a = i < la && (j >= lb || !elem_less<OneSeg>(bk[j], bt[j], ak[i], at[i]));
         if (take_a) {
           dk[out + q] = ak[i];
           dt[out + q] = at[i];
@@ -530,8 +538,11 @@ __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint
       __syncthreads();
     }
 
+    bool first_pass = true;  // every tag is make_tag(0, position, 1)
     while (true) {
-      block_sort<NT>(m, n);
+      if (first_pass) block_sort<NT, true>(m, n);
+      else block_sort<NT, false>(m, n);
+      first_pass = false;
       if (threadIdx.x == 0) s_max_open = 0;
       for (uint32_t j = threadIdx.x; j < n; j += NT) {
         const uint32_t tg = m.tag[j];
