@@ -460,14 +460,22 @@ __global__ void __launch_bounds__(kBlock, 3) k_big_scatter(const BigCtl* __restr
   const GenTask* __restrict__ gt = ctl->gt;
   load_tile_starts(gt, G, ts);
   unsigned long long bytes = 0;
+  uint32_t loaded = 0xFFFFFFFFu;
+  GenTask g{};
+  SetDesc sd{};
   ItemStream items{work, 0u};
   for (uint32_t tg = items.first(); tg < tiles; tg = items.next()) {
     items.claim();
     if (threadIdx.x == 0) s_g = find_gen_task_ts(gt, ts, G, tg);
     __syncthreads();
     const uint32_t gi = s_g;
-    const GenTask g = gt[gi];
-    const SetDesc sd = c.sets[task_set(g.t)];
+    // the subset's task, set and per-bucket descriptors and starts stay in
+    // registers and shared memory while the block's tiles come from one subset
+    const bool fresh = gi != loaded;  // uniform over the block
+    if (fresh) {
+      g = gt[gi];
+      sd = c.sets[task_set(g.t)];
+    }
     const uint32_t tile = tg - g.tile_start;
     const uint32_t T = kBlock * R;
     const uint32_t t0 = tile * T;
@@ -478,15 +486,18 @@ __global__ void __launch_bounds__(kBlock, 3) k_big_scatter(const BigCtl* __restr
     const uint32_t* sc = ctl->counters + cnt_base(g) + tile;
     for (uint32_t b = threadIdx.x; b < Gm::K; b += kBlock) {
       base[b] = g.t.begin + sc[(uint64_t)b * g.tiles] - g.rec_base;
-      desc[b] = ctl->gdesc[(uint64_t)gi * Gm::KP + b];
-      bfirst[b] = g.t.begin + ctl->gstart[(uint64_t)gi * Gm::KP + b];
+      if (fresh) {
+        desc[b] = ctl->gdesc[(uint64_t)gi * Gm::KP + b];
+        bfirst[b] = g.t.begin + ctl->gstart[(uint64_t)gi * Gm::KP + b];
+      }
     }
-    if (threadIdx.x == 0) bfirst[Gm::K] = g.t.begin + g.t.len;  // bucket sizes from neighbouring starts
+    if (fresh && threadIdx.x == 0) bfirst[Gm::K] = g.t.begin + g.t.len;  // bucket sizes from neighbouring starts
+    loaded = gi;
     __syncthreads();
     const uint32_t src0 = g.t.begin + t0;
     const uint32_t depth = g.t.depth;
     const uint32_t wide = c.wide[task_set(g.t)];
-    if (threadIdx.x == 0) bytes += 12ull * Gm::K;  // per-bucket tile offsets, descriptors and starts
+    if (threadIdx.x == 0) bytes += (fresh ? 12ull : 4ull) * Gm::K;  // per-bucket tile offsets (+ descriptors and starts)
     tile_scatter<LOGV, kWideMoveBatch>(
         tb, tl, R, base, cntw,
         [&](const uint32_t(&pp)[kWideMoveBatch], const uint32_t(&bb)[kWideMoveBatch],
