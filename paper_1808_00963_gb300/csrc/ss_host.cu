@@ -206,12 +206,13 @@ static uint32_t pmax_of(uint32_t cutoff) {
 constexpr uint32_t kCtrlWords = 64;                          // status and list counters
 constexpr size_t kCtrlBytes = kCtrlWords * 4 + kKClasses * 8;  // + algorithmic byte counters
 enum Ctrl : uint32_t { kCStatus = 0, kCBig0 = 1, kCBig1 = 2, kCHead = 3, kCTail = 4, kCPending = 5,
-                       kCSmallW = 6, kCSmallC = 7, kCSmallD = 8, kCMarks = 9 };
+                       kCSmallW = 6, kCSmallC = 7, kCSmallD = 8, kCMarks = 9, kCSmallCW = 10,
+                       kCClaim = 11 /* and 12 */ };
 
 struct Layout {
   size_t ctrl, sets, wide, rec0, rec1, wid0, wid1, bucket_of, big0, big1, gen, spl, counters, partials, gstart,
-      gdesc, bigctl, marks, mq_items, mq_ready, sw_items, sc_items, total;
-  uint32_t cap_big, cap_mq, cap_sw, cap_sc;
+      gdesc, bigctl, marks, mq_items, mq_ready, sw_items, sc_items, scw_items, total;
+  uint32_t cap_big, cap_mq, cap_sw, cap_sc, cap_scw;
   uint64_t ncounters_max;
 };
 
@@ -227,6 +228,7 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   // least 2 strings (<= M/2), then as many deferred runs (<= M/2)
   L.cap_sw = (uint32_t)(M / 2 + 1);
   L.cap_sc = (uint32_t)(M / 33 + 2);
+  L.cap_scw = (uint32_t)(M / (kSmallCtaNarrowMax + 1) + 2);
   const uint64_t KP = 2ull << o.logv_big;
   const uint64_t tiles_max = big ? M / (kBlock * 8) + L.cap_big : 0;
   L.ncounters_max = big ? KP * (tiles_max + L.cap_big) : 0;
@@ -252,6 +254,7 @@ static Layout make_layout(uint64_t M, uint32_t num_sets, const Opts& o, bool big
   L.mq_ready = take((size_t)L.cap_mq * 4);
   L.sw_items = take(2 * (size_t)L.cap_sw * sizeof(Task));
   L.sc_items = take((size_t)L.cap_sc * sizeof(Task));
+  L.scw_items = take((size_t)L.cap_scw * sizeof(Task));
   L.total = off;
   return L;
 }
@@ -277,6 +280,8 @@ static SortCtx make_ctx(uint8_t* ws, const Layout& L, uint32_t num_sets, uint32_
   c.small_warp = TaskList{reinterpret_cast<Task*>(ws + L.sw_items), ctrl + kCSmallW, L.cap_sw};
   c.small_deep = TaskList{reinterpret_cast<Task*>(ws + L.sw_items) + L.cap_sw, ctrl + kCSmallD, L.cap_sw};
   c.small_cta = TaskList{reinterpret_cast<Task*>(ws + L.sc_items), ctrl + kCSmallC, L.cap_sc};
+  c.small_cta_wide = TaskList{reinterpret_cast<Task*>(ws + L.scw_items), ctrl + kCSmallCW, L.cap_scw};
+  c.small_claim = ctrl + kCClaim;
   c.marks = reinterpret_cast<uint32_t*>(ws + L.marks);
   c.marks_count = ctrl + kCMarks;
   c.marks_cap = big ? total : 0u;

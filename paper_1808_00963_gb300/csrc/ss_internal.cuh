@@ -79,6 +79,10 @@ struct GenTask {
 };
 
 // Append-only task list in device memory.
+// Block-sort subsets of up to this many strings go to 64-thread blocks, larger
+// ones to 256-thread blocks; each size class has its own task list.
+constexpr uint32_t kSmallCtaNarrowMax = 256;
+
 struct TaskList {
   Task* items;
   uint32_t* count;     // device counter
@@ -121,7 +125,9 @@ struct SortCtx {
   WorkQueue mq;            // tasks for the persistent single-block kernel
   TaskList small_warp;     // 2..32 records
   TaskList small_deep;     // runs the first warp pass deferred (long common prefixes)
-  TaskList small_cta;      // 33..small_cutoff records
+  TaskList small_cta;      // 33..min(small_cutoff, kSmallCtaNarrowMax) records (64-thread block sorts)
+  TaskList small_cta_wide; // kSmallCtaNarrowMax + 1..small_cutoff records (256-thread block sorts)
+  uint32_t* small_claim;   // [2] next subset to claim, for the two block-sort launches
   uint32_t* marks;         // record positions whose LCP entry holds a mark (multi-block step boundaries)
   uint32_t* marks_count;
   uint32_t marks_cap;
@@ -543,7 +549,7 @@ __device__ __forceinline__ void route_task(const SortCtx& c, const Task& t, uint
   if (t.depth > kMaxDepth) { latch_status(c.status, kStTooDeep); return; }
   if (c.big_enabled && t.len > c.big_threshold) list_push(c.big[next_big], t, c.status);
   else if (t.len > c.small_cutoff) queue_push(c.mq, t, c.status, c.wait_ns);
-  else if (t.len > 32) list_push(c.small_cta, t, c.status);
+  else if (t.len > 32) list_push(t.len > kSmallCtaNarrowMax ? c.small_cta_wide : c.small_cta, t, c.status);
   else list_push(c.small_warp, t, c.status);
 }
 

@@ -452,12 +452,13 @@ __device__ void block_max_scan(uint16_t* a, uint32_t n) {
   __syncthreads();
 }
 
-// Subsets with lo < len <= hi; while there are fewer than min_count subsets
-// in all, the narrow kernel (narrow = 1) leaves every subset to the wide one
-// (narrow = 0), which then takes all sizes.
+// The narrow launch (narrow = 1) sorts the subsets of c.small_cta, the wide
+// one those of c.small_cta_wide; while there are fewer than min_count subsets
+// in all, the narrow launch leaves every subset to the wide one.  Each block
+// claims one subset at a time from its launch's counter (subset sizes vary
+// several-fold, so a fixed share per block left many SMs idle at the end).
 template <uint32_t NT, bool DNA>
-__global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint32_t lo, uint32_t hi,
-                                                  uint32_t min_count, uint32_t narrow) {
+__global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint32_t min_count, uint32_t narrow) {
   constexpr uint32_t dna = DNA ? 1u : 0u;  // the character encoding, fixed per instance
   extern __shared__ __align__(16) uint8_t smem[];
   CtaSmem m;
@@ -472,14 +473,26 @@ __global__ void __launch_bounds__(NT) k_small_cta(SortCtx c, uint32_t pmax, uint
   __shared__ uint32_t s_max_open, s_jstop, s_neq;
   __shared__ uint64_t s_lead[kLookWindows];
   unsigned long long bytes = 0;
-  const uint32_t count = min(*c.small_cta.count, c.small_cta.cap);
-  if (count < min_count) {
-    if (narrow) return;
-    lo = 0;
-  }
-  for (uint32_t ti = blockIdx.x; ti < count; ti += gridDim.x) {
-    const Task t = c.small_cta.items[ti];
-    if (t.len <= lo || t.len > hi) continue;  // another block size takes this subset
+  const uint32_t n_narrow = min(*c.small_cta.count, c.small_cta.cap);
+  const uint32_t n_wide = min(*c.small_cta_wide.count, c.small_cta_wide.cap);
+  const bool few = n_narrow + n_wide < min_count;
+  if (narrow && few) return;
+  // this launch's subsets: the first na of the narrow list, then the wide list
+  const uint32_t na = (narrow || few) ? n_narrow : 0u;
+  const uint32_t count = narrow ? n_narrow : na + n_wide;
+  uint32_t* claim = c.small_claim + (narrow ? 0 : 1);
+  __shared__ uint32_t s_ti;
+  if (threadIdx.x == 0) s_ti = atomicAdd(claim, 1u);
+  __syncthreads();
+  for (uint32_t ti = s_ti; ti < count; ti = s_ti) {
+    const Task t = ti < na ? c.small_cta.items[ti] : c.small_cta_wide.items[ti - na];
+    __syncthreads();  // every thread has read s_ti
+    if (threadIdx.x == 0) s_ti = atomicAdd(claim, 1u);  // the next subset, claimed while this one sorts
+    if (t.len > pmax) {  // cannot happen: a list holds only sizes its launch's shared arrays take
+      if (threadIdx.x == 0) latch_status(c.status, kStQueueFull);
+      __syncthreads();
+      continue;
+    }
     const SetDesc sd = c.sets[task_set(t)];
     const uint32_t kw = key_width(dna);  // characters per key
     const uint32_t par = task_par(t);
@@ -712,8 +725,6 @@ __global__ void k_pack_dna(const uint8_t* __restrict__ chars, uint64_t len, uint
   }
 }
 
-constexpr uint32_t kSmallCtaNarrowMax = 256;
-
 size_t small_cta_smem(uint32_t pmax) { return (size_t)pmax * (8 + 8 + 8 + 4 + 4 + 4 + 4 + 2); }
 
 cudaError_t launch_init(const SortCtx& c, cudaStream_t st, const LaunchHook& hook) {
@@ -740,16 +751,16 @@ static cudaError_t launch_small_t(const SortCtx& c, uint32_t pmax, uint32_t grid
   const uint32_t min_count = 2 * grid_cta;
   if (pmax <= kSmallCtaNarrowMax) {
     hook.run("small_cta", [&] {
-      k_small_cta<64, DNA><<<grid_cta * 4, 64, small_cta_smem(pmax), st>>>(c, pmax, 0u, pmax, 0u, 1u);
+      k_small_cta<64, DNA><<<grid_cta * 4, 64, small_cta_smem(pmax), st>>>(c, pmax, 0u, 1u);
     });
   } else {
     hook.run("small_cta", [&] {
       k_small_cta<64, DNA><<<grid_cta * 4, 64, small_cta_smem(kSmallCtaNarrowMax), st>>>(
-          c, kSmallCtaNarrowMax, 0u, kSmallCtaNarrowMax, min_count, 1u);
+          c, kSmallCtaNarrowMax, min_count, 1u);
     });
     hook.run("small_cta", [&] {
       k_small_cta<kBlock, DNA><<<grid_cta, kBlock, small_cta_smem(pmax), st>>>(
-          c, pmax, kSmallCtaNarrowMax, 0xFFFFFFFFu, min_count, 0u);
+          c, pmax, min_count, 0u);
     });
   }
   // the lists alternate: a pass reads one and defers into the other, emptied first
