@@ -432,8 +432,9 @@ __global__ void __launch_bounds__(kBlock) k_big_emit(const BigCtl* __restrict__ 
           if (J > KeyOps<u128>::width(0) && J != 0xFFFFFFFFu) desc = g.t.depth + J;
         }
         emit_bucket(c, sd, g.t, s, size, desc, next_big, kLcpMark | kLcpWide);
-        if (s > 0 && sd.lcp) {  // the fix-up at the end visits the listed marks only
-          const uint32_t k = atomicAdd(c.marks_count, 1u);
+        const bool mark = s > 0 && sd.lcp;  // the fix-up at the end visits the listed marks only
+        const uint32_t k = warp_slot(c.marks_count, mark);
+        if (mark) {
           if (k < c.marks_cap) c.marks[k] = g.t.begin + s;
           else latch_status(c.status, kStQueueFull);
         }
@@ -509,7 +510,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_big_scatter(const BigCtl* __restr
   account(c, kKBigScatter, bytes);
 }
 
-// ---- exclusive prefix sum over uint32 (three phases) ----------------------------
+// ---- exclusive prefix sum over uint32 (two phases) ------------------------------
 
 constexpr uint32_t kScanItems = 16;
 constexpr uint32_t kScanChunk = kBlock * kScanItems;
@@ -542,7 +543,26 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t& excl) 
   return total;
 }
 
-// The counters of the round: ctl->ncounters values, in chunks of kScanChunk.
+// The kScanItems counters of thread t of chunk blk are a[blk * kScanChunk +
+// t * kScanItems ...]; in a full chunk they are read as four 16-byte words
+// (the counters start 256-byte aligned and a chunk spans 16 KiB).
+__device__ __forceinline__ void load_scan_items(const uint32_t* __restrict__ a, uint64_t n, uint64_t k0,
+                                                bool full, uint32_t (&v)[kScanItems]) {
+  if (full) {
+    const uint4* a4 = reinterpret_cast<const uint4*>(a + k0);
+#pragma unroll
+    for (uint32_t q = 0; q < kScanItems / 4; ++q) {
+      const uint4 x = a4[q];
+      v[4 * q] = x.x; v[4 * q + 1] = x.y; v[4 * q + 2] = x.z; v[4 * q + 3] = x.w;
+    }
+  } else {
+#pragma unroll
+    for (uint32_t j = 0; j < kScanItems; ++j) v[j] = k0 + j < n ? a[k0 + j] : 0u;
+  }
+}
+
+// Phase 1: the total of every chunk of kScanChunk counters of the round
+// (ctl->ncounters values).
 __global__ void __launch_bounds__(kBlock) k_scan_reduce(const BigCtl* __restrict__ ctl) {
   const uint64_t n = ctl->ncounters;
   const uint32_t* __restrict__ a = ctl->counters;
@@ -550,64 +570,69 @@ __global__ void __launch_bounds__(kBlock) k_scan_reduce(const BigCtl* __restrict
   const uint64_t nb = (n + kScanChunk - 1) / kScanChunk;
   unsigned long long bytes = 0;
   for (uint64_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
-    const uint64_t b0 = blk * kScanChunk;
+    const uint64_t c0 = blk * kScanChunk;
+    uint32_t v[kScanItems];
+    load_scan_items(a, n, c0 + (uint64_t)threadIdx.x * kScanItems, c0 + kScanChunk <= n, v);
     uint32_t s = 0;
-    for (uint32_t i = threadIdx.x; i < kScanChunk; i += kBlock) {
-      const uint64_t k = b0 + i;
-      if (k < n) s += a[k];
-    }
+#pragma unroll
+    for (uint32_t j = 0; j < kScanItems; ++j) s += v[j];
     uint32_t ex;
     const uint32_t total = block_excl_scan(s, ex);
     if (threadIdx.x == 0) {
       part[blk] = total;
-      const uint64_t left = n - b0;
+      const uint64_t left = n - c0;
       bytes += 4ull * (left < kScanChunk ? left : kScanChunk);
     }
   }
   account(ctl->c, kKScan, bytes);
 }
 
-__global__ void __launch_bounds__(kBlock) k_scan_partials(const BigCtl* __restrict__ ctl) {
-  const uint64_t n = ctl->ncounters;
-  uint32_t* __restrict__ part = ctl->partials;
-  const uint32_t m = (uint32_t)((n + kScanChunk - 1) / kScanChunk);
-  uint32_t carry = 0;
-  for (uint32_t i0 = 0; i0 < m; i0 += kBlock) {
-    const uint32_t i = i0 + threadIdx.x;
-    const uint32_t v = i < m ? part[i] : 0;
-    uint32_t ex;
-    const uint32_t total = block_excl_scan(v, ex);
-    if (i < m) part[i] = carry + ex;
-    carry += total;
-  }
-}
-
+// Phase 2: every counter replaced by the sum of the counters before it.  A
+// block finds the offset of its chunk by summing the chunk totals before it
+// (carried from one of its chunks to its next), so no third kernel scans the
+// totals.
 __global__ void __launch_bounds__(kBlock) k_scan_down(const BigCtl* __restrict__ ctl) {
   const uint64_t n = ctl->ncounters;
   uint32_t* __restrict__ a = ctl->counters;
   const uint32_t* __restrict__ part = ctl->partials;
   const uint64_t nb = (n + kScanChunk - 1) / kScanChunk;
   unsigned long long bytes = 0;
+  uint32_t pre = 0;   // sum of part[0, upto)
+  uint64_t upto = 0;
   for (uint64_t blk = blockIdx.x; blk < nb; blk += gridDim.x) {
-    const uint64_t b0 = blk * kScanChunk + (uint64_t)threadIdx.x * kScanItems;
+    uint32_t ps = 0;
+    for (uint64_t i = upto + threadIdx.x; i < blk; i += kBlock) ps += part[i];
+    uint32_t unused;
+    pre += block_excl_scan(ps, unused);
+    upto = blk;
+    const uint64_t c0 = blk * kScanChunk;
+    const uint64_t k0 = c0 + (uint64_t)threadIdx.x * kScanItems;
+    const bool full = c0 + kScanChunk <= n;
     uint32_t v[kScanItems];
+    load_scan_items(a, n, k0, full, v);
     uint32_t s = 0;
 #pragma unroll
-    for (uint32_t j = 0; j < kScanItems; ++j) {
-      const uint64_t k = b0 + j;
-      v[j] = k < n ? a[k] : 0;
-      s += v[j];
-    }
+    for (uint32_t j = 0; j < kScanItems; ++j) s += v[j];
     uint32_t ex;
     block_excl_scan(s, ex);
-    uint32_t run = part[blk] + ex;
+    uint32_t run = pre + ex;
 #pragma unroll
     for (uint32_t j = 0; j < kScanItems; ++j) {
-      const uint64_t k = b0 + j;
-      if (k < n) a[k] = run;
-      run += v[j];
+      const uint32_t x = v[j];
+      v[j] = run;
+      run += x;
     }
-    const uint64_t left = n > b0 ? n - b0 : 0;
+    if (full) {
+      uint4* a4 = reinterpret_cast<uint4*>(a + k0);
+#pragma unroll
+      for (uint32_t q = 0; q < kScanItems / 4; ++q)
+        a4[q] = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (uint32_t j = 0; j < kScanItems; ++j)
+        if (k0 + j < n) a[k0 + j] = v[j];
+    }
+    const uint64_t left = n > k0 ? n - k0 : 0;
     bytes += 8ull * (left < kScanItems ? left : kScanItems);
   }
   account(ctl->c, kKScan, bytes);
@@ -648,7 +673,6 @@ static cudaError_t launch_big_round_t(BigCtl* ctl, uint32_t R_max, uint32_t sms,
   hook.run("big_sample", [&] { k_big_sample<LOGV><<<sms * 8, kBlock, 0, st>>>(ctl, &ctl->next_item[0]); });
   hook.run("big_classify", [&] { k_big_classify<LOGV><<<sms * 8, kBlock, 0, st>>>(ctl, &ctl->next_item[1]); });
   hook.run("scan", [&] { k_scan_reduce<<<sms * 8, kBlock, 0, st>>>(ctl); });
-  hook.run("scan", [&] { k_scan_partials<<<1, kBlock, 0, st>>>(ctl); });
   hook.run("scan", [&] { k_scan_down<<<sms * 8, kBlock, 0, st>>>(ctl); });
   hook.run("big_emit", [&] { k_big_emit<LOGV><<<sms * 8, kBlock, 0, st>>>(ctl, &ctl->next_item[2]); });
   hook.run("big_scatter", [&] { k_big_scatter<LOGV><<<sms * 3, kBlock, smem, st>>>(ctl, &ctl->next_item[3]); });

@@ -526,12 +526,12 @@ __device__ __forceinline__ bool wait_flag(const uint32_t* flag, uint32_t want, u
   return true;
 }
 
-// Push to the work queue of the persistent kernel.  The slot's previous task
-// has always been claimed already (see WorkQueue); the wait only covers the
-// moment between that claim and its read.
-__device__ __forceinline__ void queue_push(const WorkQueue& q, const Task& t, uint32_t* status, uint64_t wait_ns) {
-  atomicAdd(q.pending, 1u);
-  const uint32_t k = atomicAdd(q.tail, 1u);
+// Writes task t to slot k of the work queue's ring, once the slot's previous
+// task has been claimed (see WorkQueue: that claim has always happened
+// already; the wait only covers the moment between it and its read).  The
+// caller has counted the task in q.pending and taken k from q.tail.
+__device__ __forceinline__ void queue_put(const WorkQueue& q, uint32_t k, const Task& t, uint32_t* status,
+                                          uint64_t wait_ns) {
   const uint32_t slot = k % q.cap, lap = k / q.cap;
   if (!wait_flag(q.ready + slot, 2 * lap, wait_ns)) {
     latch_status(status, kStTimeout);
@@ -544,16 +544,68 @@ __device__ __forceinline__ void queue_push(const WorkQueue& q, const Task& t, ui
   atomicExch(q.ready + slot, 2 * lap + 1);
 }
 
-// Route a new subset (len >= 2, not finished) to the list that handles its size.
-__device__ __forceinline__ void route_task(const SortCtx& c, const Task& t, uint32_t next_big) {
-  if (t.depth > kMaxDepth) { latch_status(c.status, kStTooDeep); return; }
-  if (c.big_enabled && t.len > c.big_threshold) list_push(c.big[next_big], t, c.status);
-  else if (t.len > c.small_cutoff) queue_push(c.mq, t, c.status, c.wait_ns);
-  else if (t.len > 32) list_push(t.len > kSmallCtaNarrowMax ? c.small_cta_wide : c.small_cta, t, c.status);
-  else list_push(c.small_warp, t, c.status);
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
 }
 
-__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+// Route new subsets (len >= 2, not finished) to the lists that handle their
+// sizes.  The lanes of a warp that call it together take their slots in each
+// list with one atomic per list: every block of the sort appends to the same
+// few counters, and one atomic per lane would queue up at those addresses.
+__device__ __forceinline__ void route_task(const SortCtx& c, const Task& t, uint32_t next_big) {
+  constexpr uint32_t kToBig = 0, kToQueue = 1, kToCtaWide = 2, kToCta = 3, kToWarp = 4, kToNone = 5;
+  const uint32_t len = t.len;
+  uint32_t to = len > 32 ? (len > kSmallCtaNarrowMax ? kToCtaWide : kToCta) : kToWarp;
+  to = len > c.small_cutoff ? kToQueue : to;
+  to = (c.big_enabled && len > c.big_threshold) ? kToBig : to;
+  to = t.depth > kMaxDepth ? kToNone : to;
+  const uint32_t active = __activemask();
+  uint32_t peers = 0;  // the calling lanes with the same destination
+#pragma unroll
+  for (uint32_t k = 0; k <= kToNone; ++k) {
+    const uint32_t m = __ballot_sync(active, to == k);
+    peers = to == k ? m : peers;
+  }
+  const uint32_t leader = __ffs(peers) - 1;
+  uint32_t* const ctr = to == kToBig ? c.big[next_big].count
+                        : to == kToQueue ? c.mq.tail
+                        : to == kToCtaWide ? c.small_cta_wide.count
+                        : to == kToCta ? c.small_cta.count : c.small_warp.count;
+  uint32_t base = 0;
+  if (to != kToNone && lane_id() == leader) {
+    if (to == kToQueue) atomicAdd(c.mq.pending, (uint32_t)__popc(peers));  // counted before they can be claimed
+    base = atomicAdd(ctr, (uint32_t)__popc(peers));
+  }
+  base = __shfl_sync(active, base, leader);
+  const uint32_t k = base + __popc(peers & lanemask_lt());
+  if (to == kToNone) {
+    latch_status(c.status, kStTooDeep);
+  } else if (to == kToQueue) {
+    queue_put(c.mq, k, t, c.status, c.wait_ns);
+  } else {
+    const TaskList& l = to == kToBig ? c.big[next_big]
+                        : to == kToCtaWide ? c.small_cta_wide
+                        : to == kToCta ? c.small_cta : c.small_warp;
+    if (k < l.cap) l.items[k] = t;
+    else latch_status(c.status, kStQueueFull);
+  }
+}
+
+// A slot of *counter for each calling lane of the warp with pred set: the
+// lanes that call it together take consecutive slots with one atomic.
+__device__ __forceinline__ uint32_t warp_slot(uint32_t* counter, bool pred) {
+  const uint32_t active = __activemask();
+  const uint32_t peers = __ballot_sync(active, pred);
+  const uint32_t leader = peers ? __ffs(peers) - 1 : __ffs(active) - 1;
+  uint32_t base = 0;
+  if (peers && lane_id() == leader) base = atomicAdd(counter, (uint32_t)__popc(peers));
+  base = __shfl_sync(active, base, leader);
+  return base + __popc(peers & lanemask_lt());
+}
 
 // Adds a thread's algorithmic byte count to its kernel class (one atomic per
 // warp; every lane of the warp must call it).
@@ -561,11 +613,6 @@ __device__ __forceinline__ void account(const SortCtx& c, uint32_t cls, unsigned
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) bytes += __shfl_xor_sync(0xFFFFFFFFu, bytes, o);
   if ((threadIdx.x & 31u) == 0 && bytes) atomicAdd(c.abytes + cls, bytes);
-}
-__device__ __forceinline__ uint32_t lanemask_lt() {
-  uint32_t m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
 }
 
 }  // namespace ss

@@ -56,8 +56,8 @@ struct BigCtl {
 constexpr uint32_t kMaxBigRounds = 1u << 20;
 
 // Kernel launches of one multi-block round after its plan: sample, classify,
-// the three prefix-sum kernels, emit and scatter.
-constexpr uint32_t kBigRoundKernels = 7;
+// the two prefix-sum kernels, emit and scatter.
+constexpr uint32_t kBigRoundKernels = 6;
 
 size_t big_splitters_bytes(int logv);
 size_t big_scatter_smem(int logv, uint32_t R);

@@ -294,8 +294,8 @@ __device__ __forceinline__ void classify_batch(const K (&k)[U], uint32_t (&b)[U]
 }
 
 // Classifies n keys (the classification loop of Algorithm 4.1): writes the bucket of
-// keys[p] to bo[p] and counts it in hist (shared memory, warp-aggregated
-// atomics).  Each thread loads 8 keys before descending the tree for them,
+// keys[p] to bo[p] and counts it in hist (one shared-memory atomic per key:
+// cheaper than grouping a warp's equal buckets with __match_any_sync first).  Each thread loads 8 keys before descending the tree for them,
 // so that the loads of a batch overlap.  Returns this thread's records.
 template <int LOGV, typename K, typename KeyAt>
 __device__ __forceinline__ uint32_t classify_count_k(KeyAt&& key_at, uint16_t* __restrict__ bo, uint32_t n,
@@ -324,8 +324,7 @@ __device__ __forceinline__ uint32_t classify_count_k(KeyAt&& key_at, uint16_t* _
         bo[p] = (uint16_t)b;
         ++mine;
       }
-      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
-      if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[b], (uint32_t)__popc(peers));
+      if (valid) atomicAdd(&hist[b], 1u);
       if constexpr (sizeof(K) == 8) {
         // smallest and largest key of each even bucket (an equality bucket's
         // keys all equal its splitter), for the LCPs at bucket boundaries
@@ -395,11 +394,7 @@ __device__ void tile_scatter(const uint16_t* tb, uint32_t tl, uint32_t R, uint32
   const uint32_t p0 = w * 32 * R;
   for (uint32_t r = 0; r < R; ++r) {
     const uint32_t p = p0 + r * 32 + lane;
-    const bool valid = p < tl;
-    const uint32_t b = valid ? tb[p] : 0xFFFFu;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
-    if (valid && lane == (uint32_t)(__ffs(peers) - 1)) mine[b] += __popc(peers);
-    __syncwarp();
+    if (p < tl) atomicAdd(&mine[tb[p]], 1u);  // counts only: no need to group equal buckets
   }
   __syncthreads();
   for (uint32_t b = threadIdx.x; b < G::K; b += blockDim.x) {
