@@ -69,7 +69,7 @@ typedef struct ss_options {
                                   ends after max_len bytes: a byte at position
                                   >= max_len reads as the terminator.           */
     uint32_t splitters_log2;   /* d with v = 2^d - 1 splitters per step in the
-                                  single-block steps; 8..10 (default 8).        */
+                                  single-block steps; 7..10 (default 8).        */
     uint32_t big_splitters_log2; /* d for the multi-block steps (16-character keys);
                                   8..9 (default 9).                              */
     uint32_t tile_rounds;      /* multi-block tile = 256 * tile_rounds strings;

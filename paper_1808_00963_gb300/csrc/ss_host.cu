@@ -123,7 +123,7 @@ static ss_status device_info(DevInfo& out) {
     d.ok = (p.major == 10 && p.minor == 3);
     d.sms = p.multiProcessorCount;
     if (d.ok) {
-      for (int l = 8; l <= 10; ++l) {
+      for (int l = 7; l <= 10; ++l) {
         int b = 0;
         if (queue_occupancy(l, &b) != cudaSuccess || b < 1) return SS_ERR_CUDA;
         d.queue_blocks[l] = b;
@@ -170,7 +170,7 @@ static ss_status resolve_opts(const ss_options* o, Opts& r) {
   r.host_parts = o->host_parts;
   if (o->max_len) r.cap = o->max_len;
   if (o->splitters_log2) {
-    if (o->splitters_log2 < 8 || o->splitters_log2 > 10) return SS_ERR_INVALID;
+    if (o->splitters_log2 < 7 || o->splitters_log2 > 10) return SS_ERR_INVALID;
     r.logv = (int)o->splitters_log2;
   }
   if (o->big_splitters_log2) {  // wide keys: 2^10 splitters would not fit a block's static shared memory

@@ -255,6 +255,7 @@ cudaError_t set_queue_attr() {
 
 size_t queue_smem(int logv) {
   switch (logv) {
+    case 7: return sizeof(QueueSmem<7>);
     case 8: return sizeof(QueueSmem<8>);
     case 9: return sizeof(QueueSmem<9>);
     default: return sizeof(QueueSmem<10>);
@@ -263,6 +264,9 @@ size_t queue_smem(int logv) {
 
 cudaError_t queue_occupancy(int logv, int* blocks_per_sm) {
   switch (logv) {
+    case 7:
+      if (cudaError_t e = set_queue_attr<7>()) return e;
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_queue<7>, kBlock, sizeof(QueueSmem<7>));
     case 8:
       if (cudaError_t e = set_queue_attr<8>()) return e;
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_queue<8>, kBlock, sizeof(QueueSmem<8>));
@@ -279,6 +283,10 @@ cudaError_t queue_occupancy(int logv, int* blocks_per_sm) {
 cudaError_t launch_queue(int logv, const SortCtx& c, uint32_t grid, uint32_t R, cudaStream_t st,
                          const LaunchHook& hook) {
   switch (logv) {
+    case 7:
+      if (cudaError_t e = set_queue_attr<7>()) return e;
+      hook.run("queue", [&] { k_queue<7><<<grid, kBlock, sizeof(QueueSmem<7>), st>>>(c, R); });
+      break;
     case 8:
       if (cudaError_t e = set_queue_attr<8>()) return e;
       hook.run("queue", [&] { k_queue<8><<<grid, kBlock, sizeof(QueueSmem<8>), st>>>(c, R); });

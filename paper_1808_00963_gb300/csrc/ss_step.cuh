@@ -373,6 +373,23 @@ __device__ __forceinline__ uint32_t bucket_desc(uint32_t b, uint32_t size, uint3
 constexpr int kMoveBatch = 4;
 constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 
+// The lanes of the warp whose record falls into the same bucket b as this
+// lane's (valid lanes only; every lane of the warp calls it): the mask of
+// valid lanes narrowed by one ballot per bit of the bucket index.  Cheaper to
+// issue than __match_any_sync (measured on the distribution) and stable in
+// lane order like it.
+template <int LOGV>
+__device__ __forceinline__ uint32_t bucket_peers(uint32_t b, bool valid) {
+  uint32_t m = __ballot_sync(0xFFFFFFFFu, valid);
+#pragma unroll
+  for (int i = 0; i <= LOGV; ++i) {  // bucket indices have LOGV + 1 bits
+    const bool bit = (b >> i) & 1u;
+    const uint32_t v = __ballot_sync(0xFFFFFFFFu, bit);
+    m &= bit ? v : ~v;
+  }
+  return m;
+}
+
 // Stable distribution of one tile of records (the redistribution of Algorithm 4.1 with the
 // per-processor bucket arrays of Theorem 4.4, one per warp).
 //   tb[0..tl)    bucket of each record of the tile (shared memory)
@@ -380,7 +397,8 @@ constexpr uint32_t kInvalid = 0xFFFFFFFFu;
 //                out: base[b] + number of the tile's records in bucket b
 //   cntw         shared scratch, kWarps * KP uint32
 // Warp w owns records [w * 32R, (w + 1) * 32R) of the tile; inside a warp
-// ranks come from __match_any_sync, so equal buckets keep input order.
+// ranks come from the lanes with the same bucket (bucket_peers), so equal
+// buckets keep input order.
 // move(p[], b[], dest[]) is called with kMoveBatch rounds of one warp at a time
 // (p = kInvalid for lanes without a record).  Ends with __syncthreads().
 template <int LOGV, int MB = kMoveBatch, typename Move>
@@ -416,8 +434,8 @@ __device__ void tile_scatter(const uint16_t* tb, uint32_t tl, uint32_t R, uint32
       const uint32_t r = r0 + u;
       const uint32_t p = p0 + r * 32 + lane;
       const bool valid = r < R && p < tl;
-      const uint32_t b = valid ? tb[p] : 0xFFFFu;
-      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, b);
+      const uint32_t b = valid ? tb[p] : 0u;
+      const uint32_t peers = bucket_peers<LOGV>(b, valid);
       uint32_t dest = 0;
       if (valid) dest = mine[b] + __popc(peers & lt);
       __syncwarp();

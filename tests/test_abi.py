@@ -51,7 +51,7 @@ def test_host_side_argument_checks(lib):
     assert lib.ss_sort_ex(None, dummy, 5, dummy, None, ctypes.byref(o), None) == 1
     assert lib.ss_sort_ex(dummy, dummy, 5, None, None, ctypes.byref(o), None) == 1
     # option ranges
-    for bad in (dict(splitters_log2=7), dict(splitters_log2=11), dict(small_cutoff=32),
+    for bad in (dict(splitters_log2=6), dict(splitters_log2=11), dict(small_cutoff=32),
                 dict(small_cutoff=8192), dict(tile_rounds=64), dict(host_parts=3), dict(host_parts=32), dict(classifier=4),
                 dict(small_cutoff=1024, big_threshold=512),
                 dict(big_splitters_log2=7), dict(big_splitters_log2=10)):

@@ -138,6 +138,8 @@ def test_sizes(kind, n):
 @pytest.mark.parametrize("opts", [dict(big_threshold=2048), dict(big_threshold=4096, big_splitters_log2=8),
                                   dict(big_threshold=2048, big_splitters_log2=9, tile_rounds=8),
                                   dict(splitters_log2=8, small_cutoff=64),
+                                  dict(splitters_log2=7, small_cutoff=128),
+                                  dict(splitters_log2=7, big_threshold=32768),
                                   dict(splitters_log2=10, small_cutoff=4096),
                                   dict(small_cutoff=256, big_threshold=256)])
 def test_paths(kind, opts):
