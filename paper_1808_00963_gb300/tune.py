@@ -10,7 +10,9 @@ move time between the kernels:
   tile_rounds         multi-block tile = 256 * rounds strings (0 = chosen per step)
 
 For each workload class the tuner runs a coordinate descent (one parameter
-at a time, two passes) timing complete sorts with CUDA events, and writes
+at a time, two passes) timing complete sorts with CUDA events, starting from
+the options the existing table holds for that class (so that a retune after
+a kernel change moves only where it measures a gain), and writes
   tuned.json      best options per workload class (and for the batched form)
   csrc/ss_tuned.h the compiled-in defaults: the options with the best
                   geometric mean over the plain workload classes
@@ -104,9 +106,9 @@ def _timer_batch(sets, reps):
     return run
 
 
-def coordinate_descent(run, space, start, passes=2, log=print):
+def coordinate_descent(run, space, start, passes=2, log=print, cache=None):
     best = dict(start)
-    cache = {}
+    cache = {} if cache is None else cache
 
     def cost(o):
         key = tuple(sorted(o.items()))
@@ -129,6 +131,17 @@ def coordinate_descent(run, space, start, passes=2, log=print):
         if not improved:
             break
     return best, best_ms, cache
+
+
+def warm_start(table, path, space, default):
+    """The options stored at table[path[0]][path[1]]...["options"] restricted
+    to the keys and values of `space`, completed from `default`; `default`
+    when the table has no such entry."""
+    e = table
+    for k in path:
+        e = e.get(k, {}) if isinstance(e, dict) else {}
+    o = e.get("options", {}) if isinstance(e, dict) else {}
+    return {k: (o[k] if o.get(k) in vals else default[k]) for k, vals in space.items()}
 
 
 def write_header(opts, path=HEADER):
@@ -170,12 +183,21 @@ def main(argv=None):
             "dna": gen.config3(1_000_000 if args.quick else 4_000_000),
             "random": gen.config1()}
     passes = 1 if args.quick else 2
+    try:
+        with open(TABLE) as f:
+            old = json.load(f)
+    except (OSError, ValueError):
+        old = {}
     table = {"plain": {}, "space": SPACE}
     all_costs = {}
     for name, s in sets.items():
         print(f"== {name}: n={s.n}", flush=True)
-        best, ms, cache = coordinate_descent(_timer_plain(s, args.reps if name != "random" else 4 * args.reps),
-                                             SPACE, START, passes)
+        run = _timer_plain(s, args.reps if name != "random" else 4 * args.reps)
+        # START is timed for every class, so that the default below always
+        # has a configuration every class measured
+        best, ms, cache = coordinate_descent(run, SPACE, START, 0)
+        best, ms, cache = coordinate_descent(run, SPACE, warm_start(old, ("plain", name), SPACE, START), passes,
+                                             cache=cache)
         table["plain"][name] = {"options": best, "ms": ms, "n": s.n}
         all_costs[name] = cache
         print(f"   best {best} {ms:.3f} ms", flush=True)
@@ -187,8 +209,9 @@ def main(argv=None):
     print(f"== default {dict(dkey)} geomean {geo[dkey]:.3f} ms", flush=True)
     # batched form (512 sets of the batched workload)
     bsets = gen.batch_sets(128 if args.quick else 512, 4)
+    bstart = {"splitters_log2": 8, "small_cutoff": 1024, "big_threshold": 8192}
     best, ms, _ = coordinate_descent(_timer_batch(bsets, args.reps), BATCH_SPACE,
-                                     {"splitters_log2": 8, "small_cutoff": 1024, "big_threshold": 8192}, passes)
+                                     warm_start(old, ("batched",), BATCH_SPACE, bstart), passes)
     table["batched"] = {"options": best, "ms": ms, "sets": len(bsets)}
     print(f"== batched {best} {ms:.3f} ms", flush=True)
     if not args.no_write:

@@ -43,3 +43,26 @@ def test_write_header(tmp_path):
     tune.write_header(tune.START, p)
     txt = open(p).read()
     assert "#define SS_TUNED_TILE_ROUNDS 0" in txt and "#pragma once" in txt
+
+
+def test_warm_start_takes_stored_options_within_the_space():
+    space = {"a": [1, 2, 3], "b": [10, 20]}
+    table = {"plain": {"url": {"options": {"a": 3, "b": 99, "c": 5}}}}
+    # a value outside the space and a missing key fall back to the default
+    assert tune.warm_start(table, ("plain", "url"), space, {"a": 1, "b": 10}) == {"a": 3, "b": 10}
+    assert tune.warm_start(table, ("plain", "dna"), space, {"a": 1, "b": 10}) == {"a": 1, "b": 10}
+    assert tune.warm_start({}, ("batched",), space, {"a": 2, "b": 20}) == {"a": 2, "b": 20}
+
+
+def test_descent_reuses_timings_across_starts():
+    space = {"a": [1, 2, 3]}
+    calls = []
+
+    def run(o):
+        calls.append(dict(o))
+        return float(o["a"])
+
+    _, _, cache = tune.coordinate_descent(run, space, {"a": 3}, 0, log=lambda *_: None)
+    best, ms, cache = tune.coordinate_descent(run, space, {"a": 2}, 1, log=lambda *_: None, cache=cache)
+    assert best == {"a": 1} and ms == 1.0
+    assert len(calls) == 3  # a = 3 was timed once, then reused
